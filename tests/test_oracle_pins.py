@@ -1,0 +1,351 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+rational arithmetic on tiny inputs, closed forms, the paper's printed values
+(tests/golden/), the error bounds it proves, invariants, or a library
+conversion routine.  A plausible mistake in the oracle (dropped term, wrong
+sign or index, transposed operand, wrong tie-break, wrong rounding) fails at
+least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_12208_gb300 import workloads
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _exact_dist(x, y):
+    return sum((Fraction(float(a)) - Fraction(float(b))) ** 2 for a, b in zip(x, y))
+
+
+# --- Table 1.1 -------------------------------------------------------------
+def test_unit_roundoffs_match_table_1_1():
+    g = json.load(open(os.path.join(GOLD, "table_1_1.json")))["formats"]
+    for name, fmt in (("fp16", 0), ("bf16", 1), ("fp32", 3), ("fp64", 4)):
+        u = oracle.unit_roundoff(fmt)
+        assert abs(u - g[name]["u"]) / g[name]["u"] < 5e-3, name
+        assert u == 2.0 ** -g[name]["t"]
+    for name, fmt in (("fp16", 0), ("bf16", 1)):
+        xmax = g[name]["xmax"]
+        got = oracle.round_to_format(1e300 if fmt == 1 else 6.55e4, fmt)
+        if fmt == 0:
+            assert abs(got - xmax) / xmax < 5e-3
+        xmin = 2.0 ** g[name]["emin"]
+        assert abs(xmin - g[name]["xmin"]) / g[name]["xmin"] < 5e-3
+        assert oracle.round_to_format(xmin, fmt) == xmin
+
+
+@pytest.mark.parametrize("fmt,tdtype", [(0, "float16"), (1, "bfloat16"), (2, "float8_e4m3fn")])
+def test_quantize_matches_torch_conversion(fmt, tdtype):
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, tdtype):
+        pytest.skip("torch lacks " + tdtype)
+    r = np.random.default_rng(5)
+    lim = {0: 6e4, 1: 1e30, 2: 440.0}[fmt]
+    xs = [r.uniform(-1, 1, 4000) * 10.0 ** r.uniform(-12, np.log10(lim), 4000)]
+    # ties, subnormals, exact values
+    if fmt == 0:
+        xs.append(np.array([2.0 ** -24, 1.5 * 2.0 ** -24, 2.5 * 2.0 ** -24, 2.0 ** -25, 1 + 2.0 ** -11,
+                            1 + 3 * 2.0 ** -11, 65504.0, 65519.0, -3e-8]))
+    if fmt == 1:
+        xs.append(np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 2.0 ** -133, 3 * 2.0 ** -134,
+                            1e-39, -1.5e-40]))
+    if fmt == 2:
+        xs.append(np.array([2.0 ** -9, 1.5 * 2.0 ** -9, 2.5 * 2.0 ** -9, 2.0 ** -10, 448.0, 1.0625,
+                            1.1875, -0.013]))
+    x = np.concatenate(xs).astype(np.float32)
+    ref = torch.from_numpy(x).to(getattr(torch, tdtype)).to(torch.float32).numpy()
+    got = oracle.quantize(x, fmt)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_e4m3_saturates():
+    assert oracle.round_to_format(1e6, 2) == 448.0
+    assert oracle.round_to_format(-465.0, 2) == -448.0
+    assert oracle.round_to_format(70000.0, 0) == math.inf
+
+
+# --- Eq. (dist-direct), Theorem 4.1 -----------------------------------------
+def test_dist_direct_exact_on_tiny_inputs_and_theorem_4_1():
+    r = np.random.default_rng(1)
+    for d in (1, 3, 7, 16):
+        X = (r.normal(size=(5, d)) * 10.0 ** r.uniform(-3, 3, size=(5, 1))).astype(np.float32)
+        C = (X[:3] + r.normal(size=(3, d)) * 1e-3).astype(np.float32)
+        D = oracle.dist_direct(X, C)
+        g = oracle.gamma(d + 2, 2.0 ** -53)
+        for i in range(5):
+            for j in range(3):
+                ex = _exact_dist(X[i], C[j])
+                assert abs(Fraction(D[i, j]) - ex) <= Fraction(g) * ex
+        # transposition / index check: D[i, j] belongs to (X_i, C_j)
+        assert D[1, 2] == pytest.approx(float(_exact_dist(X[1], C[2])), rel=1e-14)
+
+
+def test_dist_direct_zero_and_symmetry():
+    r = np.random.default_rng(2)
+    X = r.normal(size=(6, 5)).astype(np.float32)
+    D = oracle.dist_direct(X, X)
+    assert np.all(np.diag(D) == 0.0)
+    np.testing.assert_array_equal(D, D.T)
+
+
+# --- Alg. 1 assignment ------------------------------------------------------
+def test_assign_brute_force_and_ties():
+    r = np.random.default_rng(3)
+    X = r.integers(-3, 4, size=(40, 3)).astype(np.float32)
+    C = r.integers(-3, 4, size=(6, 3)).astype(np.float32)
+    C[4] = C[1]  # duplicate centre: ties must go to the lower index
+    lab, d1, d2 = oracle.assign(X, C)
+    for i in range(40):
+        ds = [_exact_dist(X[i], C[j]) for j in range(6)]
+        m = min(ds)
+        assert lab[i] == ds.index(m)
+        assert Fraction(d1[i]) == m
+        rest = sorted(ds)
+        assert Fraction(d2[i]) == rest[1]
+    assert not np.any(lab == 4)
+
+
+def test_assign_k1_second_is_inf():
+    X = np.ones((3, 2), np.float32)
+    lab, d1, d2 = oracle.assign(X, X[:1])
+    assert np.all(lab == 0) and np.all(np.isinf(d2))
+
+
+# --- Eq. (center), Lemma 4.4, Lemma 2.1 ------------------------------------
+def test_update_is_mean_within_lemma_4_4():
+    r = np.random.default_rng(4)
+    n, d, k = 300, 4, 5
+    X = (r.normal(size=(n, d)) * 3 + 100).astype(np.float32)
+    lab = r.integers(0, k, size=n).astype(np.int32)
+    C0 = np.zeros((k, d), np.float32)
+    C, cnt, shift = oracle.update(X, lab, C0, empty_policy=0)
+    for j in range(k):
+        mem = X[lab == j]
+        assert cnt[j] == len(mem)
+        for l in range(d):
+            mu = sum(Fraction(float(v)) for v in mem[:, l]) / len(mem)
+            abar = sum(abs(Fraction(float(v))) for v in mem[:, l]) / len(mem)
+            tol = Fraction(oracle.gamma(len(mem), 2.0 ** -53)) * abar + Fraction(2.0 ** -24) * abs(mu)
+            assert abs(Fraction(float(C[j, l])) - mu) <= tol
+    ex_shift = max(math.sqrt(float(sum(Fraction(float(v)) ** 2 for v in C[j]))) for j in range(k))
+    assert shift == pytest.approx(ex_shift, rel=1e-12)
+
+
+def test_lemma_2_1_identity():
+    # phi(p, S) = phi(mu, S) + |S| dist(p, mu)^2 with mu the exact mean
+    r = np.random.default_rng(6)
+    S = r.integers(-20, 20, size=(8, 3)).astype(np.float32)
+    p = np.array([[1.5, -2.0, 7.25]], np.float32)
+    lab = np.zeros(8, np.int32)
+    C, _, _ = oracle.update(S, lab, np.zeros((1, 3), np.float32))
+    mu = [sum(Fraction(float(v)) for v in S[:, l]) / 8 for l in range(3)]
+    # the fp32 mean equals the exact mean when it is representable (here: multiples of 1/8)
+    assert [Fraction(float(v)) for v in C[0]] == mu
+    phi_p = Fraction(float(oracle.dist_direct(S, p).sum()))
+    phi_mu = Fraction(float(oracle.dist_direct(S, C).sum()))
+    dpm = Fraction(float(oracle.dist_direct(p, C)[0, 0]))
+    assert phi_p == phi_mu + 8 * dpm
+
+
+def test_empty_cluster_policies():
+    X = np.array([[0.0], [1.0], [5.0], [9.0]], np.float32)
+    lab = np.array([0, 0, 0, 0], np.int32)
+    C0 = np.array([[1.0], [50.0], [60.0]], np.float32)
+    md = np.array([1.0, 0.0, 16.0, 64.0])
+    C, cnt, _ = oracle.update(X, lab, C0, empty_policy=0)
+    assert C[1, 0] == 50.0 and C[2, 0] == 60.0 and cnt.tolist() == [4, 0, 0]
+    C, cnt, _ = oracle.update(X, lab, C0, empty_policy=1, min_dist=md)
+    assert C[0, 0] == 3.75 and C[1, 0] == 9.0 and C[2, 0] == 5.0
+
+
+# --- Alg. 1 driver ----------------------------------------------------------
+def test_lloyd_closed_form_1d():
+    g = json.load(open(os.path.join(GOLD, "lloyd_1d_closed_form.json")))
+    X = np.array(g["X"], np.float32)
+    C0 = np.array(g["C_init"], np.float32)
+    C, lab, sse, it = oracle.lloyd(X, C0, g["max_iter"])
+    assert it == g["max_iter"]
+    np.testing.assert_allclose(sse, g["sse_per_iter"], rtol=1e-15)
+    assert lab.tolist() == g["final_labels"]
+    np.testing.assert_array_equal(C, np.array(g["final_centres"], np.float32))
+    # tau stop: the shift is 0 after the third update, so tau = 1e-8 stops there
+    C, lab, sse, it = oracle.lloyd(X, C0, 50, tau=1e-8)
+    assert it == 3
+
+
+def test_lloyd_invariants_on_blobs():
+    X, C0 = workloads.blobs(2000, 6, 7, seed=11)
+    C, lab, sse, it = oracle.lloyd(X, C0, 15)
+    # SSE never increases (Lemma 2.1 + argmin, Section 3)
+    assert np.all(np.diff(sse) <= 1e-9 * sse[:-1])
+    # every label is an argmin with the lowest-index tie-break
+    D = oracle.dist_direct(X, C)
+    assert np.all(D[np.arange(len(X)), lab] <= D.min(axis=1))
+    # one more Lloyd step from C reproduces update(assign(C))
+    lab1, md1, _ = oracle.assign(X, C)
+    C1, _, _ = oracle.update(X, lab1, C, empty_policy=1, min_dist=md1)
+    C2, _, _, _ = oracle.lloyd(X, C, 1)
+    np.testing.assert_array_equal(C1, C2)
+
+
+# --- Alg. 2 -----------------------------------------------------------------
+def test_alg2_closed_form_thresholds():
+    g = json.load(open(os.path.join(GOLD, "alg2_closed_forms.json")))["bf16_rho5"]
+    for cA, key in ((1.0, "c_A_1_first_r_all_flagged"), (2.0, "c_A_2_first_r_all_flagged")):
+        rstar = g[key]
+        for r in range(8, 140):
+            x = np.zeros(r, np.float32); x[0] = 1.0
+            flag, d, dh, E = oracle.mp_dist_paper(x, -x, 5.0, 1, c_A=cA)
+            assert flag == (r >= rstar), (cA, r)
+            assert dh == 4.0
+            assert d == 4.0  # flagged pairs fall back to the exact direct value
+        # beyond the threshold every pair is flagged
+        rng = np.random.default_rng(7)
+        for r in (rstar, 128):
+            for _ in range(50):
+                x = rng.normal(size=r).astype(np.float32)
+                y = rng.normal(size=r).astype(np.float32) * rng.uniform(0.1, 10)
+                assert oracle.mp_dist_paper(x, y, 5.0, 1, c_A=cA)[0]
+
+
+def test_alg2_same_point_always_flagged():
+    rng = np.random.default_rng(8)
+    for fmt in (0, 1):
+        x = rng.normal(size=16).astype(np.float32)
+        flag, d, _, _ = oracle.mp_dist_paper(x, x, 5.0, fmt)
+        assert flag and d == 0.0
+
+
+def test_alg2_undefined_gamma():
+    x = np.ones(300, np.float32)
+    assert oracle.mp_dist_paper(x, x, 5.0, 1)[0] is None  # bf16: (r+2) u >= 1
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_worked_cancellation_example(fmt):
+    # Section 4.3: x unit, y = x + delta, ||delta|| = 10 u (u = fp32 unit roundoff)
+    u = 2.0 ** -24
+    rng = np.random.default_rng(9)
+    for r in (4, 16):
+        x = rng.normal(size=r); x /= np.linalg.norm(x); x = x.astype(np.float32)
+        delta = np.zeros(r); delta[1] = 10 * u
+        y = (x.astype(np.float64) + delta).astype(np.float32)
+        flag, d, _, _ = oracle.mp_dist_paper(x, y, 5.0, fmt, c_A=2.0)
+        assert flag
+        ex = _exact_dist(x, y)
+        assert abs(Fraction(d) - ex) <= Fraction(oracle.gamma(r + 2, 2.0 ** -53)) * ex
+        # quantisation destroys the true difference (Eq. (quantis-necess-cond) fails)
+        xq, yq = oracle.quantize(x, fmt), oracle.quantize(y, fmt)
+        assert abs(float(_exact_dist(xq, yq)) - float(ex)) >= 0.5 * float(ex)
+    x = np.zeros(8, np.float32); x[0] = 1.0
+    y = x.copy(); y[1] = np.float32(10 * u)
+    flag, d, _, _ = oracle.mp_dist_paper(x, y, 5.0, fmt)
+    assert flag and d == (10 * u) ** 2
+
+
+def test_alg2_unflagged_relative_error_bound():
+    # Eq. (quantis-rel-bound-expand): unflagged => rel. err <= 2/(rho~ - 2)
+    rng = np.random.default_rng(10)
+    rho = 5.0
+    seen = 0
+    for r in (4, 8, 16):
+        for _ in range(300):
+            x = rng.normal(size=r).astype(np.float32)
+            y = (x * rng.uniform(-1, 1) + rng.normal(size=r) * 10.0 ** rng.uniform(-3, 0)).astype(np.float32)
+            flag, d, dh, E = oracle.mp_dist_paper(x, y, rho, 0, c_A=2.0)
+            ex = float(_exact_dist(x, y))
+            if not flag:
+                seen += 1
+                assert abs(d - ex) / ex <= 2.0 / (rho - 2.0)
+                assert d == dh
+            else:
+                assert abs(d - ex) <= oracle.gamma(r + 2, 2.0 ** -53) * ex
+    assert seen > 100
+
+
+# --- tensor-core instantiation of the test ----------------------------------
+def _tc_model_dhat(xq, cq, p, q, truncate=False):
+    """d^ under a model of the hardware: exact products, fp32 accumulation in
+    order (round-to-nearest, or toward zero), e = fl32(q - 2 g), d^ = fl32(p + e)."""
+    acc = np.float32(0.0)
+    for a, b in zip(xq.astype(np.float64), cq.astype(np.float64)):
+        s = float(acc) + a * b
+        if truncate:
+            f = np.float32(s)
+            if abs(float(f)) > abs(s):
+                f = np.nextafter(f, np.float32(0.0))
+            acc = f
+        else:
+            acc = np.float32(s)
+    e = np.float32(float(np.float32(q)) - 2.0 * float(acc))
+    return float(np.float32(float(np.float32(p)) + float(e)))
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_tc_bound_holds_under_hardware_models(fmt):
+    rng = np.random.default_rng(12)
+    d = 64 if fmt == 2 else 128
+    cases = []
+    X = rng.random((20, d)).astype(np.float32)
+    cases.append((X, X[::-1].copy()))
+    Xc, Cc = workloads.cancellation(20, d, 10, seed=3)
+    cases.append((Xc, Cc))
+    Xg, Cg = workloads.gaussian_mixture(20, d, 10, seed=4)
+    cases.append((Xg, Cg))
+    for X, C in cases:
+        Xq, p, nx, nxq, nrx, _ = oracle.row_quant_stats(X, fmt, per_row_scale=(fmt == 2))
+        Cq, q, nc, ncq, nrc, _ = oracle.row_quant_stats(C, fmt, per_row_scale=(fmt == 2))
+        B = oracle.tc_bound_matrix(X, C, fmt, per_row_scale=(fmt == 2))
+        for i in range(len(X)):
+            for j in range(len(C)):
+                ex = float(_exact_dist(X[i], C[j]))
+                for trunc in (False, True):
+                    dh = _tc_model_dhat(Xq[i], Cq[j], p[i], q[j], truncate=trunc)
+                    assert abs(dh - ex) <= B[i, j], (i, j, dh, ex, B[i, j])
+                # the C entry point evaluates the same formula
+                bc = oracle.tc_bound(nrx[i], nc[j], nxq[i], nrc[j], ncq[j], p[i], q[j], d, fmt)
+                assert bc == pytest.approx(B[i, j], rel=1e-14)
+
+
+def test_tc_bound_scale_and_unflagged_rel_error():
+    # B is of the order of the quantisation error (not vacuous), and unflagged
+    # pairs have relative error <= 1/(rho - 1) (Eq. (expanded-rel-bound))
+    rng = np.random.default_rng(13)
+    X = rng.random((30, 128)).astype(np.float32)
+    C = rng.random((30, 128)).astype(np.float32)
+    B = oracle.tc_bound_matrix(X, C, 1)
+    nx = np.linalg.norm(X.astype(np.float64), axis=1)
+    nc = np.linalg.norm(C.astype(np.float64), axis=1)
+    assert np.all(B <= 4.5 * 2.0 ** -8 * np.outer(nx, nc))
+    assert np.all(B >= 0.5 * 2.0 ** -8 * np.outer(nx, nc) / np.sqrt(3) * 0.5)
+    Xq, p, *_ = oracle.row_quant_stats(X, 1)
+    Cq, q, *_ = oracle.row_quant_stats(C, 1)
+    D = oracle.dist_direct(X, C)
+    rho = 5.0
+    for i in range(30):
+        for j in range(30):
+            dh = _tc_model_dhat(Xq[i], Cq[j], p[i], q[j])
+            if dh > rho * B[i, j]:
+                assert abs(dh - D[i, j]) / D[i, j] <= 1.0 / (rho - 1.0)
+
+
+def test_predict_flags_consistent():
+    X, C = workloads.cancellation(50, 128, 20, seed=5)
+    sure, maybe = oracle.predict_tc_flags(X, C, 1, 5.0)
+    assert sure.all()  # cancellation data: every pair flagged for certain
+    X, C = workloads.uniform_pairs(200, 128, 32, seed=6)
+    sure, maybe = oracle.predict_tc_flags(X, C, 1, 5.0)
+    # far data: only the 32 rows that are centres (d = 0) are flagged
+    D = oracle.dist_direct(X, C)
+    assert (sure == (D == 0)).all()
+    sure, maybe = oracle.predict_tc_flags(X, C, 1, 5.0, test="paper", c_A=1.0)
+    assert sure.all()  # Alg. 2 with bf16 at r = 128: 100% fallback (Table 6.1)
