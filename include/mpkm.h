@@ -1,0 +1,202 @@
+/*
+ * mpkm.h -- C-ABI of libmpkm: mixed-precision Lloyd's k-means on GB300.
+ *
+ * Method: E. Carson, X. Chen, X. Liu, "Computing k-means in Mixed Precision"
+ * (arXiv 2407.12208).  Distances are formed by the expanded formula
+ * Eq. (dist-expanded) with the cross term on tensor cores in a low format,
+ * screened by the reliability test of Section 4.3 (Alg. 2), and the pairs
+ * that fail it (or that could still be a row's nearest centre) are
+ * recomputed by the direct formula Eq. (dist-direct) from the original fp32
+ * data.  The centre update is Eq. (center); Lloyd's loop is Alg. 1 / Alg. 3.
+ *
+ * Conventions for every entry point:
+ *  - X is n x d, C is k x d, both row-major fp32 (points as rows, the layout
+ *    of Eq. (dist-blas3)).  Unless stated otherwise every array argument is a
+ *    DEVICE pointer owned by the caller; the library never frees it.
+ *  - The library allocates no device memory on the synchronous paths: the
+ *    caller passes a workspace `ws` of at least km_workspace_size() bytes
+ *    (256-byte aligned).  The serving calls draw from the arena given to
+ *    km_init().
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    ordered on it; outputs whose name ends in `_host` are host pointers and
+ *    imply a synchronisation of `stream` before the call returns.
+ *  - Every call returns a km_status; no exception crosses the ABI.  On
+ *    failure km_last_error() returns a message.  Argument errors are found
+ *    before any launch.  A device-side wait that runs out of its iteration
+ *    budget makes the kernel stop and the next synchronising call return
+ *    KM_ETIMEOUT.
+ *  - There is no CPU fallback: an unsupported combination returns
+ *    KM_EUNSUPPORTED.
+ */
+#ifndef MPKM_H
+#define MPKM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct km_ctx km_ctx;
+
+typedef enum {
+    KM_OK = 0,
+    KM_EINVAL = 1,        /* bad argument (null pointer, n<1, d<1, k<1, k>n, rho out of range) */
+    KM_ENOMEM = 2,        /* workspace / arena too small; a job that can never be admitted */
+    KM_ECUDA = 3,         /* a CUDA runtime or driver call failed */
+    KM_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+    KM_ENOTREADY = 5,     /* km_poll: job still running */
+    KM_ECANCELLED = 6,    /* km_poll: job was cancelled */
+    KM_EUNSUPPORTED = 7   /* combination not implemented (e.g. E4M3 with d < 16) */
+} km_status;
+
+/* Low precision u_l of the cross term (Section 4.3).  The two *_DIRECT modes
+ * skip the expanded formula and evaluate Eq. (dist-direct) on CUDA cores. */
+typedef enum {
+    KM_FP64_DIRECT = 0,   /* the plain FP64 path: Eq. (dist-direct) in binary64 */
+    KM_FP32_DIRECT = 1,   /* Eq. (dist-direct) in fp32, certified, fp64 where ambiguous */
+    KM_FP16 = 2,          /* binary16 cross term (Table 1.1), FP32 accumulation */
+    KM_BF16 = 3,          /* bfloat16 cross term (Table 1.1), FP32 accumulation */
+    KM_E4M3 = 4           /* FP8 E4M3 cross term with power-of-two per-row scales */
+} km_low;
+
+/* Reliability test of Section 4.3. */
+typedef enum {
+    KM_TEST_TC = 0,       /* Theorem 4.2 + Eq. (quantis-convert-error) instantiated for
+                             tensor-core arithmetic: flag iff d^ <= rho * B(x, c) */
+    KM_TEST_PAPER = 1,    /* Alg. 2: flag iff d^ <= rho * c_A * gamma^l_{r+2} (||x~||^2 + ||c~||^2) */
+    KM_TEST_OFF = 2       /* no flags (uniform low precision); argmin still certified */
+} km_test;
+
+typedef enum {
+    KM_EMPTY_KEEP = 0,     /* an empty cluster keeps its previous centre */
+    KM_EMPTY_FARTHEST = 1  /* empty clusters (ascending j) take the points with the largest
+                              current min_dist, ties to the lowest index, each point once */
+} km_empty;
+
+typedef struct {
+    int32_t low;          /* km_low */
+    int32_t test;         /* km_test */
+    double rho;           /* safety factor, > 1 for KM_TEST_TC, > 2 for KM_TEST_PAPER (Eq. (quantis-reliability-test)); default 5 */
+    double paper_factor;  /* c_A in {1, 2}: 1 = Alg. 2 as printed, 2 = E^l of Section 4.3 (default 2) */
+    int32_t max_iter;     /* Lloyd iterations t_max (Alg. 1) */
+    int32_t empty;        /* km_empty */
+    double tau;           /* stop when max_j ||c_j^(t) - c_j^(t-1)|| < tau; tau <= 0 runs max_iter iterations */
+} km_params;
+
+/* Counters of the last assign / distances / lloyd call on a context. */
+typedef struct {
+    uint64_t pairs;           /* point-centre pairs screened (n*k per assignment) */
+    uint64_t flagged;         /* pairs failing the reliability test: eta = flagged / pairs (Eq. (eta)) */
+    uint64_t fp32_evals;      /* direct-formula evaluations in fp32 (certification of the argmin) */
+    uint64_t fp64_evals;      /* direct-formula evaluations in binary64 */
+    uint64_t ambiguous_rows;  /* rows whose low-precision argmin could not be certified */
+    uint64_t overflow_rows;   /* rows whose candidate list overflowed (re-scanned over all centres) */
+    double sse;               /* sum of min_dist of the last assignment (Eq. (sse)) */
+} km_stats;
+
+/* Fills the defaults: BF16, KM_TEST_TC, rho 5, c_A 2, max_iter 20, tau 0, FARTHEST. */
+void km_default_params(km_params* p);
+
+/* Creates a context on `device`.  `arena` (device memory, caller-owned, may
+ * be NULL with arena_bytes 0) backs the serving calls only; it must stay
+ * valid until km_destroy. */
+km_status km_init(km_ctx** out, int device, void* arena, size_t arena_bytes);
+km_status km_destroy(km_ctx* ctx);
+const char* km_last_error(const km_ctx* ctx);
+
+/* Bytes of workspace the synchronous calls need for these sizes. */
+km_status km_workspace_size(const km_ctx* ctx, int64_t n, int d, int k, const km_params* p,
+                            size_t* bytes);
+
+/* Alg. 2 for all pairs (Section 4.3; the distance-matrix experiments of
+ * Section 6.1).  D (n x k fp32, row-major) receives, per pair, the expanded
+ * low-precision value where the reliability test passes and the binary64
+ * direct value (rounded to fp32, the working precision) where it fails.
+ * flag_bits (nullable; ceil(n*k/32) words, bit (i*k+j) of the row-major
+ * pair index) marks the pairs that fell back.  n_flagged_host (nullable,
+ * host) receives the number of flagged pairs.  low must be FP16/BF16/E4M3. */
+km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
+                       const km_params* p, float* D, uint32_t* flag_bits,
+                       uint64_t* n_flagged_host, void* ws, size_t ws_bytes, void* stream);
+
+/* Assignment step of Alg. 3: labels[i] = argmin_j d(x_i, c_j)^2 (lowest j on
+ * ties).  The argmin is certified: it equals the binary64 direct-formula
+ * argmin wherever that row's best/second-best gap exceeds the proved error
+ * bounds (in practice: relative gaps above ~1e-7).  min_dist (nullable,
+ * n doubles) receives ||x_i - c_label||^2 by the direct formula: binary64
+ * where it was recomputed in binary64, else fp32 with relative error
+ * <= gamma_{d+2}(2^-24) (Theorem 4.1).  n_flagged_host (nullable, host):
+ * number of pairs that failed the reliability test. */
+km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
+                    const km_params* p, int32_t* labels, double* min_dist,
+                    uint64_t* n_flagged_host, void* ws, size_t ws_bytes, void* stream);
+
+/* Centre update, Eq. (center), in precision higher than the working one
+ * (Section 4.4): per-cluster sums are formed exactly in 64-bit fixed point
+ * (order-independent, hence deterministic), divided in binary64 and stored
+ * in fp32.  counts (k int64), C_new (k x d fp32).  min_dist (nullable, n
+ * doubles) is needed only for KM_EMPTY_FARTHEST.  shift_host (nullable,
+ * host): max_j ||c_new_j - c_old_j||. */
+km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d,
+                              const int32_t* labels, int k, const float* C_old,
+                              const km_params* p, const double* min_dist, float* C_new,
+                              int64_t* counts, double* shift_host, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Alg. 3: Lloyd's loop with the mixed-precision assignment.  C_out (k x d)
+ * receives the final centres, labels (n) the final reassignment.
+ * sse_per_iter and eta_per_iter (nullable, host, max_iter + 1 doubles):
+ * SSE and flagged fraction of every assignment, the last one being the
+ * final reassignment.  iters_done (nullable, host). */
+km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
+                       const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
+                       double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/* Counters of the last assign / distances / lloyd call (synchronises that
+ * call's stream).  Returns KM_ETIMEOUT if a device-side wait ran out. */
+km_status km_get_stats(km_ctx* ctx, km_stats* out);
+
+/* ---- serving (continuous batching on one GPU) ---------------------------- */
+
+/* A job: X (n x d) and C_init (k x d) are HOST pointers, copied into the
+ * arena at admission.  kind 0 = Lloyd (Alg. 3, p.max_iter iterations),
+ * kind 1 = one nearest-centre assignment against C_init. */
+typedef struct {
+    const float* X;
+    int64_t n;
+    int32_t d;
+    int32_t k;
+    const float* C_init;
+    km_params p;
+    int32_t kind;
+} km_job;
+
+typedef struct {
+    km_status status;     /* KM_OK when finished */
+    int32_t iters;
+    double sse;
+    double eta;           /* flagged fraction over all assignments of the job */
+    double latency_ms;    /* submit -> completion */
+    double queue_ms;      /* submit -> admission */
+    const float* C;       /* device pointer into the arena (k x d), valid until km_release */
+    const int32_t* labels;/* device pointer into the arena (n), valid until km_release */
+} km_result;
+
+/* Queues a job; it is admitted when its memory fits in the arena.  The host
+ * arrays are copied before the call returns.  KM_ENOMEM if the job could
+ * never fit in the arena. */
+km_status km_submit(km_ctx* ctx, const km_job* job, uint64_t* job_id);
+/* KM_ENOTREADY until the job is done; then fills *out. */
+km_status km_poll(km_ctx* ctx, uint64_t job_id, km_result* out);
+/* Frees a finished job's arena memory (its result pointers become invalid). */
+km_status km_release(km_ctx* ctx, uint64_t job_id);
+/* Cancels a queued or running job (a running job stops between iterations). */
+km_status km_cancel(km_ctx* ctx, uint64_t job_id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPKM_H */

@@ -1,0 +1,288 @@
+"""ctypes binding of libmpkm (include/mpkm.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch
+provides device memory (tensors whose data_ptr() is passed) and streams.
+There is no fallback: if the library is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpkm.so")
+
+KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ENOTREADY, KM_ECANCELLED, KM_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["KM_OK", "KM_EINVAL", "KM_ENOMEM", "KM_ECUDA", "KM_ETIMEOUT", "KM_ENOTREADY",
+                "KM_ECANCELLED", "KM_EUNSUPPORTED"]
+FP64_DIRECT, FP32_DIRECT, FP16, BF16, E4M3 = range(5)
+TEST_TC, TEST_PAPER, TEST_OFF = range(3)
+EMPTY_KEEP, EMPTY_FARTHEST = range(2)
+LOW_NAMES = {"fp64": FP64_DIRECT, "fp32": FP32_DIRECT, "fp16": FP16, "bf16": BF16, "e4m3": E4M3}
+TEST_NAMES = {"tc": TEST_TC, "paper": TEST_PAPER, "off": TEST_OFF}
+
+# Symbols declared in include/mpkm.h
+EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_workspace_size",
+           "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
+           "km_submit", "km_poll", "km_release", "km_cancel"]
+
+
+class KmError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("low", ctypes.c_int32), ("test", ctypes.c_int32), ("rho", ctypes.c_double),
+                ("paper_factor", ctypes.c_double), ("max_iter", ctypes.c_int32), ("empty", ctypes.c_int32),
+                ("tau", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("flagged", ctypes.c_uint64), ("fp32_evals", ctypes.c_uint64),
+                ("fp64_evals", ctypes.c_uint64), ("ambiguous_rows", ctypes.c_uint64),
+                ("overflow_rows", ctypes.c_uint64), ("sse", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("C_init", ctypes.c_void_p), ("p", Params), ("kind", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("sse", ctypes.c_double),
+                ("eta", ctypes.c_double), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("C", ctypes.c_void_p), ("labels", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Loads libmpkm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libmpkm.so is not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        c = ctypes
+        vp, i64, i32, sz = c.c_void_p, c.c_int64, c.c_int, c.c_size_t
+        P = c.POINTER(Params)
+        lib.km_default_params.argtypes = [P]
+        lib.km_default_params.restype = None
+        lib.km_init.argtypes = [c.POINTER(vp), i32, vp, sz]
+        lib.km_destroy.argtypes = [vp]
+        lib.km_last_error.argtypes = [vp]
+        lib.km_last_error.restype = c.c_char_p
+        lib.km_workspace_size.argtypes = [vp, i64, i32, i32, P, c.POINTER(sz)]
+        lib.km_distances.argtypes = [vp, vp, i64, vp, i32, i32, P, vp, vp, c.POINTER(c.c_uint64), vp, sz, vp]
+        lib.km_assign.argtypes = [vp, vp, i64, vp, i32, i32, P, vp, vp, c.POINTER(c.c_uint64), vp, sz, vp]
+        lib.km_update_centroids.argtypes = [vp, vp, i64, i32, vp, i32, vp, P, vp, vp, vp, c.POINTER(c.c_double),
+                                            vp, sz, vp]
+        lib.km_lloyd_run.argtypes = [vp, vp, i64, i32, i32, vp, P, vp, vp, vp, vp, c.POINTER(c.c_int), vp, sz, vp]
+        lib.km_get_stats.argtypes = [vp, c.POINTER(Stats)]
+        lib.km_submit.argtypes = [vp, c.POINTER(Job), c.POINTER(c.c_uint64)]
+        lib.km_poll.argtypes = [vp, c.c_uint64, c.POINTER(Result)]
+        lib.km_release.argtypes = [vp, c.c_uint64]
+        lib.km_cancel.argtypes = [vp, c.c_uint64]
+        for f in EXPORTS:
+            fn = getattr(lib, f)
+            if f not in ("km_default_params", "km_last_error"):
+                fn.restype = c.c_int
+        _lib = lib
+        return lib
+
+
+def params(low="bf16", test="tc", rho=5.0, paper_factor=2.0, max_iter=20, empty="farthest", tau=0.0) -> Params:
+    p = Params()
+    load().km_default_params(ctypes.byref(p))
+    p.low = LOW_NAMES[low] if isinstance(low, str) else int(low)
+    p.test = TEST_NAMES[test] if isinstance(test, str) else int(test)
+    p.rho = float(rho)
+    p.paper_factor = float(paper_factor)
+    p.max_iter = int(max_iter)
+    p.empty = {"keep": EMPTY_KEEP, "farthest": EMPTY_FARTHEST}[empty] if isinstance(empty, str) else int(empty)
+    p.tau = float(tau)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A libmpkm context on one GPU; optional serving arena (a torch tensor)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 0):
+        import torch
+        self.lib = load()
+        self.device = device
+        self._arena = None
+        h = ctypes.c_void_p()
+        arena_ptr, nbytes = None, 0
+        if arena_bytes:
+            self._arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda:%d" % device)
+            arena_ptr, nbytes = ctypes.c_void_p(self._arena.data_ptr()), int(arena_bytes)
+        rc = self.lib.km_init(ctypes.byref(h), device, arena_ptr, nbytes)
+        if rc != KM_OK:
+            raise KmError(rc, "km_init failed")
+        self.h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.km_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != KM_OK:
+            raise KmError(rc, self.lib.km_last_error(self.h).decode())
+
+    def workspace_size(self, n, d, k, p: Params) -> int:
+        b = ctypes.c_size_t()
+        self._check(self.lib.km_workspace_size(self.h, int(n), int(d), int(k), ctypes.byref(p), ctypes.byref(b)))
+        return b.value
+
+    def workspace(self, n, d, k, p: Params):
+        """A cached device workspace large enough for (n, d, k, p)."""
+        import torch
+        need = self.workspace_size(n, d, k, p)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda:%d" % self.device)
+        return self._ws
+
+    def assign(self, X, C, p: Params, labels=None, min_dist=None, ws=None, stream=None, want_flagged=True):
+        import torch
+        n, d = X.shape
+        k = C.shape[0]
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32, device=X.device)
+        if min_dist is None:
+            min_dist = torch.empty(n, dtype=torch.float64, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p)
+        nf = ctypes.c_uint64(0)
+        self._check(self.lib.km_assign(self.h, _ptr(X), n, _ptr(C), k, d, ctypes.byref(p), _ptr(labels),
+                                       _ptr(min_dist), ctypes.byref(nf) if want_flagged else None, _ptr(ws),
+                                       ws.numel(), _stream(stream)))
+        return labels, min_dist, (nf.value if want_flagged else None)
+
+    def distances(self, X, C, p: Params, D=None, flag_bits=None, ws=None, stream=None):
+        import torch
+        n, d = X.shape
+        k = C.shape[0]
+        if D is None:
+            D = torch.empty((n, k), dtype=torch.float32, device=X.device)
+        if flag_bits is None:
+            flag_bits = torch.empty((n * k + 31) // 32, dtype=torch.int32, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p)
+        nf = ctypes.c_uint64(0)
+        self._check(self.lib.km_distances(self.h, _ptr(X), n, _ptr(C), k, d, ctypes.byref(p), _ptr(D),
+                                          _ptr(flag_bits), ctypes.byref(nf), _ptr(ws), ws.numel(),
+                                          _stream(stream)))
+        return D, flag_bits, nf.value
+
+    def update_centroids(self, X, labels, C_old, p: Params, min_dist=None, C_new=None, counts=None, ws=None,
+                         stream=None):
+        import torch
+        n, d = X.shape
+        k = C_old.shape[0]
+        if C_new is None:
+            C_new = torch.empty_like(C_old)
+        if counts is None:
+            counts = torch.empty(k, dtype=torch.int64, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p)
+        sh = ctypes.c_double(0.0)
+        self._check(self.lib.km_update_centroids(self.h, _ptr(X), n, d, _ptr(labels), k, _ptr(C_old),
+                                                 ctypes.byref(p), _ptr(min_dist), _ptr(C_new), _ptr(counts),
+                                                 ctypes.byref(sh), _ptr(ws), ws.numel(), _stream(stream)))
+        return C_new, counts, sh.value
+
+    def lloyd_run(self, X, C_init, p: Params, C_out=None, labels=None, ws=None, stream=None):
+        import numpy as np
+        import torch
+        n, d = X.shape
+        k = C_init.shape[0]
+        if C_out is None:
+            C_out = torch.empty_like(C_init)
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p)
+        sse = np.zeros(p.max_iter + 1, dtype=np.float64)
+        eta = np.zeros(p.max_iter + 1, dtype=np.float64)
+        it = ctypes.c_int(0)
+        self._check(self.lib.km_lloyd_run(self.h, _ptr(X), n, d, k, _ptr(C_init), ctypes.byref(p), _ptr(C_out),
+                                          _ptr(labels), sse.ctypes.data_as(ctypes.c_void_p),
+                                          eta.ctypes.data_as(ctypes.c_void_p), ctypes.byref(it), _ptr(ws),
+                                          ws.numel(), _stream(stream)))
+        t = it.value
+        return C_out, labels, sse[: t + 1], eta[: t + 1], t
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.lib.km_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    # ---- serving
+    def submit(self, X, C_init, p: Params, kind: int = 0) -> int:
+        """X, C_init: C-contiguous float32 numpy arrays (host); copied before return."""
+        import numpy as np
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        C = np.ascontiguousarray(C_init, dtype=np.float32)
+        j = Job()
+        j.X = X.ctypes.data_as(ctypes.c_void_p)
+        j.n, j.d = X.shape
+        j.k = C.shape[0]
+        j.C_init = C.ctypes.data_as(ctypes.c_void_p)
+        j.p = p
+        j.kind = int(kind)
+        jid = ctypes.c_uint64(0)
+        self._check(self.lib.km_submit(self.h, ctypes.byref(j), ctypes.byref(jid)))
+        return jid.value
+
+    def poll(self, job_id: int):
+        """None while running; else a dict (C / labels as device pointers)."""
+        r = Result()
+        rc = self.lib.km_poll(self.h, ctypes.c_uint64(job_id), ctypes.byref(r))
+        if rc == KM_ENOTREADY:
+            return None
+        return {"status": rc, "iters": r.iters, "sse": r.sse, "eta": r.eta, "latency_ms": r.latency_ms,
+                "queue_ms": r.queue_ms, "C": r.C, "labels": r.labels}
+
+    def release(self, job_id: int):
+        self._check(self.lib.km_release(self.h, ctypes.c_uint64(job_id)))
+
+    def cancel(self, job_id: int):
+        self._check(self.lib.km_cancel(self.h, ctypes.c_uint64(job_id)))
+
+
+def device_array(ptr: int, shape, dtype_str: str, device: int = 0):
+    """A torch tensor viewing library-owned device memory (serving results)."""
+    import torch
+
+    class _CAI:
+        def __init__(self):
+            self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": dtype_str, "data": (ptr, False),
+                                             "version": 3, "strides": None}
+
+    return torch.as_tensor(_CAI(), device="cuda:%d" % device)

@@ -1,0 +1,623 @@
+// api.cu -- the C-ABI of libmpkm (include/mpkm.h): argument checks, the
+// workspace layout, and the launch sequences of the hot path:
+//   assign  = quantise X and C (+ statistics) -> tensor-core screening with
+//             the fused reliability test and candidate collection ->
+//             refinement by the direct formula (fp32, then binary64 where the
+//             argmin is still open) -> full-row direct pass for overflowed rows
+//   update  = exact fixed-point centroid sums -> means, empty clusters, shift
+//   lloyd   = Alg. 3 on top of the two.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <vector>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/mpkm.h"
+#include "common.cuh"
+#include "internal.h"
+#include "serve.h"
+
+using namespace km;
+
+struct km_ctx {
+    int device = 0;
+    int num_sms = 148;
+    std::string err;
+    // last call, for km_get_stats
+    DevCounters* last_cnt = nullptr;
+    double* last_sse = nullptr;
+    cudaStream_t last_stream = nullptr;
+    uint64_t last_pairs = 0;
+    km_serve* serve = nullptr;
+};
+
+namespace {
+
+constexpr int kCandSlots = 16;
+constexpr int kSumParts = 256;
+
+km_status fail(km_ctx* c, km_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(expr)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (expr);                                                                     \
+        if (e_ != cudaSuccess) return fail(ctx, KM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+int fmt_of(int low) { return low == KM_FP16 ? 0 : (low == KM_BF16 ? 1 : 2); }
+bool is_tc(int low) { return low == KM_FP16 || low == KM_BF16 || low == KM_E4M3; }
+double unit_roundoff(int fmt) { return fmt == 0 ? std::ldexp(1.0, -11) : (fmt == 1 ? std::ldexp(1.0, -8) : std::ldexp(1.0, -4)); }
+double gamma_m(int m, double u) {
+    double mu = m * u;
+    return mu >= 1.0 ? INFINITY : mu / (1.0 - mu);
+}
+int ldq_of(int fmt, int d) { return fmt == 2 ? ((d + 15) / 16) * 16 : ((d + 7) / 8) * 8; }
+
+struct Carve {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Workspace of one assignment / distance computation.
+struct AssignWs {
+    DevCounters* cnt;
+    ColMax* colmax;
+    float* cscale_u;
+    void* Xq;
+    void* Cq;
+    float4* xstat;
+    float* xscale;
+    float4* cstat;
+    float* cscale;
+    int2* cand;
+    int4* rowinfo;
+    int32_t* ovf_list;
+    int32_t* amb_list;
+    double* partials;
+    double* sse;
+    int2* queue;
+    unsigned long long* qlen;
+};
+
+AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distances) {
+    AssignWs w{};
+    w.cnt = cv.take<DevCounters>(1);
+    w.colmax = cv.take<ColMax>(1);
+    w.cscale_u = cv.take<float>(1);
+    w.partials = cv.take<double>(kSumParts);
+    w.sse = cv.take<double>(1);
+    w.amb_list = cv.take<int32_t>((size_t)n);
+    if (is_tc(low)) {
+        const int fmt = fmt_of(low);
+        const int esz = fmt == 2 ? 1 : 2;
+        const int ldq = ldq_of(fmt, d);
+        w.Xq = cv.take<char>((size_t)n * ldq * esz);
+        w.Cq = cv.take<char>((size_t)k * ldq * esz);
+        w.xstat = cv.take<float4>((size_t)n);
+        w.xscale = cv.take<float>((size_t)n);
+        w.cstat = cv.take<float4>((size_t)k);
+        w.cscale = cv.take<float>((size_t)k);
+        w.rowinfo = cv.take<int4>((size_t)n);
+        w.ovf_list = cv.take<int32_t>((size_t)n);
+        if (!distances) {
+            w.cand = cv.take<int2>((size_t)n * kCandSlots);
+        } else {
+            w.queue = cv.take<int2>((size_t)n * k);
+            w.qlen = cv.take<unsigned long long>(1);
+        }
+    }
+    return w;
+}
+
+struct UpdateWs {
+    long long* sums;
+    long long* counts;
+    unsigned* absmax;
+    double* shift;
+    int32_t* taken;
+};
+UpdateWs carve_update(Carve& cv, int d, int k) {
+    UpdateWs u{};
+    u.sums = cv.take<long long>((size_t)k * d);
+    u.counts = cv.take<long long>((size_t)k);
+    u.absmax = cv.take<unsigned>(1);
+    u.shift = cv.take<double>(1);
+    u.taken = cv.take<int32_t>((size_t)k);
+    return u;
+}
+
+struct LloydWs {
+    AssignWs a;
+    UpdateWs u;
+    float* C0;
+    float* C1;
+    double* min_dist;
+    double* sse_hist;
+    unsigned long long* flag_hist;
+    int64_t* counts;
+};
+LloydWs carve_lloyd(Carve& cv, int64_t n, int d, int k, int low, int max_iter) {
+    LloydWs L{};
+    L.a = carve_assign(cv, n, d, k, low, false);
+    L.u = carve_update(cv, d, k);
+    L.C0 = cv.take<float>((size_t)k * d);
+    L.C1 = cv.take<float>((size_t)k * d);
+    L.min_dist = cv.take<double>((size_t)n);
+    L.sse_hist = cv.take<double>((size_t)max_iter + 1);
+    L.flag_hist = cv.take<unsigned long long>((size_t)max_iter + 1);
+    L.counts = cv.take<int64_t>((size_t)k);
+    return L;
+}
+
+km_status check_params(km_ctx* ctx, const km_params* p, int d) {
+    if (!p) return fail(ctx, KM_EINVAL, "params is NULL");
+    if (p->low < KM_FP64_DIRECT || p->low > KM_E4M3) return fail(ctx, KM_EINVAL, "unknown low precision %d", p->low);
+    if (p->test < KM_TEST_TC || p->test > KM_TEST_OFF) return fail(ctx, KM_EINVAL, "unknown test %d", p->test);
+    if (p->empty != KM_EMPTY_KEEP && p->empty != KM_EMPTY_FARTHEST) return fail(ctx, KM_EINVAL, "unknown empty policy");
+    if (is_tc(p->low)) {
+        if (p->test == KM_TEST_TC && !(p->rho > 1.0)) return fail(ctx, KM_EINVAL, "rho must exceed 1 for the tc test");
+        if (p->test == KM_TEST_PAPER) {
+            if (!(p->rho > 2.0)) return fail(ctx, KM_EINVAL, "rho must exceed 2 for the paper test (Eq. (quantis-reliability-test))");
+            if (!(p->paper_factor > 0.0)) return fail(ctx, KM_EINVAL, "paper_factor must be positive");
+            if ((d + 2) * unit_roundoff(fmt_of(p->low)) >= 1.0)
+                return fail(ctx, KM_EUNSUPPORTED, "gamma^l_{d+2} undefined: (d+2) u_l >= 1 for d=%d", d);
+        }
+        if (p->low == KM_E4M3 && d < 16) return fail(ctx, KM_EUNSUPPORTED, "E4M3 needs d >= 16");
+        if (tc_smem_bytes(fmt_of(p->low), d, 1) == 0) return fail(ctx, KM_EUNSUPPORTED, "d=%d too large for the tensor-core tiles", d);
+    } else {
+        if (d > 256) return fail(ctx, KM_EUNSUPPORTED, "direct paths support d <= 256");
+    }
+    return KM_OK;
+}
+
+TestParams make_tp(const km_params* p, int d) {
+    TestParams tp{};
+    const double u32 = std::ldexp(1.0, -24);
+    const int fmt = is_tc(p->low) ? fmt_of(p->low) : 1;
+    const double uacc = fmt == 2 ? std::ldexp(1.0, -13) : std::ldexp(1.0, -21);
+    tp.test = p->test;
+    tp.rho = (float)p->rho;
+    tp.kacc = (float)((2.0 * gamma_m(d, uacc) + 4.0 * u32) * (1.0 + 1e-6));
+    tp.kn = (float)(4.0 * u32);
+    tp.paper_coef = is_tc(p->low) ? (float)(p->rho * p->paper_factor * gamma_m(d + 2, unit_roundoff(fmt))) : 0.0f;
+    tp.bsafe = (float)(1.0 + std::ldexp(1.0, -10));
+    tp.gamma32 = (float)(gamma_m(d + 2, u32) * 1.01 + std::ldexp(1.0, -22));
+    return tp;
+}
+
+bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
+
+// One assignment of X against C into labels/min_dist (all device).
+km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
+                     int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st) {
+    const TestParams tp = make_tp(p, d);
+    if (p->low == KM_FP64_DIRECT || p->low == KM_FP32_DIRECT) {
+        const bool acc64 = p->low == KM_FP64_DIRECT;
+        CK(launch_direct_assign(acc64, X, n, C, k, d, nullptr, nullptr, labels, min_dist, w.amb_list, w.cnt,
+                                tp.gamma32, ctx->num_sms, st));
+        if (!acc64)
+            CK(launch_rows_fp64(X, C, k, d, w.amb_list, &w.cnt->amb_count, n, labels, min_dist, w.cnt, ctx->num_sms, st));
+        return KM_OK;
+    }
+    const int fmt = fmt_of(p->low);
+    const int ldq = ldq_of(fmt, d);
+    const int esz = fmt == 2 ? 1 : 2;
+    if (!x_prepared)
+        CK(launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
+    if (fmt == 2) {
+        CK(launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
+        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
+        CK(launch_colmax(w.cstat, k, w.cscale_u, w.colmax, st));
+    } else {
+        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
+        CK(launch_colmax(w.cstat, k, nullptr, w.colmax, st));
+    }
+    TcArgs a{};
+    a.n = n; a.k = k; a.d = d; a.fmt = fmt;
+    a.kchunks = (ldq * esz + 127) / 128;
+    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.colmax = w.colmax;
+    a.tp = tp; a.mode = 0; a.L = kCandSlots; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    CK(launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
+    CK(launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st));
+    // rows whose candidate list overflowed: full-row fp32 direct, then binary64 where uncertified
+    CK(launch_direct_assign(false, X, n, C, k, d, w.ovf_list, &w.cnt->ovf_count, labels, min_dist, w.amb_list,
+                            w.cnt, tp.gamma32, ctx->num_sms, st));
+    CK(launch_rows_fp64(X, C, k, d, w.amb_list, &w.cnt->amb_count, n, labels, min_dist, w.cnt, ctx->num_sms, st));
+    (void)esz;
+    return KM_OK;
+}
+
+km_status sync_status(km_ctx* ctx, DevCounters* cnt, cudaStream_t st) {
+    CK(cudaStreamSynchronize(st));
+    unsigned status = 0;
+    CK(cudaMemcpy(&status, &cnt->status, sizeof status, cudaMemcpyDeviceToHost));
+    if (status & KM_DEVERR_TIMEOUT) return fail(ctx, KM_ETIMEOUT, "a device-side wait ran out of its budget");
+    if (status) return fail(ctx, KM_ECUDA, "device status word 0x%x", status);
+    return KM_OK;
+}
+
+km_status check_common(km_ctx* ctx, const void* X, int64_t n, const void* C, int k, int d) {
+    if (!ctx) return KM_EINVAL;
+    if (!X || !C) return fail(ctx, KM_EINVAL, "null input pointer");
+    if (n < 1 || d < 1 || k < 1) return fail(ctx, KM_EINVAL, "need n, d, k >= 1 (n=%lld d=%d k=%d)", (long long)n, d, k);
+    if ((int64_t)k > n) return fail(ctx, KM_EINVAL, "k=%d exceeds n=%lld", k, (long long)n);
+    if (n > (int64_t)INT32_MAX) return fail(ctx, KM_EINVAL, "n too large");
+    return KM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void km_default_params(km_params* p) {
+    if (!p) return;
+    p->low = KM_BF16;
+    p->test = KM_TEST_TC;
+    p->rho = 5.0;
+    p->paper_factor = 2.0;
+    p->max_iter = 20;
+    p->empty = KM_EMPTY_FARTHEST;
+    p->tau = 0.0;
+}
+
+km_status km_init(km_ctx** out, int device, void* arena, size_t arena_bytes) {
+    if (!out) return KM_EINVAL;
+    *out = nullptr;
+    km_ctx* ctx = new km_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete ctx; return KM_ECUDA; }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) ctx->num_sms = sms;
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (major != 10) { delete ctx; return KM_EUNSUPPORTED; }
+    if (arena && arena_bytes) {
+        km_status s = serve_create(&ctx->serve, device, ctx->num_sms, arena, arena_bytes);
+        if (s != KM_OK) { delete ctx; return s; }
+    }
+    *out = ctx;
+    return KM_OK;
+}
+
+km_status km_destroy(km_ctx* ctx) {
+    if (!ctx) return KM_EINVAL;
+    if (ctx->serve) serve_destroy(ctx->serve);
+    delete ctx;
+    return KM_OK;
+}
+
+const char* km_last_error(const km_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+km_status km_workspace_size(const km_ctx* cctx, int64_t n, int d, int k, const km_params* p, size_t* bytes) {
+    km_ctx* ctx = const_cast<km_ctx*>(cctx);
+    if (!ctx || !bytes || !p) return KM_EINVAL;
+    if (n < 1 || d < 1 || k < 1) return fail(ctx, KM_EINVAL, "need n, d, k >= 1");
+    Carve a{nullptr};
+    carve_lloyd(a, n, d, k, p->low, std::max(0, (int)p->max_iter));
+    Carve b{nullptr};
+    carve_assign(b, n, d, k, p->low, true);
+    *bytes = std::max(a.off, b.off) + 256;
+    return KM_OK;
+}
+
+km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
+                    int32_t* labels, double* min_dist, uint64_t* n_flagged_host, void* ws, size_t ws_bytes,
+                    void* stream) {
+    km_status s = check_common(ctx, X, n, C, k, d);
+    if (s != KM_OK) return s;
+    if ((s = check_params(ctx, p, d)) != KM_OK) return s;
+    if (!labels || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    AssignWs w = carve_assign(cv, n, d, k, p->low, false);
+    double* md = min_dist;
+    Carve tmp{nullptr};
+    carve_assign(tmp, n, d, k, p->low, false);
+    size_t need = tmp.off;
+    if (!md) {  // scratch min_dist when the caller does not want it
+        Carve c2{(char*)ws};
+        c2.off = tmp.off;
+        md = c2.take<double>((size_t)n);
+        need = c2.off;
+    }
+    if (ws_bytes < need) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
+    s = run_assign(ctx, X, n, C, k, d, p, labels, md, w, false, st);
+    if (s != KM_OK) return s;
+    CK(launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
+    ctx->last_cnt = w.cnt;
+    ctx->last_sse = w.sse;
+    ctx->last_stream = st;
+    ctx->last_pairs = (uint64_t)n * (uint64_t)k;
+    if (n_flagged_host) {
+        if ((s = sync_status(ctx, w.cnt, st)) != KM_OK) return s;
+        unsigned long long f = 0;
+        CK(cudaMemcpy(&f, &w.cnt->flagged, sizeof f, cudaMemcpyDeviceToHost));
+        *n_flagged_host = f;
+    }
+    return KM_OK;
+}
+
+km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
+                       float* D, uint32_t* flag_bits, uint64_t* n_flagged_host, void* ws, size_t ws_bytes,
+                       void* stream) {
+    km_status s = check_common(ctx, X, n, C, k, d);
+    if (s != KM_OK) return s;
+    if ((s = check_params(ctx, p, d)) != KM_OK) return s;
+    if (!is_tc(p->low)) return fail(ctx, KM_EUNSUPPORTED, "km_distances needs a low format (FP16/BF16/E4M3)");
+    if (!D || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    AssignWs w = carve_assign(cv, n, d, k, p->low, true);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
+    CK(cudaMemsetAsync(w.qlen, 0, sizeof(unsigned long long), st));
+    if (flag_bits) CK(cudaMemsetAsync(flag_bits, 0, ((size_t)n * k + 31) / 32 * 4, st));
+    const int fmt = fmt_of(p->low);
+    const int ldq = ldq_of(fmt, d);
+    const int esz = fmt == 2 ? 1 : 2;
+    CK(launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
+    if (fmt == 2) {
+        CK(launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
+        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
+        CK(launch_colmax(w.cstat, k, w.cscale_u, w.colmax, st));
+    } else {
+        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
+        CK(launch_colmax(w.cstat, k, nullptr, w.colmax, st));
+    }
+    TcArgs a{};
+    a.n = n; a.k = k; a.d = d; a.fmt = fmt;
+    a.kchunks = (ldq * esz + 127) / 128;
+    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.colmax = w.colmax;
+    a.tp = make_tp(p, d); a.mode = 1; a.L = kCandSlots; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = n * (int64_t)k;
+    a.flag_queue_len = w.qlen;
+    CK(launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
+    CK(launch_patch_flagged(X, C, k, d, w.queue, w.qlen, n * (int64_t)k, D, w.cnt, ctx->num_sms, st));
+    ctx->last_cnt = w.cnt;
+    ctx->last_sse = nullptr;
+    ctx->last_stream = st;
+    ctx->last_pairs = (uint64_t)n * (uint64_t)k;
+    if (n_flagged_host) {
+        if ((s = sync_status(ctx, w.cnt, st)) != KM_OK) return s;
+        unsigned long long f = 0;
+        CK(cudaMemcpy(&f, &w.cnt->flagged, sizeof f, cudaMemcpyDeviceToHost));
+        *n_flagged_host = f;
+    }
+    return KM_OK;
+}
+
+km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, const int32_t* labels, int k,
+                              const float* C_old, const km_params* p, const double* min_dist, float* C_new,
+                              int64_t* counts, double* shift_host, void* ws, size_t ws_bytes, void* stream) {
+    km_status s = check_common(ctx, X, n, C_old, k, d);
+    if (s != KM_OK) return s;
+    if (!p || !labels || !C_new || !ws) return fail(ctx, KM_EINVAL, "null argument");
+    if (p->empty != KM_EMPTY_KEEP && p->empty != KM_EMPTY_FARTHEST) return fail(ctx, KM_EINVAL, "unknown empty policy");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    DevCounters* cnt = cv.take<DevCounters>(1);
+    UpdateWs u = carve_update(cv, d, k);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), st));
+    CK(launch_absmax(X, n * (int64_t)d, u.absmax, st));
+    CK(launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, ctx->num_sms, st));
+    CK(launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts, u.shift,
+                       u.taken, st));
+    if (shift_host) {
+        if ((s = sync_status(ctx, cnt, st)) != KM_OK) return s;
+        CK(cudaMemcpy(shift_host, u.shift, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return KM_OK;
+}
+
+static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
+                            const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
+                            double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
+                            const volatile int* cancel);
+
+km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
+                       const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
+                       double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream) {
+    return lloyd_impl(ctx, X, n, d, k, C_init, p, C_out, labels, sse_per_iter, eta_per_iter, iters_done, ws,
+                      ws_bytes, stream, nullptr);
+}
+
+}  // extern "C"
+
+static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
+                            const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
+                            double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
+                            const volatile int* cancel) {
+    km_status s = check_common(ctx, X, n, C_init, k, d);
+    if (s != KM_OK) return s;
+    if ((s = check_params(ctx, p, d)) != KM_OK) return s;
+    if (!C_out || !labels || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
+    if (p->max_iter < 0) return fail(ctx, KM_EINVAL, "max_iter must be >= 0");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    LloydWs L = carve_lloyd(cv, n, d, k, p->low, p->max_iter);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(L.a.cnt, 0, sizeof(DevCounters), st));
+    CK(cudaMemcpyAsync(L.C0, C_init, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToDevice, st));
+    // the quantised data and its norms are computed once (Section 3.2)
+    if (is_tc(p->low)) {
+        const int fmt = fmt_of(p->low);
+        CK(launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, 0, nullptr, st));
+    }
+    CK(launch_absmax(X, n * (int64_t)d, L.u.absmax, st));
+    float* cur = L.C0;
+    float* nxt = L.C1;
+    int t = 0;
+    for (t = 0; t < p->max_iter; t++) {
+        CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
+        s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
+        if (s != KM_OK) return s;
+        CK(launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
+        CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+        CK(launch_accumulate(X, n, d, labels, k, L.u.absmax, L.u.sums, L.u.counts, ctx->num_sms, st));
+        CK(launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt, L.counts,
+                           L.u.shift, L.u.taken, st));
+        std::swap(cur, nxt);
+        if (cancel && *cancel) {
+            CK(cudaStreamSynchronize(st));
+            return fail(ctx, KM_ECANCELLED, "cancelled");
+        }
+        if (p->tau > 0.0) {
+            double shift = 0.0;
+            CK(cudaMemcpyAsync(&shift, L.u.shift, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (shift < p->tau) { t++; break; }
+        }
+    }
+    CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
+    s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
+    if (s != KM_OK) return s;
+    CK(launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
+    CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+    CK(launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.a.sse, st));
+    CK(cudaMemcpyAsync(C_out, cur, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToDevice, st));
+    ctx->last_cnt = L.a.cnt;
+    ctx->last_sse = L.a.sse;
+    ctx->last_stream = st;
+    ctx->last_pairs = (uint64_t)n * (uint64_t)k * (uint64_t)(t + 1);
+    if ((s = sync_status(ctx, L.a.cnt, st)) != KM_OK) return s;
+    std::vector<double> sse(t + 1);
+    std::vector<unsigned long long> fl(t + 1);
+    CK(cudaMemcpy(sse.data(), L.sse_hist, sizeof(double) * (t + 1), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(fl.data(), L.flag_hist, sizeof(unsigned long long) * (t + 1), cudaMemcpyDeviceToHost));
+    const double pairs = (double)n * (double)k;
+    for (int i = 0; i <= t; i++) {
+        if (sse_per_iter) sse_per_iter[i] = sse[i];
+        if (eta_per_iter) eta_per_iter[i] = (double)(fl[i] - (i ? fl[i - 1] : 0ull)) / pairs;
+    }
+    if (iters_done) *iters_done = t;
+    return KM_OK;
+}
+
+extern "C" {
+
+km_status km_get_stats(km_ctx* ctx, km_stats* out) {
+    if (!ctx || !out) return KM_EINVAL;
+    if (!ctx->last_cnt) return fail(ctx, KM_EINVAL, "no call to report on");
+    km_status s = sync_status(ctx, ctx->last_cnt, ctx->last_stream);
+    DevCounters c{};
+    CK(cudaMemcpy(&c, ctx->last_cnt, sizeof c, cudaMemcpyDeviceToHost));
+    out->pairs = ctx->last_pairs;
+    out->flagged = c.flagged;
+    out->fp32_evals = c.fp32_evals;
+    out->fp64_evals = c.fp64_evals;
+    out->ambiguous_rows = c.amb_rows;
+    out->overflow_rows = c.ovf_rows;
+    out->sse = 0.0;
+    if (ctx->last_sse) CK(cudaMemcpy(&out->sse, ctx->last_sse, sizeof(double), cudaMemcpyDeviceToHost));
+    return s;
+}
+
+km_status km_submit(km_ctx* ctx, const km_job* job, uint64_t* job_id) {
+    if (!ctx || !job || !job_id) return KM_EINVAL;
+    if (!ctx->serve) return fail(ctx, KM_EINVAL, "context has no serving arena (km_init with arena_bytes > 0)");
+    if (!job->X || !job->C_init || job->n < 1 || job->d < 1 || job->k < 1 || job->k > job->n)
+        return fail(ctx, KM_EINVAL, "bad job shape");
+    km_status s = check_params(ctx, &job->p, job->d);
+    if (s != KM_OK) return s;
+    return serve_submit(ctx->serve, job, job_id, &ctx->err);
+}
+km_status km_poll(km_ctx* ctx, uint64_t job_id, km_result* out) {
+    if (!ctx || !out) return KM_EINVAL;
+    if (!ctx->serve) return fail(ctx, KM_EINVAL, "context has no serving arena");
+    return serve_poll(ctx->serve, job_id, out);
+}
+km_status km_release(km_ctx* ctx, uint64_t job_id) {
+    if (!ctx) return KM_EINVAL;
+    if (!ctx->serve) return fail(ctx, KM_EINVAL, "context has no serving arena");
+    return serve_release(ctx->serve, job_id);
+}
+km_status km_cancel(km_ctx* ctx, uint64_t job_id) {
+    if (!ctx) return KM_EINVAL;
+    if (!ctx->serve) return fail(ctx, KM_EINVAL, "context has no serving arena");
+    return serve_cancel(ctx->serve, job_id);
+}
+
+}  // extern "C"
+
+size_t km_internal_ws_bytes(int64_t n, int d, int k, const km_params* p) {
+    Carve a{nullptr};
+    carve_lloyd(a, n, d, k, p->low, std::max(0, (int)p->max_iter));
+    Carve b{nullptr};
+    carve_assign(b, n, d, k, p->low, false);
+    b.take<double>((size_t)n);
+    return std::max(a.off, b.off) + 256;
+}
+
+// Used by the serving engine: one whole Lloyd / assign job on its own stream.
+km_status km_internal_run_job(km_ctx_view* v, const float* X, int64_t n, int d, int k, const float* C_init,
+                              const km_params* p, int kind, float* C_out, int32_t* labels, void* ws, size_t ws_bytes,
+                              cudaStream_t st, double* sse, double* eta, int* iters, std::string* err,
+                              const volatile int* cancel) {
+    km_ctx ctx;
+    ctx.device = v->device;
+    ctx.num_sms = v->num_sms;
+    km_status s;
+    if (kind == 1) {
+        s = km_assign(&ctx, X, n, C_init, k, d, p, labels, nullptr, nullptr, ws, ws_bytes, st);
+        if (s == KM_OK) {
+            km_stats stt{};
+            s = km_get_stats(&ctx, &stt);
+            *sse = stt.sse;
+            *eta = stt.pairs ? (double)stt.flagged / (double)stt.pairs : 0.0;
+            *iters = 0;
+        }
+        if (s == KM_OK && C_out != C_init)
+            cudaMemcpyAsync(C_out, C_init, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToDevice, st);
+    } else {
+        std::vector<double> sh(p->max_iter + 1), eh(p->max_iter + 1);
+        s = lloyd_impl(&ctx, X, n, d, k, C_init, p, C_out, labels, sh.data(), eh.data(), iters, ws, ws_bytes, st,
+                       cancel);
+        if (s == KM_OK) {
+            *sse = sh[*iters];
+            double fl = 0;
+            for (int i = 0; i <= *iters; i++) fl += eh[i];
+            *eta = fl / (*iters + 1);
+        }
+    }
+    if (s != KM_OK && err) *err = ctx.err;
+    if (s == KM_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            if (err) *err = cudaGetErrorString(e);
+            s = KM_ECUDA;
+        }
+    }
+    return s;
+}

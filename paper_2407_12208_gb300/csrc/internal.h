@@ -1,0 +1,116 @@
+// internal.h -- declarations shared between the C-ABI layer and the kernel
+// translation units of libmpkm.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace km {
+
+// Per-call device counters (lives in the workspace, zeroed per call).
+struct DevCounters {
+    unsigned long long pairs;
+    unsigned long long flagged;
+    unsigned long long fp32_evals;
+    unsigned long long fp64_evals;
+    unsigned long long amb_rows;
+    unsigned long long ovf_rows;
+    unsigned status;     // KM_DEVERR_* bits
+    int amb_count;       // length of the ambiguous-row list
+    int ovf_count;       // length of the overflow-row list
+    int pad;
+};
+
+// Column-side constants of the reliability bound: maxima over centres.
+struct ColMax {
+    float nc;    // max ||c_j||
+    float nrc;   // max ||c~_j - c_j||
+    float ncq;   // max ||c~_j||
+    float q;     // max ||c_j||^2
+    float ncq2;  // max ||c~_j||^2
+    float cscale;  // uniform power-of-two scale of the quantised centres (E4M3), 1 otherwise
+    float pad[2];
+};
+
+// Parameters of the reliability test / candidate window, host-computed.
+struct TestParams {
+    int test;        // 0 tc, 1 paper, 2 off
+    float rho;
+    float kacc;      // accumulation coefficient of B (2 gamma_d(u_acc) + 4 u32)
+    float kn;        // norm/rounding coefficient of B
+    float paper_coef;  // rho * c_A * gamma^l_{d+2} (paper test)
+    float bsafe;     // relative safety factor applied to B evaluated in fp32
+    float gamma32;   // gamma_{d+2}(2^-24) with safety, for fp32 direct certification
+};
+
+// ---- kernels (launch wrappers; all asynchronous on `st`) -----------------
+// quantise rows of A (m x d fp32) to fmt (0 fp16, 1 bf16, 2 e4m3) with row
+// stride ldq elements; stat[i] = (||a||^2 fp32, ||a||, ||a~||, ||a~ - a||);
+// rscale[i] = per-row scale (e4m3, scale_mode 0) or the uniform scale read
+// from *uscale (scale_mode 1); fp16/bf16 write 1.
+cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
+                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st);
+// amax over all of C (for the uniform E4M3 centre scale): writes the scale.
+cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out, cudaStream_t st);
+// column maxima of the centre statistics
+cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, cudaStream_t st);
+
+// direct-formula assignment (thread per row).  acc64: binary64 accumulation
+// (the plain FP64 path) else fp32 with certification; rows = all n, or the
+// device list row_list[0 .. *row_count).  Uncertified fp32 rows are appended
+// to amb_list / cnt->amb_count.
+cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const float* C, int k, int d,
+                                 const int32_t* row_list, const int* row_count, int32_t* labels,
+                                 double* min_dist, int32_t* amb_list, DevCounters* cnt, float gamma32,
+                                 int num_sms, cudaStream_t st);
+// binary64 exact argmin of the rows of a device list (warp per row)
+cudaError_t launch_rows_fp64(const float* X, const float* C, int k, int d, const int32_t* row_list,
+                             const int* row_count, int64_t max_rows, int32_t* labels, double* min_dist,
+                             DevCounters* cnt, int num_sms, cudaStream_t st);
+
+// tensor-core screening kernel (tcgen05).  mode 0: candidates; mode 1: distance matrix.
+struct TcArgs {
+    int64_t n;
+    int k, d, fmt, kchunks;   // kchunks = number of 128-byte K atoms
+    const float4* xstat;
+    const float* xscale;
+    const float4* cstat;
+    const ColMax* colmax;
+    TestParams tp;
+    int mode;
+    int L;                    // candidate slots per row
+    int2* cand;               // n x L (j, d^ bits)
+    int4* rowinfo;            // n: (count, overflow, nflag, d^min bits)
+    float* D;                 // mode 1: n x k
+    uint32_t* flag_bits;      // mode 1 (nullable)
+    int2* flag_queue;         // mode 1: flagged pairs for the fp64 patch
+    int64_t flag_queue_cap;
+    unsigned long long* flag_queue_len;
+    DevCounters* cnt;
+};
+cudaError_t launch_tc(const void* Xq, const void* Cq, int ldq, const TcArgs& a, int num_sms,
+                      cudaStream_t st);
+size_t tc_smem_bytes(int fmt, int d, int k);
+
+// candidate refinement (warp per row): certified argmin + min_dist
+cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels,
+                          double* min_dist, int32_t* ovf_list, int32_t* amb_list, int num_sms,
+                          cudaStream_t st);
+// fp64 direct values for flagged pairs of the distance matrix
+cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, const int2* queue,
+                                 const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt,
+                                 int num_sms, cudaStream_t st);
+
+// centre update
+cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cudaStream_t st);
+cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
+                              const unsigned* absmax_bits, long long* sums, long long* counts,
+                              int num_sms, cudaStream_t st);
+cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
+                            int64_t n, int k, int d, const float* C_old, int empty_policy,
+                            const float* X, const double* min_dist, float* C_new, int64_t* counts_out,
+                            double* shift, int32_t* taken_rows, cudaStream_t st);
+// deterministic sum of n doubles (fixed two-level order)
+cudaError_t launch_sum_f64(const double* v, int64_t n, double* partials, int nparts, double* out,
+                           cudaStream_t st);
+
+}  // namespace km

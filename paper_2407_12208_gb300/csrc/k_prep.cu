@@ -1,0 +1,180 @@
+// k_prep.cu -- input quantisation and row statistics (Section 4.3, Alg. 2
+// line 1: x~ = fl_l(x)), and the norms the expanded formula reuses
+// (Section 3.2: p_i = x_i^T x_i "precomputed and stored").
+//
+// One warp per row.  Output per row: the quantised row (fp16 / bf16, or
+// E4M3 scaled by a power of two), and stat = (p, ||x||, ||x~||, ||x~ - x||):
+//   p is ||x||^2 accumulated as an fp32 double-float (error ~2^-44) and then
+//   rounded to fp32 -- the same value as binary64 rounded to fp32 except in
+//   ties below 2^-44;  ||x~|| and ||x~ - x|| are fp32 sums inflated by
+//   (1 + 2^-12), which covers their own rounding (gamma_d(2^-24) < 2^-12 for
+//   d <= 4096), so the bound B built from them stays rigorous.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace km {
+
+constexpr float kNormInflate = 1.0f + 1.0f / 4096.0f;
+
+KM_DEV float quant_val(float v, int fmt) {
+    if (fmt == 0) return __half2float(__float2half_rn(v));
+    if (fmt == 1) return __bfloat162float(__float2bfloat16_rn(v));
+    __nv_fp8_storage_t s = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    __half_raw hr = __nv_cvt_fp8_to_halfraw(s, __NV_E4M3);
+    return __half2float(__half(hr));
+}
+
+// Smallest power of two s with amax / s <= 448 (E4M3's largest finite value).
+KM_DEV float e4m3_row_scale(float amax) {
+    if (!(amax > 0.0f)) return 1.0f;
+    float t = amax / 448.0f;  // exact up to rounding; the power-of-two choice below is conservative
+    int e;
+    float f = frexpf(t, &e);  // t = f 2^e, f in [0.5, 1)
+    float s = ldexpf(1.0f, e);
+    if (f == 0.5f) s = ldexpf(1.0f, e - 1);
+    // guarantee amax / s <= 448 despite the rounding of t
+    while (amax / s > 448.0f) s *= 2.0f;
+    return s;
+}
+
+__global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
+                           float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
+                           const float* __restrict__ uscale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < m; i += nw) {
+        const float* a = A + i * d;
+        float s = 1.0f;
+        if (fmt == 2) {
+            if (scale_mode == 1) {
+                s = *uscale;
+            } else {
+                float amax = 0.0f;
+                for (int l = lane; l < d; l += 32) amax = fmaxf(amax, fabsf(a[l]));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+                s = e4m3_row_scale(amax);
+            }
+        }
+        const float inv = 1.0f / s;  // exact: s is a power of two
+        float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
+        for (int l = lane; l < ldq; l += 32) {
+            float v = (l < d) ? a[l] : 0.0f;
+            float qv = quant_val(v * inv, fmt);  // quantised value of x / s
+            if (l < d) {
+                df_add_sq(v, ph, pl);
+                float qs = qv * s;                // x~ = s fl_l(x / s), exact scaling
+                q2 = fmaf(qs, qs, q2);
+                float rr = qs - v;                // exact (Sterbenz): qs and v are within a factor 2
+                r2 = fmaf(rr, rr, r2);
+            }
+            if (fmt == 0) {
+                reinterpret_cast<__half*>(Aq)[i * ldq + l] = __float2half_rn(qv);
+            } else if (fmt == 1) {
+                reinterpret_cast<__nv_bfloat16*>(Aq)[i * ldq + l] = __float2bfloat16_rn(qv);
+            } else {
+                reinterpret_cast<__nv_fp8_storage_t*>(Aq)[i * ldq + l] =
+                    __nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            float oh = __shfl_xor_sync(0xffffffffu, ph, off);
+            float ol = __shfl_xor_sync(0xffffffffu, pl, off);
+            df_add(ph, pl, oh, ol);
+            q2 += __shfl_xor_sync(0xffffffffu, q2, off);
+            r2 += __shfl_xor_sync(0xffffffffu, r2, off);
+        }
+        if (lane == 0) {
+            float p = ph + pl;
+            float4 o;
+            o.x = p;
+            o.y = sqrtf(p) * kNormInflate;
+            o.z = sqrtf(q2) * kNormInflate;
+            o.w = sqrtf(r2) * kNormInflate;
+            // an element that overflowed the low format makes the row unusable
+            // for the expanded formula: an infinite bound flags all its pairs
+            if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
+            stat[i] = o;
+            if (rscale) rscale[i] = s;
+        }
+    }
+}
+
+__global__ void k_amax_scale(const float* __restrict__ C, int64_t count, float* out) {
+    __shared__ float red[32];
+    float amax = 0.0f;
+    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) amax = fmaxf(amax, fabsf(C[e]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        amax = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        if (threadIdx.x == 0) *out = e4m3_row_scale(amax);
+    }
+}
+
+__global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* __restrict__ cscale, ColMax* out) {
+    __shared__ float red[5][32];
+    float a = 0, b = 0, c = 0, q = 0, c2 = 0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        float4 s = cstat[j];
+        a = fmaxf(a, s.y);
+        b = fmaxf(b, s.w);
+        c = fmaxf(c, s.z);
+        q = fmaxf(q, s.x);
+        c2 = fmaxf(c2, s.z * s.z);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, off));
+        b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
+        c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
+        q = fmaxf(q, __shfl_xor_sync(0xffffffffu, q, off));
+        c2 = fmaxf(c2, __shfl_xor_sync(0xffffffffu, c2, off));
+    }
+    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (ln == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = c; red[3][w] = q; red[4][w] = c2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x / 32); i++) {
+            a = fmaxf(a, red[0][i]); b = fmaxf(b, red[1][i]); c = fmaxf(c, red[2][i]);
+            q = fmaxf(q, red[3][i]); c2 = fmaxf(c2, red[4][i]);
+        }
+        ColMax o;
+        o.nc = a; o.nrc = b; o.ncq = c; o.q = q; o.ncq2 = c2;
+        o.cscale = cscale ? *cscale : 1.0f;
+        o.pad[0] = o.pad[1] = 0.0f;
+        *out = o;
+    }
+}
+
+cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
+                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st) {
+    int64_t warps = m;
+    int64_t blocks = (warps * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out, cudaStream_t st) {
+    k_amax_scale<<<1, 1024, 0, st>>>(C, count, scale_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, cudaStream_t st) {
+    k_colmax<<<1, 1024, 0, st>>>(cstat, k, cscale, out);
+    return cudaGetLastError();
+}
+
+}  // namespace km

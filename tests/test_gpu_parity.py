@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle, on the
+same seeded inputs, at sizes that span several tiles and a ragged tail."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_12208_gb300 import workloads
+from gpu_util import MARGIN, RTOL_FP64, RTOL_MIXED, check_assign
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import build
+    build.build()
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run_assign(ctx, X, C, low, test="tc", rho=5.0, c_A=2.0):
+    import paper_2407_12208_gb300 as pkg
+    p = pkg.params(low, test, rho=rho, paper_factor=c_A)
+    lab, md, nf = ctx.assign(_dev(X), _dev(C), p)
+    torch.cuda.synchronize()
+    return lab.cpu().numpy(), md.cpu().numpy(), nf, ctx.stats()
+
+
+# ------------------------------------------------------------- direct paths
+def test_fp64_direct_blobs(ctx):
+    X, C = workloads.blobs(4099, 16, 8, seed=1)
+    lab, md, nf, st = _run_assign(ctx, X, C, "fp64")
+    olab, od1, _ = oracle.assign(X, C)
+    assert np.array_equal(lab, olab)
+    np.testing.assert_allclose(md, od1, rtol=RTOL_FP64)
+    assert nf == 0
+
+
+@pytest.mark.parametrize("n,d,k", [(5000, 5, 16), (1000, 16, 8), (777, 33, 40), (300, 2, 300)])
+def test_fp32_direct_certified(ctx, n, d, k):
+    if d == 5:
+        X, C = workloads.voronoi_image(50, 100, 16, k, seed=2)
+    else:
+        X, C = workloads.blobs(n, d, k, seed=3)
+    lab, md, nf, st = _run_assign(ctx, X, C, "fp32")
+    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+
+
+# ------------------------------------------------------- tensor-core paths
+CASES = [
+    ("uniform", 3001, 128, 300),
+    ("uniform", 1000, 128, 1024),
+    ("mixture", 2500, 64, 256),
+    ("cancellation", 1500, 128, 64),
+    ("uniform", 700, 37, 130),
+    ("mixture", 129, 256, 100),
+]
+
+
+def _data(kind, n, d, k, seed):
+    if kind == "uniform":
+        return workloads.uniform_pairs(n, d, k, seed)
+    if kind == "mixture":
+        return workloads.gaussian_mixture(n, d, k, seed)
+    return workloads.cancellation(n, d, k, seed)
+
+
+@pytest.mark.parametrize("low", ["bf16", "fp16", "e4m3"])
+@pytest.mark.parametrize("kind,n,d,k", CASES)
+def test_tc_assign_parity(ctx, low, kind, n, d, k):
+    X, C = _data(kind, n, d, k, seed=n + d + k)
+    lab, md, nf, st = _run_assign(ctx, X, C, low)
+    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    fmt = {"fp16": 0, "bf16": 1, "e4m3": 2}[low]
+    sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0, per_row_scale=(fmt == 2))
+    lo, hi = int(sure.sum()), int((sure | maybe).sum())
+    assert lo <= nf <= hi, (nf, lo, hi)
+    assert st["pairs"] == n * k
+
+
+@pytest.mark.parametrize("low", ["bf16", "fp16"])
+def test_tc_paper_test_flags_everything_at_r128_bf16(ctx, low):
+    X, C = workloads.uniform_pairs(600, 128, 50, seed=4)
+    lab, md, nf, st = _run_assign(ctx, X, C, low, test="paper", c_A=1.0)
+    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    fmt = {"fp16": 0, "bf16": 1}[low]
+    sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0, test="paper", c_A=1.0)
+    assert int(sure.sum()) <= nf <= int((sure | maybe).sum())
+    if low == "bf16":
+        assert nf == 600 * 50  # Alg. 2 at r >= 72 with BF16: 100% fallback (Table 6.1)
+
+
+def test_tc_test_off_still_certified(ctx):
+    X, C = workloads.gaussian_mixture(2000, 64, 64, seed=5)
+    lab, md, nf, st = _run_assign(ctx, X, C, "bf16", test="off")
+    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    assert nf == 0
+
+
+@pytest.mark.parametrize("low", ["bf16", "fp16"])
+def test_tc_edges(ctx, low):
+    # k = 1; k = n; duplicate centres (ties -> lowest index); n < one tile
+    X, C = workloads.uniform_pairs(50, 96, 1, seed=6)
+    lab, md, *_ = _run_assign(ctx, X, C, low)
+    assert np.all(lab == 0)
+    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    X = workloads.uniform_pairs(200, 64, 200, seed=7)[0]
+    lab, md, *_ = _run_assign(ctx, X, X.copy(), low)
+    assert np.array_equal(lab, np.arange(200))
+    assert np.all(md == 0.0)
+    X, C = workloads.uniform_pairs(400, 64, 40, seed=8)
+    C[25] = C[3]
+    lab, md, *_ = _run_assign(ctx, X, C, low)
+    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    assert not np.any(lab == 25)
+
+
+def test_tc_rejects_bad_arguments(ctx):
+    import paper_2407_12208_gb300 as pkg
+    X = _dev(np.zeros((10, 8), np.float32))
+    with pytest.raises(pkg.KmError) as e:
+        ctx.assign(X, _dev(np.zeros((11, 8), np.float32)), pkg.params("bf16"))  # k > n
+    assert e.value.status == 1
+    with pytest.raises(pkg.KmError) as e:
+        ctx.assign(X, X[:2], pkg.params("e4m3"))  # E4M3 needs d >= 16
+    assert e.value.status == 7
+    with pytest.raises(pkg.KmError) as e:
+        ctx.assign(X, X[:2], pkg.params("bf16", "paper", rho=2.0))  # rho~ > 2 required
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------ distance matrix
+@pytest.mark.parametrize("low", ["fp16", "bf16"])
+@pytest.mark.parametrize("scenario", ["far", "near"])
+def test_distances_alg2(ctx, low, scenario):
+    import paper_2407_12208_gb300 as pkg
+    if scenario == "far":
+        X, C = workloads.near_far(600, 128, 0.0, seed=9)
+    else:
+        X, C = workloads.near_far(600, 128, 0.5, seed=9)
+    C = C[:500]
+    p = pkg.params(low, "tc")
+    D, bits, nf = ctx.distances(_dev(X), _dev(C), p)
+    D = D.cpu().numpy().astype(np.float64)
+    bits = bits.cpu().numpy().view(np.uint32)
+    n, k = D.shape
+    flags = ((bits[(np.arange(n * k) >> 5)] >> (np.arange(n * k) & 31)) & 1).reshape(n, k).astype(bool)
+    assert flags.sum() == nf
+    Dex = oracle.dist_direct(X, C)
+    fmt = {"fp16": 0, "bf16": 1}[low]
+    B = oracle.tc_bound_matrix(X, C, fmt)
+    # unflagged: within the bound (Theorem 4.2 + conversion error); relative error <= 1/(rho-1)
+    un = ~flags
+    assert np.all(np.abs(D[un] - Dex[un]) <= B[un] + 1e-6 * Dex[un])
+    assert np.all(np.abs(D[un] - Dex[un]) <= Dex[un] / 4.0)
+    # flagged: binary64 direct value stored in fp32
+    np.testing.assert_allclose(D[flags], Dex[flags], rtol=2 ** -23, atol=1e-38)
+    sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0)
+    assert np.all(flags[sure & ~maybe]) and not np.any(flags[~sure & ~maybe])
+
+
+# ---------------------------------------------------------------- centre update
+@pytest.mark.parametrize("policy", ["keep", "farthest"])
+def test_update_centroids(ctx, policy):
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.gaussian_mixture(5003, 24, 37, seed=10)
+    olab, od1, _ = oracle.assign(X, C)
+    olab = olab.copy()
+    olab[olab == 5] = 6  # make clusters 5 empty
+    olab[olab == 30] = 0
+    p = pkg.params("fp64", empty=policy)
+    Cn, cnt, shift = ctx.update_centroids(_dev(X), _dev(olab), _dev(C), p, min_dist=_dev(od1))
+    oC, ocnt, oshift = oracle.update(X, olab, C, 1 if policy == "farthest" else 0, od1)
+    assert np.array_equal(cnt.cpu().numpy(), ocnt)
+    Cn = Cn.cpu().numpy()
+    # exact sums: at most a one-ulp difference from binary64 recursive summation
+    np.testing.assert_allclose(Cn, oC, rtol=2 ** -22, atol=1e-30)
+    assert shift == pytest.approx(oshift, rel=1e-6)
+
+
+def test_update_is_bitwise_reproducible(ctx):
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.gaussian_mixture(20000, 64, 64, seed=11)
+    lab = _dev(oracle.assign(X, C)[0])
+    p = pkg.params("fp64")
+    a = ctx.update_centroids(_dev(X), lab, _dev(C), p)[0].cpu().numpy()
+    b = ctx.update_centroids(_dev(X), lab, _dev(C), p)[0].cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+# --------------------------------------------------------------------- Lloyd
+def test_lloyd_fp64_config_plain():
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    X, C0 = workloads.blobs(10000, 16, 8, seed=12)
+    p = pkg.params("fp64", max_iter=20)
+    C, lab, sse, eta, it = c.lloyd_run(_dev(X), _dev(C0), p)
+    oC, olab, osse, oit = oracle.lloyd(X, C0, 20)
+    assert it == oit == 20
+    np.testing.assert_allclose(sse, osse, rtol=RTOL_FP64)
+    assert np.array_equal(lab.cpu().numpy(), olab)
+    np.testing.assert_allclose(C.cpu().numpy(), oC, rtol=2 ** -22)
+
+
+@pytest.mark.parametrize("low", ["fp16", "e4m3", "bf16"])
+def test_lloyd_mixed_trajectory(low):
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    X, C0 = workloads.gaussian_mixture(20000, 64, 32, seed=13)
+    p = pkg.params(low, max_iter=8)
+    C, lab, sse, eta, it = c.lloyd_run(_dev(X), _dev(C0), p)
+    oC, olab, osse, oit = oracle.lloyd(X, C0, 8)
+    np.testing.assert_allclose(sse, osse, rtol=RTOL_MIXED)
+    assert np.array_equal(lab.cpu().numpy(), olab)
+    assert np.all(eta >= 0) and np.all(eta <= 1)
+
+
+def test_tau_stop():
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    X, C0 = workloads.blobs(3000, 4, 3, seed=14)
+    p = pkg.params("fp16", max_iter=100, tau=1e-8)
+    C, lab, sse, eta, it = c.lloyd_run(_dev(X), _dev(C0), p)
+    oC, olab, osse, oit = oracle.lloyd(X, C0, 100, tau=1e-8)
+    assert it == oit < 100
+    np.testing.assert_allclose(sse, osse, rtol=RTOL_MIXED)
+
+
+# ------------------------------------------------- full size, sampled outputs
+def test_full_size_bf16_sampled():
+    """n=1e6, d=128, k=1024 (the headline shape) in the bench's launch
+    configuration; labels and distances checked on 2000 sampled rows."""
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    X, C = workloads.uniform_pairs(1_000_000, 128, 1024, seed=15)
+    lab, md, nf = c.assign(_dev(X), _dev(C), pkg.params("bf16"))
+    lab = lab.cpu().numpy()
+    md = md.cpu().numpy()
+    rows = np.random.default_rng(0).choice(len(X), 2000, replace=False)
+    check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MIXED)
+    st = c.stats()
+    assert st["pairs"] == 1_000_000 * 1024
