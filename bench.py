@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: point-centre pairs/s of the mixed-precision assignment step.
+
+One step = the whole hot path over the resident synthetic batch, through the
+library's C-ABI: quantise X and C, tensor-core screening with the reliability
+test, direct-formula refinement and certified argmin (labels, min_dist),
+then the centre update (Eq. (center)).  Default workload: X uniform[0,1)
+1e6 x 128 fp32, C = 1024 distinct rows of X, BF16 cross term, rho = 5.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (on a bounded sample of the same workload).  Multi-GPU (torchrun):
+independent replicas, one per GPU, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, n, d, k, description)
+    "c2a": ("uniform_pairs", 1_000_000, 128, 1024,
+            "dist+argmin, X uniform[0,1) 1e6 x 128 fp32, C = 1024 distinct rows of X"),
+    "c2b": ("cancellation", 1_000_000, 128, 1024,
+            "dist+argmin, X = 1e3 + N(0, 1e-2^2) 1e6 x 128 fp32, C = 1024 distinct rows of X"),
+}
+METRIC = "point-center pairs/s (dist+argmin)"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _profile_traffic(n: int):
+    """DRAM bytes per launch of the screening kernel from the committed ncu
+    summary, scaled to n rows, if that summary was taken on the current
+    kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_tc_screen_bf16_c2a.md")
+    src = os.path.join(ROOT, "paper_2407_12208_gb300", "csrc", "k_tc.cu")
+    try:
+        txt = open(path).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        mh = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+        mb = re.search(r"dram_bytes_per_row:\s*([0-9.eE+]+)", txt)
+        if mh and mb and mh.group(1) == h:
+            return float(mb.group(1)) * n
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock / throttle reasons during the timed region."""
+
+    def __init__(self, device_uuid: str | None):
+        self.proc = None
+        self.out = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        cmd = ["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "100"]
+        if device_uuid:
+            cmd[1:1] = ["-i", device_uuid]
+        try:
+            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import build as pbuild
+    from paper_2407_12208_gb300 import workloads
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        pbuild.build()
+    gen, n, d, k, desc = WORKLOADS[args.workload]
+    X, C = getattr(workloads, gen)(n, d, k, seed=15 + rank)
+    dev = torch.device("cuda", local)
+    Xd = torch.from_numpy(X).to(dev)
+    Cd = torch.from_numpy(C).to(dev)
+    ctx = pkg.Context(local)
+    p = pkg.params(args.low, "tc", rho=5.0)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    md = torch.empty(n, dtype=torch.float64, device=dev)
+    Cn = torch.empty_like(Cd)
+    counts = torch.empty(k, dtype=torch.int64, device=dev)
+    ws = ctx.workspace(n, d, k, p)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.assign(Xd, Cd, p, labels=labels, min_dist=md, ws=ws, stream=stream, want_flagged=False)
+        ctx.update_centroids(Xd, labels, Cd, p, min_dist=md, C_new=Cn, counts=counts, ws=ws, stream=stream,
+                             want_shift=False)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    # ---------------------------------------------------------- timed region
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clk = ClockSampler(uuid)
+    time.sleep(0.3)
+    ctx.phase_times()
+    ctx.set_profiling(True)
+    l0 = ctx.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - l0
+    ctx.set_profiling(False)
+    phases = ctx.phase_times()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    pairs_per_step = float(n) * k
+    value = pairs_per_step * world / (ms_per_step / 1e3)
+
+    # ------------------------------------------------ roofline of the screen kernel
+    peaks = _measured_peaks()
+    scr_ms, scr_cnt = phases["screen"]
+    flops = 2.0 * n * k * d
+    achieved = flops / (scr_ms / max(scr_cnt, 1) / 1e3) / 1e12 if scr_cnt else None
+    if peaks:
+        peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        peak_src = "measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    else:
+        peak, peak_src = 1700.0, "fallback"
+    if args.low == "fp16":
+        pass  # same nominal rate as bf16
+    elif args.low == "e4m3":
+        peak = peak * 2.0
+        peak_src += " x2 (nominal fp8/bf16 ratio)"
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": _profile_traffic(n),
+            "kernel": "k_tc (tcgen05 screen)", "algorithmic_flops_per_launch": flops, "peak_source": peak_src}
+
+    # ------------------------------------------------------------- end to end
+    Xh = torch.from_numpy(X).pin_memory()
+    Ch = torch.from_numpy(C).pin_memory()
+    lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    md_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        Cd.copy_(Ch, non_blocking=True)
+        step()
+        lab_h.copy_(labels, non_blocking=True)
+        md_h.copy_(md, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": pairs_per_step * world / (e2e_ms / 1e3), "unit": "pairs/s",
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + Ch.numel() * 4),
+           "d2h_bytes_per_step": int(lab_h.numel() * 4 + md_h.numel() * 8), "ms_per_step": e2e_ms}
+
+    stats = ctx.stats()
+    # ------------------------------------------------- FP64 path, same GPU
+    fp64 = None
+    if not args.no_fp64:
+        rows = 16384
+        p64 = pkg.params("fp64")
+        Xs = Xd[:rows]
+        lab64 = torch.empty(rows, dtype=torch.int32, device=dev)
+        md64 = torch.empty(rows, dtype=torch.float64, device=dev)
+        ctx.assign(Xs, Cd, p64, labels=lab64, min_dist=md64, want_flagged=False)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        ctx.assign(Xs, Cd, p64, labels=lab64, min_dist=md64, stream=stream, want_flagged=False)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t64 = g0.elapsed_time(g1) / 1e3
+        v64 = rows * float(k) / t64
+        agree = bool(torch.equal(lab64, labels[:rows]))
+        fp64 = {"value": v64, "unit": "pairs/s", "sample_rows": rows, "labels_equal_on_sample": agree,
+                "mixed_over_fp64": value / world / v64}
+
+    # ------------------------------------------------------- CPU oracle baseline
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rows = args.cpu_rows
+        t0 = time.perf_counter()
+        olab, od1, _ = oracle.assign(X[:rows], C)
+        oracle.update(X[:rows], olab, C, 1, od1)
+        tc = time.perf_counter() - t0
+        cpu = {"value": rows * float(k) / tc, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "first %d of %d rows x %d centres (assign + centre update, binary64 direct)" % (rows, n, k),
+               "seconds": tc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.low, "data": "synthetic",
+            "config": {"workload": args.workload + ": " + desc, "n": n, "d": d, "k": k, "low": args.low,
+                       "test": "tc", "rho": 5.0, "parallelism": "replicas" if world > 1 else "single",
+                       "step": "km_assign (quantise, screen, refine, argmin, min_dist) + km_update_centroids",
+                       "l2": "inputs larger than L2 (X %d MB fp32)" % (n * d * 4 // (1 << 20))},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "fp64_path": fp64,
+            "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},
+            "eta": stats["flagged"] / max(stats["pairs"], 1),
+            "assign_stats": {kk: stats[kk] for kk in ("fp32_evals", "fp64_evals", "ambiguous_rows", "overflow_rows")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The CPU oracle, timed as the reference arm on a bounded sample."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2407_12208_gb300 import workloads
+    oracle.build()
+    gen, n, d, k, desc = WORKLOADS[args.workload]
+    X, C = getattr(workloads, gen)(n, d, k, seed=15)
+    rows = args.ref_rows
+    Xs = X[:rows]
+
+    def step():
+        lab, d1, _ = oracle.assign(Xs, C)
+        oracle.update(Xs, lab, C, 1, d1)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = rows * float(k) / dt
+    sample = "first %d of %d rows x %d centres per step (assign + centre update, binary64 direct)" % (rows, n, k)
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload + ": " + desc, "n": n, "d": d, "k": k, "low": "fp64-direct (oracle)",
+                       "step": "oracle assign + centre update on a row sample"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2a")
+    ap.add_argument("--low", choices=["bf16", "fp16", "e4m3"], default="bf16")
+    ap.add_argument("--cpu-rows", type=int, default=100_000)
+    ap.add_argument("--ref-rows", type=int, default=10_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.warmup < 1:
+            args.warmup = 1
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,25 @@ km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, con
  * call's stream).  Returns KM_ETIMEOUT if a device-side wait ran out. */
 km_status km_get_stats(km_ctx* ctx, km_stats* out);
 
+/* Phase timing.  While on, every call on this context records a pair of
+ * CUDA events on its stream around each phase below (no device memory is
+ * allocated; the events are host-side driver objects). */
+enum {
+    KM_PHASE_QUANTISE = 0,   /* low-precision copies of X and C + norms (Alg. 2 line 1) */
+    KM_PHASE_SCREEN = 1,     /* tensor-core cross term + reliability test + candidates */
+    KM_PHASE_REFINE = 2,     /* direct-formula recompute of candidates, certified argmin */
+    KM_PHASE_FULLROW = 3,    /* rows re-scanned over all centres */
+    KM_PHASE_UPDATE = 4,     /* centre update (Eq. (center)) */
+    KM_PHASE_DIRECT = 5,     /* direct-formula assignment (FP64 / FP32 paths) */
+    KM_NUM_PHASES = 6
+};
+km_status km_set_profiling(km_ctx* ctx, int on);
+/* Sum of each phase's duration (ms, ms[KM_NUM_PHASES]) and number of timed
+ * occurrences (counts, nullable) since the previous read; synchronises. */
+km_status km_get_phase_times(km_ctx* ctx, double* ms, int64_t* counts);
+/* Number of kernels this context has launched since km_init. */
+km_status km_get_launch_count(const km_ctx* ctx, uint64_t* launches);
+
 /* ---- serving (continuous batching on one GPU) ---------------------------- */
 
 /* A job: X (n x d) and C_init (k x d) are HOST pointers, copied into the

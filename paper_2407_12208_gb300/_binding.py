@@ -26,7 +26,9 @@ TEST_NAMES = {"tc": TEST_TC, "paper": TEST_PAPER, "off": TEST_OFF}
 # Symbols declared in include/mpkm.h
 EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_workspace_size",
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
-           "km_submit", "km_poll", "km_release", "km_cancel"]
+           "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
+           "km_get_launch_count"]
+PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
 
 class KmError(RuntimeError):
@@ -94,6 +96,9 @@ def load(path: str = LIB_PATH):
         lib.km_poll.argtypes = [vp, c.c_uint64, c.POINTER(Result)]
         lib.km_release.argtypes = [vp, c.c_uint64]
         lib.km_cancel.argtypes = [vp, c.c_uint64]
+        lib.km_set_profiling.argtypes = [vp, i32]
+        lib.km_get_phase_times.argtypes = [vp, vp, vp]
+        lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
         for f in EXPORTS:
             fn = getattr(lib, f)
             if f not in ("km_default_params", "km_last_error"):
@@ -203,7 +208,7 @@ class Context:
         return D, flag_bits, nf.value
 
     def update_centroids(self, X, labels, C_old, p: Params, min_dist=None, C_new=None, counts=None, ws=None,
-                         stream=None):
+                         stream=None, want_shift=True):
         import torch
         n, d = X.shape
         k = C_old.shape[0]
@@ -215,8 +220,9 @@ class Context:
         sh = ctypes.c_double(0.0)
         self._check(self.lib.km_update_centroids(self.h, _ptr(X), n, d, _ptr(labels), k, _ptr(C_old),
                                                  ctypes.byref(p), _ptr(min_dist), _ptr(C_new), _ptr(counts),
-                                                 ctypes.byref(sh), _ptr(ws), ws.numel(), _stream(stream)))
-        return C_new, counts, sh.value
+                                                 ctypes.byref(sh) if want_shift else None, _ptr(ws), ws.numel(),
+                                                 _stream(stream)))
+        return C_new, counts, (sh.value if want_shift else None)
 
     def lloyd_run(self, X, C_init, p: Params, C_out=None, labels=None, ws=None, stream=None):
         import numpy as np
@@ -242,6 +248,23 @@ class Context:
         s = Stats()
         self._check(self.lib.km_get_stats(self.h, ctypes.byref(s)))
         return s.as_dict()
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.km_set_profiling(self.h, int(bool(on))))
+
+    def phase_times(self):
+        """{phase: (total ms, count)} since the previous read (synchronises)."""
+        import numpy as np
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        cnt = np.zeros(len(PHASES), dtype=np.int64)
+        self._check(self.lib.km_get_phase_times(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                                cnt.ctypes.data_as(ctypes.c_void_p)))
+        return {ph: (float(ms[i]), int(cnt[i])) for i, ph in enumerate(PHASES)}
+
+    def launch_count(self) -> int:
+        v = ctypes.c_uint64(0)
+        self._check(self.lib.km_get_launch_count(self.h, ctypes.byref(v)))
+        return v.value
 
     # ---- serving
     def submit(self, X, C_init, p: Params, kind: int = 0) -> int:

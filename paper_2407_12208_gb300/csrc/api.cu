@@ -32,11 +32,37 @@ struct km_ctx {
     cudaStream_t last_stream = nullptr;
     uint64_t last_pairs = 0;
     km_serve* serve = nullptr;
+    // phase timing (km_set_profiling) and launch counting
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[KM_NUM_PHASES];
+    uint64_t launches = 0;
+    ~km_ctx() {
+        for (auto& v : ev)
+            for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
+};
+
+// Records the start / end of a phase on `st` while profiling is on.
+struct PhaseScope {
+    km_ctx* c;
+    int ph;
+    cudaStream_t st;
+    cudaEvent_t b = nullptr, e = nullptr;
+    PhaseScope(km_ctx* c_, int ph_, cudaStream_t st_) : c(c_), ph(ph_), st(st_) {
+        if (c->prof && cudaEventCreate(&b) == cudaSuccess && cudaEventCreate(&e) == cudaSuccess) cudaEventRecord(b, st);
+        else b = e = nullptr;
+    }
+    ~PhaseScope() {
+        if (b && e) {
+            cudaEventRecord(e, st);
+            c->ev[ph].emplace_back(b, e);
+        }
+    }
 };
 
 namespace {
 
-constexpr int kCandSlots = 16;
+constexpr int kCandSlots = 16;  // per row and epilogue group of the screening kernel
 constexpr int kSumParts = 256;
 
 km_status fail(km_ctx* c, km_status s, const char* fmt, ...) {
@@ -57,6 +83,13 @@ km_status fail(km_ctx* c, km_status s, const char* fmt, ...) {
         if (e_ != cudaSuccess) return fail(ctx, KM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
     } while (0)
 
+// Launches `n` kernels through `expr` and counts them.
+#define KL(n, expr)              \
+    do {                         \
+        ctx->launches += (n);    \
+        CK(expr);                \
+    } while (0)
+
 int fmt_of(int low) { return low == KM_FP16 ? 0 : (low == KM_BF16 ? 1 : 2); }
 bool is_tc(int low) { return low == KM_FP16 || low == KM_BF16 || low == KM_E4M3; }
 double unit_roundoff(int fmt) { return fmt == 0 ? std::ldexp(1.0, -11) : (fmt == 1 ? std::ldexp(1.0, -8) : std::ldexp(1.0, -4)); }
@@ -64,6 +97,7 @@ double gamma_m(int m, double u) {
     double mu = m * u;
     return mu >= 1.0 ? INFINITY : mu / (1.0 - mu);
 }
+int kpad_of(int k) { return ((k + 255) / 256) * 256; }
 int ldq_of(int fmt, int d) { return fmt == 2 ? ((d + 15) / 16) * 16 : ((d + 7) / 8) * 8; }
 
 struct Carve {
@@ -89,7 +123,8 @@ struct AssignWs {
     float* xscale;
     float4* cstat;
     float* cscale;
-    int2* cand;
+    float* qpad;
+    uint32_t* cand;
     int4* rowinfo;
     int32_t* ovf_list;
     int32_t* amb_list;
@@ -117,10 +152,11 @@ AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distance
         w.xscale = cv.take<float>((size_t)n);
         w.cstat = cv.take<float4>((size_t)k);
         w.cscale = cv.take<float>((size_t)k);
-        w.rowinfo = cv.take<int4>((size_t)n);
+        w.qpad = cv.take<float>((size_t)kpad_of(k));
+        w.rowinfo = cv.take<int4>((size_t)n * 2);
         w.ovf_list = cv.take<int32_t>((size_t)n);
         if (!distances) {
-            w.cand = cv.take<int2>((size_t)n * kCandSlots);
+            w.cand = cv.take<uint32_t>((size_t)n * 2 * kCandSlots);
         } else {
             w.queue = cv.take<int2>((size_t)n * k);
             w.qlen = cv.take<unsigned long long>(1);
@@ -169,7 +205,7 @@ LloydWs carve_lloyd(Carve& cv, int64_t n, int d, int k, int low, int max_iter) {
     return L;
 }
 
-km_status check_params(km_ctx* ctx, const km_params* p, int d) {
+km_status check_params(km_ctx* ctx, const km_params* p, int d, int k = 1) {
     if (!p) return fail(ctx, KM_EINVAL, "params is NULL");
     if (p->low < KM_FP64_DIRECT || p->low > KM_E4M3) return fail(ctx, KM_EINVAL, "unknown low precision %d", p->low);
     if (p->test < KM_TEST_TC || p->test > KM_TEST_OFF) return fail(ctx, KM_EINVAL, "unknown test %d", p->test);
@@ -183,6 +219,7 @@ km_status check_params(km_ctx* ctx, const km_params* p, int d) {
                 return fail(ctx, KM_EUNSUPPORTED, "gamma^l_{d+2} undefined: (d+2) u_l >= 1 for d=%d", d);
         }
         if (p->low == KM_E4M3 && d < 16) return fail(ctx, KM_EUNSUPPORTED, "E4M3 needs d >= 16");
+        if (k > 65535) return fail(ctx, KM_EUNSUPPORTED, "the tensor-core paths support k <= 65535");
         if (tc_smem_bytes(fmt_of(p->low), d, 1) == 0) return fail(ctx, KM_EUNSUPPORTED, "d=%d too large for the tensor-core tiles", d);
     } else {
         if (d > 256) return fail(ctx, KM_EUNSUPPORTED, "direct paths support d <= 256");
@@ -213,36 +250,52 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     const TestParams tp = make_tp(p, d);
     if (p->low == KM_FP64_DIRECT || p->low == KM_FP32_DIRECT) {
         const bool acc64 = p->low == KM_FP64_DIRECT;
-        CK(launch_direct_assign(acc64, X, n, C, k, d, nullptr, nullptr, labels, min_dist, w.amb_list, w.cnt,
-                                tp.gamma32, ctx->num_sms, st));
-        if (!acc64)
-            CK(launch_rows_fp64(X, C, k, d, w.amb_list, &w.cnt->amb_count, n, labels, min_dist, w.cnt, ctx->num_sms, st));
+        {
+            PhaseScope ps(ctx, KM_PHASE_DIRECT, st);
+            KL(1, launch_direct_assign(acc64, X, n, C, k, d, nullptr, nullptr, labels, min_dist, w.amb_list, w.cnt,
+                                       tp.gamma32, ctx->num_sms, st));
+        }
+        if (!acc64) {
+            PhaseScope ps(ctx, KM_PHASE_FULLROW, st);
+            KL(1, launch_rows_full(false, X, C, k, d, w.amb_list, &w.cnt->amb_count, labels, min_dist, w.cnt,
+                                   tp.gamma32, ctx->num_sms, st));
+        }
         return KM_OK;
     }
     const int fmt = fmt_of(p->low);
     const int ldq = ldq_of(fmt, d);
     const int esz = fmt == 2 ? 1 : 2;
-    if (!x_prepared)
-        CK(launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
-    if (fmt == 2) {
-        CK(launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
-        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
-        CK(launch_colmax(w.cstat, k, w.cscale_u, w.colmax, st));
-    } else {
-        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
-        CK(launch_colmax(w.cstat, k, nullptr, w.colmax, st));
+    {
+        PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
+        if (!x_prepared) KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
+        if (fmt == 2) {
+            KL(1, launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
+            KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
+            KL(1, launch_colmax(w.cstat, k, w.cscale_u, w.colmax, w.qpad, kpad_of(k), st));
+        } else {
+            KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
+            KL(1, launch_colmax(w.cstat, k, nullptr, w.colmax, w.qpad, kpad_of(k), st));
+        }
     }
     TcArgs a{};
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
     a.kchunks = (ldq * esz + 127) / 128;
-    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.colmax = w.colmax;
+    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
     a.tp = tp; a.mode = 0; a.L = kCandSlots; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
-    CK(launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
-    CK(launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st));
-    // rows whose candidate list overflowed: full-row fp32 direct, then binary64 where uncertified
-    CK(launch_direct_assign(false, X, n, C, k, d, w.ovf_list, &w.cnt->ovf_count, labels, min_dist, w.amb_list,
-                            w.cnt, tp.gamma32, ctx->num_sms, st));
-    CK(launch_rows_fp64(X, C, k, d, w.amb_list, &w.cnt->amb_count, n, labels, min_dist, w.cnt, ctx->num_sms, st));
+    {
+        PhaseScope ps(ctx, KM_PHASE_SCREEN, st);
+        KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
+    }
+    {
+        PhaseScope ps(ctx, KM_PHASE_REFINE, st);
+        KL(1, launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st));
+    }
+    {
+        // rows whose candidate list overflowed: full-row fp32 direct, binary64 where uncertified
+        PhaseScope ps(ctx, KM_PHASE_FULLROW, st);
+        KL(1, launch_rows_full(true, X, C, k, d, w.ovf_list, &w.cnt->ovf_count, labels, min_dist, w.cnt, tp.gamma32,
+                               ctx->num_sms, st));
+    }
     (void)esz;
     return KM_OK;
 }
@@ -327,7 +380,7 @@ km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int 
                     void* stream) {
     km_status s = check_common(ctx, X, n, C, k, d);
     if (s != KM_OK) return s;
-    if ((s = check_params(ctx, p, d)) != KM_OK) return s;
+    if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
     if (!labels || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
     if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
     Carve cv{(char*)ws};
@@ -348,7 +401,7 @@ km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int 
     CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
     s = run_assign(ctx, X, n, C, k, d, p, labels, md, w, false, st);
     if (s != KM_OK) return s;
-    CK(launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
+    KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
     ctx->last_cnt = w.cnt;
     ctx->last_sse = w.sse;
     ctx->last_stream = st;
@@ -367,7 +420,7 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
                        void* stream) {
     km_status s = check_common(ctx, X, n, C, k, d);
     if (s != KM_OK) return s;
-    if ((s = check_params(ctx, p, d)) != KM_OK) return s;
+    if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
     if (!is_tc(p->low)) return fail(ctx, KM_EUNSUPPORTED, "km_distances needs a low format (FP16/BF16/E4M3)");
     if (!D || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
     if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
@@ -382,24 +435,24 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
     const int fmt = fmt_of(p->low);
     const int ldq = ldq_of(fmt, d);
     const int esz = fmt == 2 ? 1 : 2;
-    CK(launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
+    KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
     if (fmt == 2) {
-        CK(launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
-        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
-        CK(launch_colmax(w.cstat, k, w.cscale_u, w.colmax, st));
+        KL(1, launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
+        KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
+        KL(1, launch_colmax(w.cstat, k, w.cscale_u, w.colmax, w.qpad, kpad_of(k), st));
     } else {
-        CK(launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
-        CK(launch_colmax(w.cstat, k, nullptr, w.colmax, st));
+        KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
+        KL(1, launch_colmax(w.cstat, k, nullptr, w.colmax, w.qpad, kpad_of(k), st));
     }
     TcArgs a{};
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
     a.kchunks = (ldq * esz + 127) / 128;
-    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.colmax = w.colmax;
+    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
     a.tp = make_tp(p, d); a.mode = 1; a.L = kCandSlots; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
     a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = n * (int64_t)k;
     a.flag_queue_len = w.qlen;
-    CK(launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
-    CK(launch_patch_flagged(X, C, k, d, w.queue, w.qlen, n * (int64_t)k, D, w.cnt, ctx->num_sms, st));
+    KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
+    KL(1, launch_patch_flagged(X, C, k, d, w.queue, w.qlen, n * (int64_t)k, D, w.cnt, ctx->num_sms, st));
     ctx->last_cnt = w.cnt;
     ctx->last_sse = nullptr;
     ctx->last_stream = st;
@@ -428,10 +481,13 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
     CK(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), st));
-    CK(launch_absmax(X, n * (int64_t)d, u.absmax, st));
-    CK(launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, ctx->num_sms, st));
-    CK(launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts, u.shift,
-                       u.taken, st));
+    {
+        PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
+        KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
+        KL(1, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, ctx->num_sms, st));
+        KL(2, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts,
+                              u.shift, u.taken, st));
+    }
     if (shift_host) {
         if ((s = sync_status(ctx, cnt, st)) != KM_OK) return s;
         CK(cudaMemcpy(shift_host, u.shift, sizeof(double), cudaMemcpyDeviceToHost));
@@ -459,7 +515,7 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
                             const volatile int* cancel) {
     km_status s = check_common(ctx, X, n, C_init, k, d);
     if (s != KM_OK) return s;
-    if ((s = check_params(ctx, p, d)) != KM_OK) return s;
+    if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
     if (!C_out || !labels || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
     if (p->max_iter < 0) return fail(ctx, KM_EINVAL, "max_iter must be >= 0");
     if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
@@ -473,9 +529,10 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     // the quantised data and its norms are computed once (Section 3.2)
     if (is_tc(p->low)) {
         const int fmt = fmt_of(p->low);
-        CK(launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, 0, nullptr, st));
+        PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
+        KL(1, launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, 0, nullptr, st));
     }
-    CK(launch_absmax(X, n * (int64_t)d, L.u.absmax, st));
+    KL(1, launch_absmax(X, n * (int64_t)d, L.u.absmax, st));
     float* cur = L.C0;
     float* nxt = L.C1;
     int t = 0;
@@ -483,11 +540,14 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
         CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
         s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
         if (s != KM_OK) return s;
-        CK(launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
+        KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
         CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
-        CK(launch_accumulate(X, n, d, labels, k, L.u.absmax, L.u.sums, L.u.counts, ctx->num_sms, st));
-        CK(launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt, L.counts,
-                           L.u.shift, L.u.taken, st));
+        {
+            PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
+            KL(1, launch_accumulate(X, n, d, labels, k, L.u.absmax, L.u.sums, L.u.counts, ctx->num_sms, st));
+            KL(2, launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt,
+                                  L.counts, L.u.shift, L.u.taken, st));
+        }
         std::swap(cur, nxt);
         if (cancel && *cancel) {
             CK(cudaStreamSynchronize(st));
@@ -503,9 +563,9 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
     s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
     if (s != KM_OK) return s;
-    CK(launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
+    KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
     CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
-    CK(launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.a.sse, st));
+    KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.a.sse, st));
     CK(cudaMemcpyAsync(C_out, cur, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToDevice, st));
     ctx->last_cnt = L.a.cnt;
     ctx->last_sse = L.a.sse;
@@ -544,12 +604,43 @@ km_status km_get_stats(km_ctx* ctx, km_stats* out) {
     return s;
 }
 
+km_status km_set_profiling(km_ctx* ctx, int on) {
+    if (!ctx) return KM_EINVAL;
+    ctx->prof = on != 0;
+    return KM_OK;
+}
+
+km_status km_get_phase_times(km_ctx* ctx, double* ms, int64_t* counts) {
+    if (!ctx || !ms) return KM_EINVAL;
+    for (int ph = 0; ph < KM_NUM_PHASES; ph++) {
+        double sum = 0.0;
+        for (auto& e : ctx->ev[ph]) {
+            CK(cudaEventSynchronize(e.second));
+            float t = 0.0f;
+            CK(cudaEventElapsedTime(&t, e.first, e.second));
+            sum += t;
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        ms[ph] = sum;
+        if (counts) counts[ph] = (int64_t)ctx->ev[ph].size();
+        ctx->ev[ph].clear();
+    }
+    return KM_OK;
+}
+
+km_status km_get_launch_count(const km_ctx* ctx, uint64_t* launches) {
+    if (!ctx || !launches) return KM_EINVAL;
+    *launches = ctx->launches;
+    return KM_OK;
+}
+
 km_status km_submit(km_ctx* ctx, const km_job* job, uint64_t* job_id) {
     if (!ctx || !job || !job_id) return KM_EINVAL;
     if (!ctx->serve) return fail(ctx, KM_EINVAL, "context has no serving arena (km_init with arena_bytes > 0)");
     if (!job->X || !job->C_init || job->n < 1 || job->d < 1 || job->k < 1 || job->k > job->n)
         return fail(ctx, KM_EINVAL, "bad job shape");
-    km_status s = check_params(ctx, &job->p, job->d);
+    km_status s = check_params(ctx, &job->p, job->d, job->k);
     if (s != KM_OK) return s;
     return serve_submit(ctx->serve, job, job_id, &ctx->err);
 }

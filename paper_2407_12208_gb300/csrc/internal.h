@@ -52,7 +52,9 @@ cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, 
 // amax over all of C (for the uniform E4M3 centre scale): writes the scale.
 cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out, cudaStream_t st);
 // column maxima of the centre statistics
-cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, cudaStream_t st);
+// and q_j padded with +inf to kpad entries
+cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, int kpad,
+                          cudaStream_t st);
 
 // direct-formula assignment (thread per row).  acc64: binary64 accumulation
 // (the plain FP64 path) else fp32 with certification; rows = all n, or the
@@ -62,10 +64,12 @@ cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const fl
                                  const int32_t* row_list, const int* row_count, int32_t* labels,
                                  double* min_dist, int32_t* amb_list, DevCounters* cnt, float gamma32,
                                  int num_sms, cudaStream_t st);
-// binary64 exact argmin of the rows of a device list (warp per row)
-cudaError_t launch_rows_fp64(const float* X, const float* C, int k, int d, const int32_t* row_list,
-                             const int* row_count, int64_t max_rows, int32_t* labels, double* min_dist,
-                             DevCounters* cnt, int num_sms, cudaStream_t st);
+// exact argmin of the rows of a device list, one block per row: fp32 direct
+// values of all centres, certified, binary64 where still open (fp32_first),
+// or binary64 for all centres.
+cudaError_t launch_rows_full(bool fp32_first, const float* X, const float* C, int k, int d, const int32_t* row_list,
+                             const int* row_count, int32_t* labels, double* min_dist, DevCounters* cnt,
+                             float gamma32, int num_sms, cudaStream_t st);
 
 // tensor-core screening kernel (tcgen05).  mode 0: candidates; mode 1: distance matrix.
 struct TcArgs {
@@ -74,12 +78,13 @@ struct TcArgs {
     const float4* xstat;
     const float* xscale;
     const float4* cstat;
+    const float* qpad;        // q_j = ||c_j||^2 for j < k, +inf up to the padded tile width
     const ColMax* colmax;
     TestParams tp;
     int mode;
-    int L;                    // candidate slots per row
-    int2* cand;               // n x L (j, d^ bits)
-    int4* rowinfo;            // n: (count, overflow, nflag, d^min bits)
+    int L;                    // candidate slots per row and epilogue group
+    uint32_t* cand;           // n x 2 x L entries: column j << 16 | 16-bit lower bound of d^
+    int4* rowinfo;            // n x 2: (count, overflow, nflag, d^min bits) per epilogue group
     float* D;                 // mode 1: n x k
     uint32_t* flag_bits;      // mode 1 (nullable)
     int2* flag_queue;         // mode 1: flagged pairs for the fp64 patch

@@ -98,45 +98,129 @@ __global__ void __launch_bounds__(DA_ROWS) k_direct_assign(const float* __restri
     if (local_amb) atomicAdd(&cnt->amb_rows, local_amb);
 }
 
-// Binary64 direct distances of listed rows against all centres; lane j
-// handles centres j, j+32, ...; the warp then takes the exact argmin.
-__global__ void k_rows_fp64(const float* __restrict__ X, const float* __restrict__ C, int k, int d,
-                            const int32_t* __restrict__ row_list, const int* __restrict__ row_count,
-                            int32_t* __restrict__ labels, double* __restrict__ min_dist, DevCounters* cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// Exact argmin of listed rows, one 256-thread block per row.  Thread t takes
+// centres t, t+256, ...  fp32_first: fp32 direct values of all centres
+// (Theorem 4.1 intervals), the block's best and second best, and binary64
+// (oracle arithmetic: products and sums rounded separately, coordinates in
+// order) only for the centres whose interval can still hold the minimum.
+struct Top2 {
+    float b1, b2;
+    int j1;
+};
+KM_DEV Top2 top2_merge(Top2 A, Top2 B) {
+    Top2 r;
+    if (B.b1 < A.b1 || (B.b1 == A.b1 && B.j1 < A.j1)) {
+        r.b1 = B.b1; r.j1 = B.j1; r.b2 = fminf(A.b1, B.b2);
+    } else {
+        r.b1 = A.b1; r.j1 = A.j1; r.b2 = fminf(A.b2, B.b1);
+    }
+    return r;
+}
+
+KM_DEV double direct64(const float* x, const float* c, int d) {
+    double s = 0.0;
+    for (int l = 0; l < d; l++) {
+        const double t = __dsub_rn((double)x[l], (double)c[l]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+template <bool FP32_FIRST>
+__global__ void __launch_bounds__(256) k_rows_full(const float* __restrict__ X, const float* __restrict__ C, int k,
+                                                   int d, const int32_t* __restrict__ row_list,
+                                                   const int* __restrict__ row_count, int32_t* __restrict__ labels,
+                                                   double* __restrict__ min_dist, DevCounters* cnt, float gamma32) {
+    extern __shared__ float sh[];
+    float* xs = sh;                      // d
+    float* vs = sh + ((d + 3) & ~3);     // k fp32 values
+    __shared__ Top2 red[8];
+    __shared__ double rv[8];
+    __shared__ int rj[8];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t nrows = *row_count;
-    unsigned long long evals = 0;
-    for (int64_t w = warp; w < nrows; w += nw) {
+    unsigned long long ev32 = 0, ev64 = 0;
+    for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
         const int64_t i = row_list[w];
-        const float* x = X + i * d;
-        double best = INFINITY;
-        int arg = 0x7fffffff;
-        for (int j = lane; j < k; j += 32) {
-            const float* c = C + (int64_t)j * d;
-            double s = 0.0;
-            for (int l = 0; l < d; l++) {
-                double t = __dsub_rn((double)x[l], (double)c[l]);
-                s = __dadd_rn(s, __dmul_rn(t, t));
+        __syncthreads();
+        for (int l = tid; l < d; l += 256) xs[l] = X[i * d + l];
+        __syncthreads();
+        bool need64 = true;
+        float thr = INFINITY;
+        if (FP32_FIRST) {
+            Top2 t{INFINITY, INFINITY, 0x7fffffff};
+            for (int j = tid; j < k; j += 256) {
+                const float* c = C + (int64_t)j * d;
+                float s = 0.0f;
+                for (int l = 0; l < d; l++) {
+                    const float u = xs[l] - c[l];
+                    s = fmaf(u, u, s);
+                }
+                vs[j] = s;
+                ev32++;
+                if (s < t.b1) { t.b2 = t.b1; t.b1 = s; t.j1 = j; }
+                else if (s < t.b2) t.b2 = s;
             }
-            if (s < best) { best = s; arg = j; }
-            evals++;
-        }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, off);
-            int oa = __shfl_xor_sync(0xffffffffu, arg, off);
-            if (ob < best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+            for (int off = 16; off > 0; off >>= 1) {
+                Top2 o;
+                o.b1 = __shfl_xor_sync(0xffffffffu, t.b1, off);
+                o.b2 = __shfl_xor_sync(0xffffffffu, t.b2, off);
+                o.j1 = __shfl_xor_sync(0xffffffffu, t.j1, off);
+                t = top2_merge(t, o);
+            }
+            if (lane == 0) red[wid] = t;
+            __syncthreads();
+            t = red[0];
+            for (int q = 1; q < 8; q++) t = top2_merge(t, red[q]);
+            const float g = gamma32;
+            if (t.b2 * (1.0f - g) > t.b1 * (1.0f + g)) {
+                need64 = false;
+                if (tid == 0) {
+                    labels[i] = t.j1;
+                    min_dist[i] = (double)t.b1;
+                }
+            } else {
+                thr = t.b1 * (1.0f + g);
+                if (tid == 0) atomicAdd(&cnt->amb_rows, 1ull);
+            }
         }
-        if (lane == 0) {
-            labels[i] = arg;
-            min_dist[i] = best;
+        if (need64) {
+            double best = INFINITY;
+            int arg = 0x7fffffff;
+            for (int j = tid; j < k; j += 256) {
+                if (FP32_FIRST && !(vs[j] * (1.0f - gamma32) <= thr)) continue;
+                const double s = direct64(xs, C + (int64_t)j * d, d);
+                ev64++;
+                if (s < best) { best = s; arg = j; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+                if (ob < best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+            }
+            if (lane == 0) { rv[wid] = best; rj[wid] = arg; }
+            __syncthreads();
+            if (tid == 0) {
+                best = rv[0];
+                arg = rj[0];
+                for (int q = 1; q < 8; q++)
+                    if (rv[q] < best || (rv[q] == best && rj[q] < arg)) { best = rv[q]; arg = rj[q]; }
+                labels[i] = arg;
+                min_dist[i] = best;
+            }
         }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, off);
-    if (lane == 0 && evals) atomicAdd(&cnt->fp64_evals, evals);
+    for (int off = 16; off > 0; off >>= 1) {
+        ev32 += __shfl_xor_sync(0xffffffffu, ev32, off);
+        ev64 += __shfl_xor_sync(0xffffffffu, ev64, off);
+    }
+    if (lane == 0) {
+        if (ev32) atomicAdd(&cnt->fp32_evals, ev32);
+        if (ev64) atomicAdd(&cnt->fp64_evals, ev64);
+    }
 }
 
 static size_t direct_smem(bool acc64, int d) {
@@ -169,12 +253,20 @@ cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_rows_fp64(const float* X, const float* C, int k, int d, const int32_t* row_list,
-                             const int* row_count, int64_t max_rows, int32_t* labels, double* min_dist,
-                             DevCounters* cnt, int num_sms, cudaStream_t st) {
-    int64_t warps = max((int64_t)1, min(max_rows, (int64_t)num_sms * 32));
-    int64_t blocks = (warps * 32 + 255) / 256;
-    k_rows_fp64<<<(unsigned)blocks, 256, 0, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt);
+cudaError_t launch_rows_full(bool fp32_first, const float* X, const float* C, int k, int d, const int32_t* row_list,
+                             const int* row_count, int32_t* labels, double* min_dist, DevCounters* cnt,
+                             float gamma32, int num_sms, cudaStream_t st) {
+    const size_t sm = (size_t)(((d + 3) & ~3) + k) * sizeof(float);
+    cudaError_t e;
+    if (fp32_first) {
+        e = cudaFuncSetAttribute(k_rows_full<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_rows_full<true><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32);
+    } else {
+        e = cudaFuncSetAttribute(k_rows_full<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_rows_full<false><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32);
+    }
     return cudaGetLastError();
 }
 

@@ -122,7 +122,10 @@ __global__ void k_amax_scale(const float* __restrict__ C, int64_t count, float* 
     }
 }
 
-__global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* __restrict__ cscale, ColMax* out) {
+__global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* __restrict__ cscale, ColMax* out,
+                         float* __restrict__ qpad, int kpad) {
+    // q_j for the screening kernel, +inf on the padding so padded columns never win
+    for (int j = threadIdx.x; j < kpad; j += blockDim.x) qpad[j] = (j < k) ? cstat[j].x : INFINITY;
     __shared__ float red[5][32];
     float a = 0, b = 0, c = 0, q = 0, c2 = 0;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
@@ -172,8 +175,9 @@ cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out
     return cudaGetLastError();
 }
 
-cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, cudaStream_t st) {
-    k_colmax<<<1, 1024, 0, st>>>(cstat, k, cscale, out);
+cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, int kpad,
+                          cudaStream_t st) {
+    k_colmax<<<1, 1024, 0, st>>>(cstat, k, cscale, out, qpad, kpad);
     return cudaGetLastError();
 }
 

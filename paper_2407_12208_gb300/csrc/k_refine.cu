@@ -31,9 +31,10 @@ __global__ void k_refine(const float* __restrict__ X, const float* __restrict__ 
     const TestParams tp = a.tp;
     unsigned long long ev32 = 0, ev64 = 0, amb = 0, ovf_rows = 0;
     for (int64_t row = warp; row < a.n; row += nw) {
-        const int4 info = a.rowinfo[row];
-        const int cnt = info.x;
-        if (info.y) {  // overflowed: whole-row direct evaluation elsewhere
+        // the two epilogue groups of the screening kernel each left a list
+        const int4 i0 = a.rowinfo[row * 2], i1 = a.rowinfo[row * 2 + 1];
+        const int cnt = i0.x + i1.x;
+        if (i0.y | i1.y) {  // overflowed: whole-row direct evaluation elsewhere
             if (lane == 0) {
                 int slot = atomicAdd(&a.cnt->ovf_count, 1);
                 ovf_list[slot] = (int32_t)row;
@@ -47,13 +48,17 @@ __global__ void k_refine(const float* __restrict__ X, const float* __restrict__ 
         int j = 0x7fffffff;
         float lo = INFINITY, hi = INFINITY;
         if (lane < cnt) {
-            const int2 c = a.cand[(size_t)row * a.L + lane];
-            j = c.x;
-            const float dh = __int_as_float(c.y);
+            const size_t slot = (lane < i0.x) ? ((size_t)row * 2) * a.L + lane
+                                              : ((size_t)row * 2 + 1) * a.L + (lane - i0.x);
+            const uint32_t c = a.cand[slot];
+            j = (int)(c >> 16);
+            // the entry holds a lower bound of d^ with 8 significant bits
+            const float dl = __uint_as_float(c << 16);
+            const float du = dl + fabsf(dl) * (1.0f / 64.0f);
             const float4 cs = a.cstat[j];
             const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (xs.x + cs.x)) * tp.bsafe;
-            lo = dh - B;
-            hi = dh + B;
+            lo = dl - B;
+            hi = du + B;
         }
         float U = hi;
 #pragma unroll

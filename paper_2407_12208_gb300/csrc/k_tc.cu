@@ -30,13 +30,14 @@
 
 namespace km {
 
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;
 constexpr int TC_BM = 128;
-constexpr int SMEM_BUDGET = 225 * 1024;
+constexpr int TC_L = 16;  // candidate slots per row and epilogue group
+constexpr int SMEM_BUDGET = 227 * 1024;
 
 struct TcLayout {
     int BN, NA, NS, kchunks;
-    size_t a_bytes, b_bytes, q_off, scr_off, bar_off, total;
+    size_t a_bytes, b_bytes, q_off, list_off, bar_off, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
@@ -46,9 +47,9 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     L.a_bytes = (size_t)kchunks * TC_BM * 128;
     L.b_bytes = (size_t)kchunks * BN * 128;
     const int nt = (k + BN - 1) / BN;
-    const size_t qbytes = (((size_t)nt * BN * 4) + 1023) & ~(size_t)1023;
-    const size_t scr = (size_t)32 * TC_BM * 4;  // per-thread staging of one 32-column chunk
-    const size_t fixed = 1024 /*align slack*/ + qbytes + scr + 1024 /*barriers*/;
+    const size_t qbytes = (((size_t)nt * BN * 4) + 255) & ~(size_t)255;  // q_j of every column, +inf padded
+    const size_t lists = (size_t)2 * TC_L * TC_BM * 4;  // per-row candidate lists of both epilogue groups
+    const size_t fixed = 1024 /*align slack*/ + qbytes + lists + 256 /*barriers*/;
     L.NA = 2;
     size_t rem = (size_t)SMEM_BUDGET - fixed - 2 * L.a_bytes;
     if ((long long)rem < (long long)(2 * L.b_bytes)) {
@@ -58,9 +59,9 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     L.NS = (int)(rem / L.b_bytes);
     if (L.NS > 6) L.NS = 6;
     L.q_off = (size_t)L.NA * L.a_bytes + (size_t)L.NS * L.b_bytes;
-    L.scr_off = L.q_off + qbytes;
-    L.bar_off = L.scr_off + scr;
-    L.total = L.bar_off + 1024 + 1024;
+    L.list_off = L.q_off + qbytes;
+    L.bar_off = L.list_off + lists;
+    L.total = L.bar_off + 256 + 1024;
     return L;
 }
 
@@ -68,6 +69,69 @@ static int pick_bn(int kchunks, int k) {
     if (k <= 128) return 128;
     TcLayout L = tc_layout(256, kchunks, k);
     return (L.NS >= 2) ? 256 : 128;
+}
+
+// Asynchronous TMEM load (32 lanes x 32 columns) and the matching wait; the
+// wait names the destination registers so no read of them is scheduled
+// before it.
+KM_DEV void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+KM_DEV void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
+                   "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// Reliability test of one pair (rare path): tc form rho * B(x, c) or Alg. 2's
+// rho c_A gamma^l_{d+2} (||x~||^2 + ||c~||^2).
+__device__ __noinline__ bool pair_flagged(const TestParams& tp, const float4* cstat, int j, float dh, float a1,
+                                          float a2, float a3, float p, float nxq) {
+    const float4 cs = cstat[j];
+    if (tp.test == 0) {
+        const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (p + cs.x)) * tp.bsafe;
+        return dh <= tp.rho * B;
+    }
+    return dh <= tp.paper_coef * (nxq * nxq + cs.z * cs.z);
+}
+
+// Candidate entry: column j (16 bits) and a 16-bit lower bound of d^ (the
+// top half of its fp32 encoding, one step further from zero if negative).
+KM_DEV uint32_t cand_entry(int j, float dh) {
+    const uint32_t b = __float_as_uint(dh);
+    uint32_t hi = b >> 16;
+    if ((b & 0x80000000u) && (b & 0xFFFFu)) hi += 1;
+    return ((uint32_t)j << 16) | hi;
+}
+KM_DEV float cand_dh_lower(uint32_t e) { return __uint_as_float(e << 16); }
+
+// Keep only the list entries still inside the window (slot-major layout).
+__device__ __noinline__ int compact_list(uint32_t* list, int cnt, float lim) {
+    int w = 0;
+    for (int r = 0; r < cnt; r++) {
+        const uint32_t c = list[r * TC_BM];
+        if (cand_dh_lower(c) <= lim) list[(w++) * TC_BM] = c;
+    }
+    return w;
+}
+
+KM_DEV float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 template <int FMT, int BN, int MODE>
@@ -79,7 +143,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char* sA = smem;
     unsigned char* sB = smem + (size_t)L.NA * L.a_bytes;
     float* qs = reinterpret_cast<float*>(smem + L.q_off);
-    float* escr = reinterpret_cast<float*>(smem + L.scr_off);
+    uint32_t* lists = reinterpret_cast<uint32_t*>(smem + L.list_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* a_full = bars;            // [2]
     uint64_t* a_empty = bars + 2;       // [2]
@@ -107,10 +171,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_barrier_init();
     }
     if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
-    if (warp >= 2) {
-        // column norms q_j (+inf past k so padded columns never win)
-        for (int j = threadIdx.x - 64; j < NT * BN; j += 128) qs[j] = (j < a.k) ? a.cstat[j].x : INFINITY;
-    }
+    if (warp >= 2)  // q_j for every tile column (+inf on the padding: padded columns never win)
+        for (int j = threadIdx.x - 64; j < NT * BN; j += TC_THREADS - 64) qs[j] = a.qpad[j];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -147,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_make(FMT == 0 ? 0u : (FMT == 1 ? 1u : 0u), TC_BM, BN);
+            constexpr uint32_t idesc = idesc_make(FMT == 1 ? 1u : 0u, TC_BM, BN);
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             int64_t bcons = 0, tcount = 0;
             int iter = 0;
@@ -191,15 +253,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
+        // Two groups of four warps; group g drains accumulator buffer g, i.e.
+        // the tiles with an index of parity g, so the two groups overlap.
+        const int g = (warp - 2) >> 2;
         const int quarter = warp & 3;  // TMEM lanes this warp may access
         const int r_in = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        uint32_t* list = lists + (size_t)g * TC_L * TC_BM + r_in;  // slot s at list[s * TC_BM]
         const ColMax cm = *a.colmax;
         const TestParams tp = a.tp;
-        int64_t tcount = 0;
         unsigned long long nflag_total = 0;
         bool ok = true;
-        for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+        int iter = 0;
+        for (int64_t rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x, iter++) {
             const int64_t row = rb * TC_BM + r_in;
             const bool valid = row < a.n;
             float4 xs = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -217,122 +283,115 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (tp.test == 0) F = tp.rho * bmax;
             else if (tp.test == 1) F = tp.paper_coef * (xs.z * xs.z + cm.ncq2) * 1.0001f;
             else F = -INFINITY;
-            const float Fe = (tp.test == 2) ? -INFINITY : F - p + fabsf(F) * 1e-6f;  // in e = d^ - p units
+            if (!valid) F = -INFINITY;  // rows past n: no flags, no candidates
+            const float Fe = (F == -INFINITY) ? -INFINITY : F - p + fabsf(F) * 1e-6f;  // in e = d^ - p units
             const float W = 2.0f * bmax * 1.001f + 1e-30f;      // candidate window
             float m = INFINITY;
             int cnt = 0, ovf = 0, nflag = 0;
-            int2* crow = a.cand + (size_t)(valid ? row : 0) * a.L;
 
-            for (int nt = 0; nt < NT; nt++, tcount++) {
-                const int accb = (int)(tcount & 1);
-                ok = mbar_wait(&acc_full[accb], (tcount >> 1) & 1, abort_flag, status);
+            for (int nt = 0; nt < NT; nt++) {
+                const int64_t tc = (int64_t)iter * NT + nt;
+                if ((int)(tc & 1) != g) continue;
+                ok = mbar_wait(&acc_full[g], (uint32_t)((tc >> 1) & 1), abort_flag, status);
                 if (!ok) break;
                 tc_fence_after();
-                for (int ch = 0; ch < BN / 32; ch++) {
+                const int nch = min(BN / 32, (a.k - nt * BN + 31) / 32);
+                const uint32_t tbase = tmem_base + lane_addr + (uint32_t)(g * BN);
+                uint32_t ra[32];
+                __syncwarp();
+                tmem_ld32_async(tbase, ra);
+                tmem_wait_ld(ra);
+                auto process = [&](const uint32_t (&v)[32], int ch) {
                     const int col0 = nt * BN + ch * 32;
-                    if (col0 >= a.k) break;
-                    float v[32];
-                    __syncwarp();
-                    tmem_ld32(tmem_base + lane_addr + (uint32_t)(accb * BN + ch * 32), v);
-                    if (valid) {
+                    // q_j (+inf past k: padded columns never win); same address in all lanes
                     const float4* q4 = reinterpret_cast<const float4*>(qs + col0);
                     float e[32];
-                    float cmin = INFINITY;
 #pragma unroll
                     for (int t4 = 0; t4 < 8; t4++) {
                         const float4 qq = q4[t4];
-                        e[4 * t4 + 0] = fmaf(v[4 * t4 + 0], neg2s, qq.x);
-                        e[4 * t4 + 1] = fmaf(v[4 * t4 + 1], neg2s, qq.y);
-                        e[4 * t4 + 2] = fmaf(v[4 * t4 + 2], neg2s, qq.z);
-                        e[4 * t4 + 3] = fmaf(v[4 * t4 + 3], neg2s, qq.w);
+                        e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]), neg2s, qq.x);
+                        e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]), neg2s, qq.y);
+                        e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]), neg2s, qq.z);
+                        e[4 * t4 + 3] = fmaf(__uint_as_float(v[4 * t4 + 3]), neg2s, qq.w);
                     }
                     if (MODE == 0) {
+                        // tree minimum; the four octet minima steer the slow path
+                        float om[4];
 #pragma unroll
-                        for (int t = 0; t < 32; t++) cmin = fminf(cmin, e[t]);
+                        for (int o = 0; o < 4; o++) {
+                            const float m1 = fmin3(e[8 * o + 0], e[8 * o + 1], e[8 * o + 2]);
+                            const float m2 = fmin3(e[8 * o + 3], e[8 * o + 4], e[8 * o + 5]);
+                            om[o] = fmin3(m1, m2, fminf(e[8 * o + 6], e[8 * o + 7]));
+                        }
+                        const float cmin = fmin3(om[0], om[1], fminf(om[2], om[3]));
                         m = fminf(m, cmin);
                         const float cthr = m + W;
-                        const float sthr = fmaxf(cthr, Fe);
-                        if (cmin <= sthr) {
-                            float* scr = escr + r_in;
+                        const float sthr = valid ? fmaxf(cthr, Fe) : -INFINITY;
+                        // Warp-uniform control flow: an octet, then a column, is visited only
+                        // if some lane of the warp has a candidate or a possibly flagged pair
+                        // there; the per-lane work inside is predicated.
+                        if (__any_sync(0xffffffffu, cmin <= sthr)) {
 #pragma unroll
-                            for (int t = 0; t < 32; t++) scr[t * TC_BM] = e[t];
-#pragma unroll 1
-                            for (int t = 0; t < 32; t++) {
-                                const float et = scr[t * TC_BM];
-                                if (et <= sthr) {
-                                    const int j = col0 + t;
+                            for (int o = 0; o < 4; o++) {
+                                if (!__any_sync(0xffffffffu, om[o] <= sthr)) continue;
+                                // room for a whole octet, else drop entries that left the window
+                                if (__any_sync(0xffffffffu, cnt > TC_L - 8 && !ovf))
+                                    if (cnt > TC_L - 8 && !ovf) cnt = compact_list(list, cnt, p + cthr);
+#pragma unroll
+                                for (int q = 0; q < 8; q++) {
+                                    const float et = e[8 * o + q];
+                                    if (!__any_sync(0xffffffffu, et <= sthr)) continue;
+                                    const int j = col0 + 8 * o + q;
                                     const float dh = p + et;
-                                    if (dh <= F) {
-                                        bool fl;
-                                        if (tp.test == 0) {
-                                            const float4 cs = a.cstat[j];
-                                            const float B =
-                                                (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (p + cs.x)) * tp.bsafe;
-                                            fl = dh <= tp.rho * B;
-                                        } else {
-                                            const float4 cs = a.cstat[j];
-                                            fl = dh <= tp.paper_coef * (xs.z * xs.z + cs.z * cs.z);
-                                        }
-                                        nflag += fl ? 1 : 0;
-                                    }
                                     if (et <= cthr && !ovf) {
-                                        if (cnt == a.L) {
-                                            // compact: keep only entries still inside the window
-                                            int w = 0;
-                                            const float lim = p + cthr;
-                                            for (int r2 = 0; r2 < a.L; r2++) {
-                                                const int2 c = crow[r2];
-                                                if (__int_as_float(c.y) <= lim) crow[w++] = c;
-                                            }
-                                            cnt = w;
-                                        }
-                                        if (cnt < a.L) crow[cnt++] = make_int2(j, __float_as_int(dh));
+                                        if (cnt < TC_L) list[(cnt++) * TC_BM] = cand_entry(j, dh);
                                         else ovf = 1;
                                     }
+                                    if (dh <= F) nflag += pair_flagged(tp, a.cstat, j, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
                                 }
                             }
                         }
-                    } else {
+                    } else if (valid) {
                         // distance-matrix mode: Alg. 2's d = max(d^, 0) and its flag, every pair
                         float* drow = a.D + (size_t)row * a.k;
-                        float* scr = escr + r_in;
 #pragma unroll
-                        for (int t = 0; t < 32; t++) scr[t * TC_BM] = e[t];
-#pragma unroll 1
                         for (int t = 0; t < 32; t++) {
                             const int j = col0 + t;
-                            if (j >= a.k) break;
-                            const float dh = fmaxf(p + scr[t * TC_BM], 0.0f);
-                            bool fl = false;
-                            if (dh <= F) {
-                                const float4 cs = a.cstat[j];
-                                if (tp.test == 0) {
-                                    const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (p + cs.x)) * tp.bsafe;
-                                    fl = dh <= tp.rho * B;
-                                } else {
-                                    fl = dh <= tp.paper_coef * (xs.z * xs.z + cs.z * cs.z);
-                                }
-                            }
-                            drow[j] = dh;
-                            if (fl) {
-                                nflag++;
-                                const unsigned long long pos = atomicAdd(a.flag_queue_len, 1ull);
-                                if ((int64_t)pos < a.flag_queue_cap) a.flag_queue[pos] = make_int2((int)row, j);
-                                if (a.flag_bits) {
-                                    const unsigned long long bit = (unsigned long long)row * a.k + j;
-                                    atomicOr(&a.flag_bits[bit >> 5], 1u << (bit & 31));
+                            if (j < a.k) {
+                                const float dh = fmaxf(p + e[t], 0.0f);
+                                const bool fl = (dh <= F) && pair_flagged(tp, a.cstat, j, dh, a1, a2, a3, p, xs.z);
+                                drow[j] = dh;
+                                if (fl) {
+                                    nflag++;
+                                    const unsigned long long pos = atomicAdd(a.flag_queue_len, 1ull);
+                                    if ((int64_t)pos < a.flag_queue_cap) a.flag_queue[pos] = make_int2((int)row, j);
+                                    if (a.flag_bits) {
+                                        const unsigned long long bit = (unsigned long long)row * a.k + j;
+                                        atomicOr(&a.flag_bits[bit >> 5], 1u << (bit & 31));
+                                    }
                                 }
                             }
                         }
                     }
-                    }  // valid
+                };
+                for (int ch = 0; ch < nch; ch++) {
+                    if (ch > 0) {
+                        __syncwarp();
+                        tmem_ld32_async(tbase + (uint32_t)(ch * 32), ra);
+                        tmem_wait_ld(ra);
+                    }
+                    process(ra, ch);
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[accb]);
+                if (lane == 0) mbar_arrive(&acc_empty[g]);
             }
             if (!ok) break;
-            if (valid && MODE == 0) a.rowinfo[row] = make_int4(cnt, ovf, nflag, __float_as_int(p + m));
+            if (valid && MODE == 0) {
+                uint32_t* crow = a.cand + ((size_t)row * 2 + g) * TC_L;
+                for (int sl = 0; sl < cnt; sl++) crow[sl] = list[sl * TC_BM];
+                a.rowinfo[row * 2 + g] = make_int4(cnt, ovf, nflag, __float_as_int(p + m));
+            }
             nflag_total += (unsigned long long)nflag;
         }
 #pragma unroll

@@ -57,7 +57,7 @@ def test_fp32_direct_certified(ctx, n, d, k):
 # ------------------------------------------------------- tensor-core paths
 CASES = [
     ("uniform", 3001, 128, 300),
-    ("uniform", 1000, 128, 1024),
+    ("uniform", 2000, 128, 1024),
     ("mixture", 2500, 64, 256),
     ("cancellation", 1500, 128, 64),
     ("uniform", 700, 37, 130),
