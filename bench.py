@@ -292,7 +292,7 @@ def run_ours(args):
             "config": {"workload": args.workload + ": " + desc, "n": n, "d": d, "k": k, "low": args.low,
                        "test": "tc", "rho": 5.0, "parallelism": "replicas" if world > 1 else "single",
                        "step": "km_assign (quantise, screen, refine, argmin, min_dist) + km_update_centroids",
-                       "l2": "inputs larger than L2 (X %d MB fp32)" % (n * d * 4 // (1 << 20))},
+                       "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
             "fp64_path": fp64,
             "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},

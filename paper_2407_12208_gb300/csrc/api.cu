@@ -62,7 +62,7 @@ struct PhaseScope {
 
 namespace {
 
-constexpr int kCandSlots = 16;  // per row and epilogue group of the screening kernel
+constexpr int kCandSlots = 24;  // per row and epilogue group of the screening kernel
 constexpr int kSumParts = 256;
 
 km_status fail(km_ctx* c, km_status s, const char* fmt, ...) {
@@ -474,7 +474,10 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     if (!p || !labels || !C_new || !ws) return fail(ctx, KM_EINVAL, "null argument");
     if (p->empty != KM_EMPTY_KEEP && p->empty != KM_EMPTY_FARTHEST) return fail(ctx, KM_EINVAL, "unknown empty policy");
     if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    // the update's scratch lies past an assignment's, so the counters of the
+    // last assignment on the same workspace stay readable (km_get_stats)
     Carve cv{(char*)ws};
+    carve_assign(cv, n, d, k, p->low, false);
     DevCounters* cnt = cv.take<DevCounters>(1);
     UpdateWs u = carve_update(cv, d, k);
     if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);

@@ -52,8 +52,10 @@ KM_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // false (and flags the abort word and the global status) on timeout, or
 // immediately if another thread of the CTA already aborted.
 KM_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, unsigned* status) {
+    if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
+        __nanosleep(32);  // back off: leave the issue slots to the warps doing work
         if (*abort_flag) return false;
         if (clock64() - t0 > KM_WAIT_CYCLES) {
             *abort_flag = 1;

@@ -34,7 +34,7 @@ __global__ void k_refine(const float* __restrict__ X, const float* __restrict__ 
         // the two epilogue groups of the screening kernel each left a list
         const int4 i0 = a.rowinfo[row * 2], i1 = a.rowinfo[row * 2 + 1];
         const int cnt = i0.x + i1.x;
-        if (i0.y | i1.y) {  // overflowed: whole-row direct evaluation elsewhere
+        if ((i0.y | i1.y) || cnt > 32) {  // overflowed: whole-row direct evaluation elsewhere
             if (lane == 0) {
                 int slot = atomicAdd(&a.cnt->ovf_count, 1);
                 ovf_list[slot] = (int32_t)row;
@@ -52,9 +52,10 @@ __global__ void k_refine(const float* __restrict__ X, const float* __restrict__ 
                                               : ((size_t)row * 2 + 1) * a.L + (lane - i0.x);
             const uint32_t c = a.cand[slot];
             j = (int)(c >> 16);
-            // the entry holds a lower bound of d^ with 8 significant bits
-            const float dl = __uint_as_float(c << 16);
-            const float du = dl + fabsf(dl) * (1.0f / 64.0f);
+            // the entry holds d^ truncated toward zero to 8 significant bits
+            const float t = __uint_as_float(c << 16);
+            const float dl = t - fabsf(t) * (1.0f / 128.0f);
+            const float du = t + fabsf(t) * (1.0f / 128.0f);
             const float4 cs = a.cstat[j];
             const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (xs.x + cs.x)) * tp.bsafe;
             lo = dl - B;

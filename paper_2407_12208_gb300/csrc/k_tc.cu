@@ -32,7 +32,7 @@ namespace km {
 
 constexpr int TC_THREADS = 320;
 constexpr int TC_BM = 128;
-constexpr int TC_L = 16;  // candidate slots per row and epilogue group
+constexpr int TC_L = 24;  // candidate slots per row and epilogue group
 constexpr int SMEM_BUDGET = 227 * 1024;
 
 struct TcLayout {
@@ -48,7 +48,8 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     L.b_bytes = (size_t)kchunks * BN * 128;
     const int nt = (k + BN - 1) / BN;
     const size_t qbytes = (((size_t)nt * BN * 4) + 255) & ~(size_t)255;  // q_j of every column, +inf padded
-    const size_t lists = (size_t)2 * TC_L * TC_BM * 4;  // per-row candidate lists of both epilogue groups
+    const size_t lists = (size_t)2 * (TC_L + 1) * TC_BM * 4   // per-row candidate lists (+1 dummy slot) of both groups
+                         + (size_t)2 * TC_BM * 8;         // per-row running minimum published by each group
     const size_t fixed = 1024 /*align slack*/ + qbytes + lists + 256 /*barriers*/;
     L.NA = 2;
     size_t rem = (size_t)SMEM_BUDGET - fixed - 2 * L.a_bytes;
@@ -66,9 +67,9 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
 }
 
 static int pick_bn(int kchunks, int k) {
-    if (k <= 128) return 128;
-    TcLayout L = tc_layout(256, kchunks, k);
-    return (L.NS >= 2) ? 256 : 128;
+    (void)kchunks;
+    (void)k;
+    return 128;  // four accumulators: each epilogue group double-buffered
 }
 
 // Asynchronous TMEM load (32 lanes x 32 columns) and the matching wait; the
@@ -96,6 +97,14 @@ KM_DEV void tmem_wait_ld(uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// 32 lanes x 4 consecutive columns, waited for.
+KM_DEV void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+}
+
 // Reliability test of one pair (rare path): tc form rho * B(x, c) or Alg. 2's
 // rho c_A gamma^l_{d+2} (||x~||^2 + ||c~||^2).
 __device__ __noinline__ bool pair_flagged(const TestParams& tp, const float4* cstat, int j, float dh, float a1,
@@ -108,24 +117,40 @@ __device__ __noinline__ bool pair_flagged(const TestParams& tp, const float4* cs
     return dh <= tp.paper_coef * (nxq * nxq + cs.z * cs.z);
 }
 
-// Candidate entry: column j (16 bits) and a 16-bit lower bound of d^ (the
-// top half of its fp32 encoding, one step further from zero if negative).
-KM_DEV uint32_t cand_entry(int j, float dh) {
-    const uint32_t b = __float_as_uint(dh);
-    uint32_t hi = b >> 16;
-    if ((b & 0x80000000u) && (b & 0xFFFFu)) hi += 1;
-    return ((uint32_t)j << 16) | hi;
+// Candidate entry: column j (16 bits) and the top 16 bits of d^'s fp32
+// encoding (d^ truncated toward zero to 8 significant bits); the true d^ lies
+// within |t| 2^-7 of the truncated value t.
+KM_DEV uint32_t cand_entry(int j, float dh) { return __byte_perm((uint32_t)j, __float_as_uint(dh), 0x1076); }
+KM_DEV float cand_dh_lower(uint32_t e) {
+    const float t = __uint_as_float(e << 16);
+    return t - fabsf(t) * (1.0f / 128.0f);
 }
-KM_DEV float cand_dh_lower(uint32_t e) { return __uint_as_float(e << 16); }
 
-// Keep only the list entries still inside the window (slot-major layout).
-__device__ __noinline__ int compact_list(uint32_t* list, int cnt, float lim) {
+// Keep only the list entries still inside the window (slot-major layout):
+// all slots are read first (independent loads), then packed with predicated
+// stores.
+KM_DEV int compact_list(uint32_t* list, int cnt, float lim) {
+    uint32_t c[TC_L];
+#pragma unroll
+    for (int r = 0; r < TC_L; r++) c[r] = list[r * TC_BM];
     int w = 0;
-    for (int r = 0; r < cnt; r++) {
-        const uint32_t c = list[r * TC_BM];
-        if (cand_dh_lower(c) <= lim) list[(w++) * TC_BM] = c;
+#pragma unroll
+    for (int r = 0; r < TC_L; r++) {
+        const bool keep = r < cnt && cand_dh_lower(c[r]) <= lim;
+        if (keep) list[w * TC_BM] = c[r];
+        w += keep ? 1 : 0;
     }
     return w;
+}
+
+// Two fp32 FMAs in one packed instruction.
+KM_DEV float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
+        "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
 }
 
 KM_DEV float fmin3(float a, float b, float c) {
@@ -144,16 +169,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char* sB = smem + (size_t)L.NA * L.a_bytes;
     float* qs = reinterpret_cast<float*>(smem + L.q_off);
     uint32_t* lists = reinterpret_cast<uint32_t*>(smem + L.list_off);
+    float2* mshare = reinterpret_cast<float2*>(smem + L.list_off + (size_t)2 * (TC_L + 1) * TC_BM * 4);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* a_full = bars;            // [2]
     uint64_t* a_empty = bars + 2;       // [2]
     uint64_t* b_full = bars + 4;        // [6]
     uint64_t* b_empty = bars + 10;      // [6]
-    uint64_t* acc_full = bars + 16;     // [2]
-    uint64_t* acc_empty = bars + 18;    // [2]
-    uint64_t* mma_done = bars + 20;     // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 22);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 23);
+    uint64_t* acc_full = bars + 16;     // [4]
+    uint64_t* acc_empty = bars + 20;    // [4]
+    uint64_t* mma_done = bars + 24;     // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 26);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 27);
+    // TMEM holds NBUF accumulators of BN columns (512 columns in all); tile t
+    // uses buffer t % NBUF and is drained by epilogue group t % 2, so each group
+    // owns NBUF / 2 buffers and the MMA can run ahead of both groups.
+    constexpr int NBUF = 512 / BN;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nrb = (a.n + TC_BM - 1) / TC_BM;
@@ -165,14 +195,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; i++) { mbar_init(&a_full[i], 1); mbar_init(&a_empty[i], 1); }
         for (int i = 0; i < 6; i++) { mbar_init(&b_full[i], 1); mbar_init(&b_empty[i], 1); }
-        for (int i = 0; i < 2; i++) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 4); }
+        for (int i = 0; i < NBUF; i++) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], 4); }
         mbar_init(mma_done, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
-    if (warp >= 2)  // q_j for every tile column (+inf on the padding: padded columns never win)
+    if (warp == 1) tmem_alloc(tmem_slot, 512);
+    if (warp >= 2) {  // q_j for every tile column (+inf on the padding: padded columns never win)
         for (int j = threadIdx.x - 64; j < NT * BN; j += TC_THREADS - 64) qs[j] = a.qpad[j];
+        for (int j = threadIdx.x - 64; j < 2 * TC_BM; j += TC_THREADS - 64)
+            mshare[j] = make_float2(INFINITY, __int_as_float(-1));
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -222,8 +255,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int s = (int)(bcons % L.NS);
                     ok = mbar_wait(&b_full[s], (bcons / L.NS) & 1, abort_flag, status);
                     if (!ok) break;
-                    const int accb = (int)(tcount & 1);
-                    if (tcount >= 2) ok = mbar_wait(&acc_empty[accb], ((tcount >> 1) - 1) & 1, abort_flag, status);
+                    const int accb = (int)(tcount % NBUF);
+                    if (tcount >= NBUF) ok = mbar_wait(&acc_empty[accb], ((tcount / NBUF) - 1) & 1, abort_flag, status);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t dt = tmem_base + (uint32_t)(accb * BN);
@@ -259,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int quarter = warp & 3;  // TMEM lanes this warp may access
         const int r_in = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        uint32_t* list = lists + (size_t)g * TC_L * TC_BM + r_in;  // slot s at list[s * TC_BM]
+        uint32_t* list = lists + (size_t)g * (TC_L + 1) * TC_BM + r_in;  // slot s at list[s * TC_BM]; slot TC_L is a dummy
         const ColMax cm = *a.colmax;
         const TestParams tp = a.tp;
         unsigned long long nflag_total = 0;
@@ -292,66 +325,127 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int nt = 0; nt < NT; nt++) {
                 const int64_t tc = (int64_t)iter * NT + nt;
                 if ((int)(tc & 1) != g) continue;
-                ok = mbar_wait(&acc_full[g], (uint32_t)((tc >> 1) & 1), abort_flag, status);
+                const int buf = (int)(tc % NBUF);
+                ok = mbar_wait(&acc_full[buf], (uint32_t)((tc / NBUF) & 1), abort_flag, status);
                 if (!ok) break;
                 tc_fence_after();
                 const int nch = min(BN / 32, (a.k - nt * BN + 31) / 32);
-                const uint32_t tbase = tmem_base + lane_addr + (uint32_t)(g * BN);
-                uint32_t ra[32];
-                __syncwarp();
-                tmem_ld32_async(tbase, ra);
-                tmem_wait_ld(ra);
-                auto process = [&](const uint32_t (&v)[32], int ch) {
-                    const int col0 = nt * BN + ch * 32;
-                    // q_j (+inf past k: padded columns never win); same address in all lanes
-                    const float4* q4 = reinterpret_cast<const float4*>(qs + col0);
-                    float e[32];
+                const uint32_t tbase = tmem_base + lane_addr + (uint32_t)(buf * BN);
+                if (MODE == 0) {
+                    // chunks are taken in pairs (64 columns): twice the independent work
+                    // per dependency chain, and the per-chunk fixed costs halve
+                    const int nch2 = (nch + 1) & ~1;  // padded columns have q = +inf: they never qualify
+                    for (int ch = 0; ch < nch2; ch += 2) {
+                        const int col0 = nt * BN + ch * 32;
+                        uint32_t va[32], vb[32];
+                        __syncwarp();
+                        tmem_ld32_async(tbase + (uint32_t)(ch * 32), va);
+                        tmem_ld32_async(tbase + (uint32_t)(ch * 32 + 32), vb);
+                        const float4* q4 = reinterpret_cast<const float4*>(qs + col0);
+                        float4 qv[16];
 #pragma unroll
-                    for (int t4 = 0; t4 < 8; t4++) {
-                        const float4 qq = q4[t4];
-                        e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]), neg2s, qq.x);
-                        e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]), neg2s, qq.y);
-                        e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]), neg2s, qq.z);
-                        e[4 * t4 + 3] = fmaf(__uint_as_float(v[4 * t4 + 3]), neg2s, qq.w);
-                    }
-                    if (MODE == 0) {
-                        // tree minimum; the four octet minima steer the slow path
-                        float om[4];
+                        for (int t4 = 0; t4 < 16; t4++) qv[t4] = q4[t4];
+                        const float2 mo = mshare[(g ^ 1) * TC_BM + r_in];
+                        tmem_wait_ld(va);
+                        tmem_wait_ld(vb);
+                        float e[64];
 #pragma unroll
-                        for (int o = 0; o < 4; o++) {
-                            const float m1 = fmin3(e[8 * o + 0], e[8 * o + 1], e[8 * o + 2]);
-                            const float m2 = fmin3(e[8 * o + 3], e[8 * o + 4], e[8 * o + 5]);
-                            om[o] = fmin3(m1, m2, fminf(e[8 * o + 6], e[8 * o + 7]));
+                        for (int t4 = 0; t4 < 16; t4++) {
+                            const uint32_t* v = (t4 < 8) ? va : vb;
+                            const int o = (t4 & 7) * 4;
+                            const float4 qq = qv[t4];
+                            const float2 lo = ffma2(make_float2(__uint_as_float(v[o + 0]), __uint_as_float(v[o + 1])),
+                                                    make_float2(neg2s, neg2s), make_float2(qq.x, qq.y));
+                            const float2 hi = ffma2(make_float2(__uint_as_float(v[o + 2]), __uint_as_float(v[o + 3])),
+                                                    make_float2(neg2s, neg2s), make_float2(qq.z, qq.w));
+                            e[4 * t4 + 0] = lo.x;
+                            e[4 * t4 + 1] = lo.y;
+                            e[4 * t4 + 2] = hi.x;
+                            e[4 * t4 + 3] = hi.y;
                         }
-                        const float cmin = fmin3(om[0], om[1], fminf(om[2], om[3]));
+                        // quad minima (they steer the slow path) and the minimum of the pair
+                        float qm[16];
+#pragma unroll
+                        for (int qd = 0; qd < 16; qd++)
+                            qm[qd] = fmin3(e[4 * qd + 0], e[4 * qd + 1], fminf(e[4 * qd + 2], e[4 * qd + 3]));
+                        float c4[4];
+#pragma unroll
+                        for (int i = 0; i < 4; i++) c4[i] = fmin3(qm[4 * i], qm[4 * i + 1], fminf(qm[4 * i + 2], qm[4 * i + 3]));
+                        const float cmin = fmin3(c4[0], c4[1], fminf(c4[2], c4[3]));
                         m = fminf(m, cmin);
-                        const float cthr = m + W;
+                        // publish this group's running minimum; use the other group's (read
+                        // before the TMEM wait): any upper bound of the row minimum keeps the
+                        // window a superset of the final one
+                        mshare[g * TC_BM + r_in] = make_float2(m, __int_as_float((int)rb));
+                        const float mm = (__float_as_int(mo.y) == (int)rb) ? fminf(m, mo.x) : m;
+                        const float cthr = mm + W;
                         const float sthr = valid ? fmaxf(cthr, Fe) : -INFINITY;
-                        // Warp-uniform control flow: an octet, then a column, is visited only
-                        // if some lane of the warp has a candidate or a possibly flagged pair
-                        // there; the per-lane work inside is predicated.
-                        if (__any_sync(0xffffffffu, cmin <= sthr)) {
+                        unsigned qmask = 0;
 #pragma unroll
-                            for (int o = 0; o < 4; o++) {
-                                if (!__any_sync(0xffffffffu, om[o] <= sthr)) continue;
-                                // room for a whole octet, else drop entries that left the window
-                                if (__any_sync(0xffffffffu, cnt > TC_L - 8 && !ovf))
-                                    if (cnt > TC_L - 8 && !ovf) cnt = compact_list(list, cnt, p + cthr);
+                        for (int qd = 0; qd < 16; qd++) qmask |= (qm[qd] <= sthr) ? (1u << qd) : 0u;
+                        // Slow path, warp-uniform: the union over the warp's lanes of the quads
+                        // holding a candidate or a possibly flagged pair is visited quad by quad;
+                        // each lane appends its own candidates with branch-free stores (a lane
+                        // with nothing to add writes the dummy slot).
+                        const unsigned U = __reduce_or_sync(0xffffffffu, qmask);
+                        if (U) {
+                            if (__any_sync(0xffffffffu, cnt > TC_L - 8 && !ovf)) {
+                                // every lane packs its list (dropping entries that left the window)
+                                const int cc = compact_list(list, cnt, p + cthr);
+                                if (!ovf) cnt = cc;
+                            }
+                            __syncwarp();
 #pragma unroll
-                                for (int q = 0; q < 8; q++) {
-                                    const float et = e[8 * o + q];
-                                    if (!__any_sync(0xffffffffu, et <= sthr)) continue;
-                                    const int j = col0 + 8 * o + q;
-                                    const float dh = p + et;
-                                    if (et <= cthr && !ovf) {
-                                        if (cnt < TC_L) list[(cnt++) * TC_BM] = cand_entry(j, dh);
-                                        else ovf = 1;
+                            for (int half = 0; half < 2; half++) {
+                                unsigned Uh = (U >> (8 * half)) & 0xffu;
+                                const float* eh = e + 32 * half;
+                                while (Uh) {
+                                    const int qd = __ffs(Uh) - 1;
+                                    Uh &= Uh - 1;
+                                    // the quad's four values, picked from registers by a select tree
+                                    const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
+#pragma unroll
+                                    for (int c = 0; c < 4; c++) {
+                                        const float s0 = b0 ? eh[4 + c] : eh[c], s1 = b0 ? eh[12 + c] : eh[8 + c];
+                                        const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
+                                        const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
+                                        const float et = b2 ? t1 : t0;
+                                        const bool pc = (et <= cthr) && !ovf;
+                                        const bool room = cnt < TC_L;
+                                        const int slot = (pc && room) ? cnt : TC_L;
+                                        list[slot * TC_BM] = cand_entry(col0 + 32 * half + 4 * qd + c, p + et);
+                                        ovf |= (pc && !room);
+                                        cnt += (pc && room) ? 1 : 0;
                                     }
-                                    if (dh <= F) nflag += pair_flagged(tp, a.cstat, j, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
+                                }
+                            }
+                            if (__any_sync(0xffffffffu, p + cmin <= F)) {
+#pragma unroll
+                                for (int t = 0; t < 64; t++) {
+                                    const float dh = p + e[t];
+                                    if (dh <= F) nflag += pair_flagged(tp, a.cstat, col0 + t, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
                                 }
                             }
                         }
-                    } else if (valid) {
+                    }
+                } else {
+                    for (int ch = 0; ch < nch; ch++) {
+                        const int col0 = nt * BN + ch * 32;
+                        uint32_t v[32];
+                        __syncwarp();
+                        tmem_ld32_async(tbase + (uint32_t)(ch * 32), v);
+                        tmem_wait_ld(v);
+                        if (!valid) continue;
+                        const float4* q4 = reinterpret_cast<const float4*>(qs + col0);
+                        float e[32];
+#pragma unroll
+                        for (int t4 = 0; t4 < 8; t4++) {
+                            const float4 qq = q4[t4];
+                            e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]), neg2s, qq.x);
+                            e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]), neg2s, qq.y);
+                            e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]), neg2s, qq.z);
+                            e[4 * t4 + 3] = fmaf(__uint_as_float(v[4 * t4 + 3]), neg2s, qq.w);
+                        }
                         // distance-matrix mode: Alg. 2's d = max(d^, 0) and its flag, every pair
                         float* drow = a.D + (size_t)row * a.k;
 #pragma unroll
@@ -372,19 +466,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 }
                             }
                         }
+                    
                     }
-                };
-                for (int ch = 0; ch < nch; ch++) {
-                    if (ch > 0) {
-                        __syncwarp();
-                        tmem_ld32_async(tbase + (uint32_t)(ch * 32), ra);
-                        tmem_wait_ld(ra);
-                    }
-                    process(ra, ch);
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[g]);
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
             }
             if (!ok) break;
             if (valid && MODE == 0) {
@@ -401,7 +488,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem_base, 2 * BN);
+    if (warp == 1) tmem_dealloc(tmem_base, 512);
 }
 
 // ----------------------------------------------------------------- host side
