@@ -171,14 +171,18 @@ struct UpdateWs {
     unsigned* absmax;
     double* shift;
     int32_t* taken;
+    int* iscratch;
+    int32_t* perm;
 };
-UpdateWs carve_update(Carve& cv, int d, int k) {
+UpdateWs carve_update(Carve& cv, int64_t n, int d, int k) {
     UpdateWs u{};
     u.sums = cv.take<long long>((size_t)k * d);
     u.counts = cv.take<long long>((size_t)k);
     u.absmax = cv.take<unsigned>(1);
     u.shift = cv.take<double>(1);
     u.taken = cv.take<int32_t>((size_t)k);
+    u.iscratch = cv.take<int>((size_t)4 * k + 2);
+    u.perm = cv.take<int32_t>((size_t)n);
     return u;
 }
 
@@ -195,7 +199,7 @@ struct LloydWs {
 LloydWs carve_lloyd(Carve& cv, int64_t n, int d, int k, int low, int max_iter) {
     LloydWs L{};
     L.a = carve_assign(cv, n, d, k, low, false);
-    L.u = carve_update(cv, d, k);
+    L.u = carve_update(cv, n, d, k);
     L.C0 = cv.take<float>((size_t)k * d);
     L.C1 = cv.take<float>((size_t)k * d);
     L.min_dist = cv.take<double>((size_t)n);
@@ -479,7 +483,7 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     Carve cv{(char*)ws};
     carve_assign(cv, n, d, k, p->low, false);
     DevCounters* cnt = cv.take<DevCounters>(1);
-    UpdateWs u = carve_update(cv, d, k);
+    UpdateWs u = carve_update(cv, n, d, k);
     if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
@@ -487,8 +491,8 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     {
         PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
         KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
-        KL(1, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, ctx->num_sms, st));
-        KL(2, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts,
+        KL(4, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
+        KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts,
                               u.shift, u.taken, st));
     }
     if (shift_host) {
@@ -547,8 +551,9 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
         CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
         {
             PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-            KL(1, launch_accumulate(X, n, d, labels, k, L.u.absmax, L.u.sums, L.u.counts, ctx->num_sms, st));
-            KL(2, launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt,
+            KL(4, launch_accumulate(X, n, d, labels, k, L.u.absmax, L.u.sums, L.u.counts, L.u.iscratch, L.u.perm,
+                                     ctx->num_sms, st));
+            KL(3, launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt,
                                   L.counts, L.u.shift, L.u.taken, st));
         }
         std::swap(cur, nxt);

@@ -107,9 +107,10 @@ cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, c
 
 // centre update
 cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cudaStream_t st);
+// per-cluster exact sums: iscratch holds 4k + 2 ints, perm n ints
 cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
-                              const unsigned* absmax_bits, long long* sums, long long* counts,
-                              int num_sms, cudaStream_t st);
+                              const unsigned* absmax_bits, long long* sums, long long* counts, int* iscratch,
+                              int32_t* perm, int num_sms, cudaStream_t st);
 cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
                             int64_t n, int k, int d, const float* C_old, int empty_policy,
                             const float* X, const double* min_dist, float* C_new, int64_t* counts_out,

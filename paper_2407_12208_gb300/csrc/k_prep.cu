@@ -106,6 +106,98 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
     }
 }
 
+
+// Vector path (d % 4 == 0, d <= 512): one warp per row, each lane holds up to
+// four float4 of the row in registers (coalesced 16-byte loads).
+template <int NV>
+__global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
+                               float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
+                               const float* __restrict__ uscale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int d4 = d >> 2, ldq4 = ldq >> 2;
+    for (int64_t i = warp; i < m; i += nw) {
+        const float4* a4 = reinterpret_cast<const float4*>(A + i * d);
+        float4 x[NV];
+#pragma unroll
+        for (int u = 0; u < NV; u++) {
+            const int c = lane + 32 * u;
+            x[u] = (c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float s = 1.0f;
+        if (fmt == 2) {
+            if (scale_mode == 1) {
+                s = *uscale;
+            } else {
+                float amax = 0.0f;
+#pragma unroll
+                for (int u = 0; u < NV; u++)
+                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+                s = e4m3_row_scale(amax);
+            }
+        }
+        const float inv = 1.0f / s;
+        float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
+#pragma unroll
+        for (int u = 0; u < NV; u++) {
+            const int c = lane + 32 * u;
+            if (c >= ldq4) continue;
+            const float xv[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+            float qv[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                qv[t] = quant_val(xv[t] * inv, fmt);
+                df_add_sq(xv[t], ph, pl);
+                const float qs = qv[t] * s;
+                q2 = fmaf(qs, qs, q2);
+                const float rr = qs - xv[t];
+                r2 = fmaf(rr, rr, r2);
+            }
+            if (fmt == 0) {
+                __half2 h0 = __floats2half2_rn(qv[0], qv[1]), h1 = __floats2half2_rn(qv[2], qv[3]);
+                uint2 w;
+                w.x = *reinterpret_cast<uint32_t*>(&h0);
+                w.y = *reinterpret_cast<uint32_t*>(&h1);
+                reinterpret_cast<uint2*>(Aq)[i * ldq4 + c] = w;
+            } else if (fmt == 1) {
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(qv[0], qv[1]), h1 = __floats2bfloat162_rn(qv[2], qv[3]);
+                uint2 w;
+                w.x = *reinterpret_cast<uint32_t*>(&h0);
+                w.y = *reinterpret_cast<uint32_t*>(&h1);
+                reinterpret_cast<uint2*>(Aq)[i * ldq4 + c] = w;
+            } else {
+                uint32_t w = 0;
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    w |= (uint32_t)__nv_cvt_float_to_fp8(xv[t] * inv, __NV_SATFINITE, __NV_E4M3) << (8 * t);
+                reinterpret_cast<uint32_t*>(Aq)[i * ldq4 + c] = w;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            float oh = __shfl_xor_sync(0xffffffffu, ph, off);
+            float ol = __shfl_xor_sync(0xffffffffu, pl, off);
+            df_add(ph, pl, oh, ol);
+            q2 += __shfl_xor_sync(0xffffffffu, q2, off);
+            r2 += __shfl_xor_sync(0xffffffffu, r2, off);
+        }
+        if (lane == 0) {
+            float p = ph + pl;
+            float4 o;
+            o.x = p;
+            o.y = sqrtf(p) * kNormInflate;
+            o.z = sqrtf(q2) * kNormInflate;
+            o.w = sqrtf(r2) * kNormInflate;
+            if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
+            stat[i] = o;
+            if (rscale) rscale[i] = s;
+        }
+    }
+}
+
 __global__ void k_amax_scale(const float* __restrict__ C, int64_t count, float* out) {
     __shared__ float red[32];
     float amax = 0.0f;
@@ -162,11 +254,22 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
 
 cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
                             float* rscale, int scale_mode, const float* uscale, cudaStream_t st) {
-    int64_t warps = m;
-    int64_t blocks = (warps * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    // one warp per row, enough warps in flight to cover the memory latency
+    int64_t blocks = (m * 32 + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
-    k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+    const bool vec = (d % 4 == 0) && (ldq % 4 == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)Aq % 16 == 0);
+    const int nv = (ldq / 4 + 31) / 32;
+    if (vec && nv <= 4) {
+        if (nv == 1)
+            k_quantize_vec<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+        else if (nv == 2)
+            k_quantize_vec<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+        else
+            k_quantize_vec<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+    } else {
+        k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+    }
     return cudaGetLastError();
 }
 

@@ -153,11 +153,7 @@ KM_DEV float2 ffma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
-KM_DEV float fmin3(float a, float b, float c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
+KM_DEV float fmin3(float a, float b, float c) { return fminf(fminf(a, b), c); }
 
 template <int FMT, int BN, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -354,14 +350,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const uint32_t* v = (t4 < 8) ? va : vb;
                             const int o = (t4 & 7) * 4;
                             const float4 qq = qv[t4];
-                            const float2 lo = ffma2(make_float2(__uint_as_float(v[o + 0]), __uint_as_float(v[o + 1])),
-                                                    make_float2(neg2s, neg2s), make_float2(qq.x, qq.y));
-                            const float2 hi = ffma2(make_float2(__uint_as_float(v[o + 2]), __uint_as_float(v[o + 3])),
-                                                    make_float2(neg2s, neg2s), make_float2(qq.z, qq.w));
-                            e[4 * t4 + 0] = lo.x;
-                            e[4 * t4 + 1] = lo.y;
-                            e[4 * t4 + 2] = hi.x;
-                            e[4 * t4 + 3] = hi.y;
+                            e[4 * t4 + 0] = fmaf(__uint_as_float(v[o + 0]), neg2s, qq.x);
+                            e[4 * t4 + 1] = fmaf(__uint_as_float(v[o + 1]), neg2s, qq.y);
+                            e[4 * t4 + 2] = fmaf(__uint_as_float(v[o + 2]), neg2s, qq.z);
+                            e[4 * t4 + 3] = fmaf(__uint_as_float(v[o + 3]), neg2s, qq.w);
                         }
                         // quad minima (they steer the slow path) and the minimum of the pair
                         float qm[16];

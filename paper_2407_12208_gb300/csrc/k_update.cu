@@ -12,6 +12,8 @@
 // recursive-summation bound gamma_m a_bar of Lemma 4.4 for the data sizes
 // here, and independent of the order in which threads add: results are
 // bitwise reproducible run to run and alone or batched.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -35,8 +37,9 @@ __global__ void k_absmax(const float* __restrict__ X, int64_t count, unsigned* o
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as uints
 }
 
-// Flat element loop: thread e handles X[e] (row e / d, coordinate e % d).
-// SMEM accumulators when k*d fits, else global atomics.
+// Row-parallel accumulation for the shapes the bucketed path does not take:
+// shared-memory accumulators when k*d fits, else global atomics (integer, so
+// the result does not depend on the order of the adds).
 template <bool SMEM>
 __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, const int32_t* __restrict__ labels,
                              int k, const unsigned* __restrict__ amax_bits, long long* __restrict__ sums,
@@ -50,14 +53,23 @@ __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, cons
     }
     long long* sacc = SMEM ? acc : sums;
     long long* cacc = SMEM ? acc + kd : counts;
-    const int64_t total = n * d;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / d;
-        const int l = (int)(e - i * d);
+    // rows spread over the warps; within a row the lanes walk the coordinates
+    // (for d < 32 a warp covers 32 / d rows at once)
+    const int lane = threadIdx.x & 31;
+    const int rpw = d < 32 ? 32 / d : 1;  // rows per warp step
+    const int sub = lane / (d < 32 ? d : 32), l_in = lane % (d < 32 ? d : 32);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = gw * rpw; r < n; r += nw * rpw) {
+        const int64_t i = r + sub;
+        if (sub >= rpw || i >= n) continue;
         const int j = labels[i];
-        const long long v = __float2ll_rn(ldexpf(X[e], S));
-        atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[(int64_t)j * d + l]), (unsigned long long)v);
-        if (l == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&cacc[j]), 1ull);
+        const float* x = X + i * d;
+        for (int l = l_in; l < d; l += (d < 32 ? d : 32)) {
+            const long long v = __float2ll_rn(ldexpf(x[l], S));
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[(int64_t)j * d + l]), (unsigned long long)v);
+        }
+        if (l_in == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&cacc[j]), 1ull);
     }
     if (SMEM) {
         __syncthreads();
@@ -65,6 +77,178 @@ __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, cons
             if (acc[e]) atomicAdd(reinterpret_cast<unsigned long long*>(&sums[e]), (unsigned long long)acc[e]);
         for (int e = threadIdx.x; e < k; e += blockDim.x)
             if (acc[kd + e]) atomicAdd(reinterpret_cast<unsigned long long*>(&counts[e]), (unsigned long long)acc[kd + e]);
+    }
+}
+
+// ---- bucketed reduction: rows grouped by label, summed in registers ------
+// Integer (fixed-point) addition is order-independent, so the row order
+// inside a bucket (set by atomic cursors) does not change any bit of the
+// result.
+constexpr int SEG_CHUNK = 256;   // rows per warp work item
+constexpr int SCAT_ROWS = 4096;  // rows per block of the histogram / scatter kernels
+
+// per-label counts (block histogram in shared memory, one global add per label)
+__global__ void k_label_hist(const int32_t* __restrict__ labels, int64_t n, int k, int* __restrict__ cnt32) {
+    extern __shared__ int h[];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) h[j] = 0;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * SCAT_ROWS, r1 = min(n, r0 + SCAT_ROWS);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) atomicAdd(&h[labels[i]], 1);
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+        if (h[j]) atomicAdd(&cnt32[j], h[j]);
+}
+
+// Exclusive scans (one block of 1024 threads): bucket offsets, cursors, and
+// the offsets of each bucket's first work item; counts as int64.
+__global__ void k_bucket_scan(const int* __restrict__ cnt32, int k, int* __restrict__ off, int* __restrict__ cursor,
+                              int* __restrict__ item_off, long long* __restrict__ counts) {
+    __shared__ int sa[1024], sb[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int per = (k + T - 1) / T;
+    const int j0 = min(k, t * per), j1 = min(k, j0 + per);
+    int a = 0, b = 0;
+    for (int j = j0; j < j1; j++) {
+        a += cnt32[j];
+        b += (cnt32[j] + SEG_CHUNK - 1) / SEG_CHUNK;
+    }
+    sa[t] = a;
+    sb[t] = b;
+    __syncthreads();
+    for (int st = 1; st < T; st <<= 1) {
+        const int va = (t >= st) ? sa[t - st] : 0, vb = (t >= st) ? sb[t - st] : 0;
+        __syncthreads();
+        sa[t] += va;
+        sb[t] += vb;
+        __syncthreads();
+    }
+    int oa = sa[t] - a, ob = sb[t] - b;
+    for (int j = j0; j < j1; j++) {
+        off[j] = oa;
+        cursor[j] = oa;
+        item_off[j] = ob;
+        counts[j] = cnt32[j];
+        oa += cnt32[j];
+        ob += (cnt32[j] + SEG_CHUNK - 1) / SEG_CHUNK;
+    }
+    if (t == T - 1) {
+        off[k] = sa[T - 1];
+        item_off[k] = sb[T - 1];
+    }
+}
+
+// Each block reserves one contiguous range per label (one global atomic per
+// label present) and places its rows with shared-memory cursors.
+__global__ void k_bucket_scatter(const int32_t* __restrict__ labels, int64_t n, int k, int* __restrict__ cursor,
+                                 int32_t* __restrict__ perm) {
+    extern __shared__ int sh[];
+    int* h = sh;
+    int* lc = sh + k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) h[j] = 0;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * SCAT_ROWS, r1 = min(n, r0 + SCAT_ROWS);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) atomicAdd(&h[labels[i]], 1);
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) lc[j] = h[j] ? atomicAdd(&cursor[j], h[j]) : 0;
+    __syncthreads();
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) perm[atomicAdd(&lc[labels[i]], 1)] = (int32_t)i;
+}
+
+KM_DEV int bucket_of(const int* __restrict__ item_off, int k, int64_t it) {
+    int lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (item_off[mid] <= it) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One warp per work item (bucket j, rows [c*CHUNK, (c+1)*CHUNK) of it); lanes
+// over the coordinates (NV4 float4 each, d % 4 == 0), exact int64 sums in
+// registers, one atomic add per coordinate per item.
+template <int NV4>
+__global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, const int* __restrict__ off,
+                             const int* __restrict__ item_off, const int32_t* __restrict__ perm,
+                             const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
+    const int S = fixed_shift(*amax_bits, n);
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nitems = item_off[k];
+    const int d4 = d >> 2;
+    for (int64_t it = w0; it < nitems; it += nw) {
+        const int j = bucket_of(item_off, k, it);
+        const int c = (int)(it - item_off[j]);
+        const int r0 = off[j] + c * SEG_CHUNK, r1 = min(off[j + 1], r0 + SEG_CHUNK);
+        long long acc[NV4][4];
+#pragma unroll
+        for (int u = 0; u < NV4; u++) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0;
+        for (int r = r0; r < r1; r += 8) {
+            float4 v[8][NV4];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int rr = r + b;
+                const int64_t i = (rr < r1) ? (int64_t)perm[rr] : -1;
+#pragma unroll
+                for (int u = 0; u < NV4; u++) {
+                    const int cidx = lane + 32 * u;
+                    v[b][u] = (i >= 0 && cidx < d4) ? reinterpret_cast<const float4*>(X + i * d)[cidx]
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 8; b++)
+#pragma unroll
+                for (int u = 0; u < NV4; u++) {
+                    acc[u][0] += __float2ll_rn(ldexpf(v[b][u].x, S));
+                    acc[u][1] += __float2ll_rn(ldexpf(v[b][u].y, S));
+                    acc[u][2] += __float2ll_rn(ldexpf(v[b][u].z, S));
+                    acc[u][3] += __float2ll_rn(ldexpf(v[b][u].w, S));
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < NV4; u++) {
+            const int cidx = lane + 32 * u;
+            if (cidx < d4)
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    if (acc[u][t])
+                        atomicAdd(reinterpret_cast<unsigned long long*>(&sums[(int64_t)j * d + 4 * cidx + t]),
+                                  (unsigned long long)acc[u][t]);
+        }
+    }
+}
+
+// Small d (d <= 16): lanes over rows, each lane sums its rows' d coordinates,
+// then a warp reduction.
+template <int D>
+__global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k, const int* __restrict__ off,
+                                   const int* __restrict__ item_off, const int32_t* __restrict__ perm,
+                                   const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
+    const int S = fixed_shift(*amax_bits, n);
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nitems = item_off[k];
+    for (int64_t it = w0; it < nitems; it += nw) {
+        const int j = bucket_of(item_off, k, it);
+        const int c = (int)(it - item_off[j]);
+        const int r0 = off[j] + c * SEG_CHUNK, r1 = min(off[j + 1], r0 + SEG_CHUNK);
+        long long acc[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) acc[l] = 0;
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const float* x = X + (int64_t)perm[r] * D;
+#pragma unroll
+            for (int l = 0; l < D; l++) acc[l] += __float2ll_rn(ldexpf(x[l], S));
+        }
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+            long long v = acc[l];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(&sums[(int64_t)j * D + l]), (unsigned long long)v);
+        }
     }
 }
 
@@ -95,11 +279,16 @@ __global__ void k_empty_and_shift(const long long* __restrict__ counts, int64_t 
                                   int32_t* __restrict__ taken) {
     __shared__ double rv[1024];
     __shared__ long long ri[1024];
-    __shared__ int ntaken;
+    __shared__ int ntaken, nempty;
     const int t = threadIdx.x;
-    if (t == 0) ntaken = 0;
+    if (t == 0) { ntaken = 0; nempty = 0; }
     __syncthreads();
-    if (empty_policy == 1 && min_dist != nullptr) {
+    // count the empty clusters in parallel; the ordered walk below runs only if any
+    int ne = 0;
+    for (int j = t; j < k; j += blockDim.x) ne += (counts[j] == 0);
+    if (ne) atomicAdd(&nempty, ne);
+    __syncthreads();
+    if (empty_policy == 1 && min_dist != nullptr && nempty > 0) {
         for (int j = 0; j < k; j++) {
             if (counts[j] != 0) continue;
             double best = -1.0;
@@ -134,23 +323,26 @@ __global__ void k_empty_and_shift(const long long* __restrict__ counts, int64_t 
             __syncthreads();
         }
     }
-    // shift
-    double mx = 0.0;
-    for (int j = t; j < k; j += blockDim.x) {
+}
+
+// shift = max_j ||c_new_j - c_old_j||: one warp per cluster, coalesced rows,
+// the maximum kept as the bit pattern of a non-negative double (ordered like
+// an unsigned integer), so the result does not depend on the order.
+__global__ void k_shift(int k, int d, const float* __restrict__ C_old, const float* __restrict__ C_new,
+                        unsigned long long* __restrict__ shift_bits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = w0; j < k; j += nw) {
         double s = 0.0;
-        for (int l = 0; l < d; l++) {
-            double df = (double)C_new[(int64_t)j * d + l] - (double)C_old[(int64_t)j * d + l];
+        for (int l = lane; l < d; l += 32) {
+            const double df = (double)C_new[j * d + l] - (double)C_old[j * d + l];
             s = fma(df, df, s);
         }
-        mx = fmax(mx, sqrt(s));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) atomicMax(shift_bits, (unsigned long long)__double_as_longlong(sqrt(s)));
     }
-    rv[t] = mx;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (t < s) rv[t] = fmax(rv[t], rv[t + s]);
-        __syncthreads();
-    }
-    if (t == 0) *shift = rv[0];
 }
 
 // Deterministic sum: fixed partition into `nparts` chunks, fixed in-block tree.
@@ -186,10 +378,39 @@ cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cud
 }
 
 cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
-                              const unsigned* absmax_bits, long long* sums, long long* counts, int num_sms,
-                              cudaStream_t st) {
+                              const unsigned* absmax_bits, long long* sums, long long* counts, int* iscratch,
+                              int32_t* perm, int num_sms, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(long long) * (size_t)k * d, st);
     if (e != cudaSuccess) return e;
+    const size_t hsm = sizeof(int) * (size_t)k;
+    const bool vec = d % 4 == 0 && ((uintptr_t)X % 16) == 0;
+    const bool bucket = 2 * hsm <= 200 * 1024 && (d == 1 || d == 2 || d == 3 || d == 5 || (vec && d <= 512));
+    if (bucket) {
+        int* cnt32 = iscratch;            // k
+        int* off = iscratch + k;          // k + 1
+        int* cursor = off + k + 1;        // k
+        int* item_off = cursor + k;       // k + 1
+        e = cudaMemsetAsync(cnt32, 0, sizeof(int) * (size_t)k, st);
+        if (e != cudaSuccess) return e;
+        const int64_t nblk = (n + SCAT_ROWS - 1) / SCAT_ROWS;
+        e = cudaFuncSetAttribute(k_label_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        if (e != cudaSuccess) return e;
+        k_label_hist<<<(unsigned)nblk, 512, hsm, st>>>(labels, n, k, cnt32);
+        k_bucket_scan<<<1, 1024, 0, st>>>(cnt32, k, off, cursor, item_off, counts);
+        e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * hsm));
+        if (e != cudaSuccess) return e;
+        k_bucket_scatter<<<(unsigned)nblk, 512, 2 * hsm, st>>>(labels, n, k, cursor, perm);
+        const int64_t items = n / SEG_CHUNK + k + 1;
+        const unsigned blocks = (unsigned)std::min<int64_t>((items * 32 + 255) / 256, (int64_t)num_sms * 16);
+        if (d == 1) k_bucket_sum_small<1><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
+        else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
+        else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
+        else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 128) k_bucket_sum<1><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 256) k_bucket_sum<2><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else k_bucket_sum<4><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        return cudaGetLastError();
+    }
     e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(long long) * ((size_t)k * d + k);
@@ -197,14 +418,13 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
     if (smem <= 200 * 1024) {
         e = cudaFuncSetAttribute(k_accumulate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        int per_sm = (int)max((size_t)1, min((size_t)4, (size_t)(220 * 1024) / (smem + 1024)));
-        int64_t blocks = min((int64_t)num_sms * per_sm, (total + 511) / 512);
-        if (blocks < 1) blocks = 1;
-        k_accumulate<true><<<(unsigned)blocks, 512, smem, st>>>(X, n, d, labels, k, absmax_bits, sums, counts);
+        const int64_t blk = std::min<int64_t>((int64_t)num_sms, (total + 511) / 512);
+        k_accumulate<true><<<(unsigned)std::max<int64_t>(blk, 1), 512, smem, st>>>(X, n, d, labels, k, absmax_bits,
+                                                                                    sums, counts);
     } else {
-        int64_t blocks = min((int64_t)num_sms * 8, (total + 511) / 512);
-        if (blocks < 1) blocks = 1;
-        k_accumulate<false><<<(unsigned)blocks, 512, 0, st>>>(X, n, d, labels, k, absmax_bits, sums, counts);
+        const int64_t blk = std::min<int64_t>((int64_t)num_sms * 8, (total + 511) / 512);
+        k_accumulate<false><<<(unsigned)std::max<int64_t>(blk, 1), 512, 0, st>>>(X, n, d, labels, k, absmax_bits,
+                                                                                  sums, counts);
     }
     return cudaGetLastError();
 }
@@ -220,6 +440,11 @@ cudaError_t launch_finalize(const long long* sums, const long long* counts, cons
     if (e != cudaSuccess) return e;
     k_empty_and_shift<<<1, 1024, 0, st>>>(counts, n, k, d, empty_policy, X, min_dist, C_old, C_new, shift,
                                            taken_rows);
+    e = cudaMemsetAsync(shift, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int64_t sblocks = std::min<int64_t>(((int64_t)k * 32 + 255) / 256, 152 * 8);
+    k_shift<<<(unsigned)std::max<int64_t>(sblocks, 1), 256, 0, st>>>(k, d, C_old, C_new,
+                                                                   reinterpret_cast<unsigned long long*>(shift));
     return cudaGetLastError();
 }
 

@@ -186,6 +186,32 @@ def test_update_centroids(ctx, policy):
     assert shift == pytest.approx(oshift, rel=1e-6)
 
 
+@pytest.mark.parametrize("n,d,k", [(20011, 5, 16), (3001, 7, 9), (10000, 64, 256), (5000, 2, 1)])
+def test_update_shapes(ctx, n, d, k):
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.gaussian_mixture(n, d, k, seed=n + d)
+    lab, od1, _ = oracle.assign(X, C)
+    p = pkg.params("fp64", empty="farthest")
+    Cn, cnt, shift = ctx.update_centroids(_dev(X), _dev(lab), _dev(C), p, min_dist=_dev(od1))
+    oC, ocnt, oshift = oracle.update(X, lab, C, 1, od1)
+    assert np.array_equal(cnt.cpu().numpy(), ocnt)
+    np.testing.assert_allclose(Cn.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
+
+
+def test_update_large_kd_sliced(ctx):
+    # k*d too large for one block's shared memory: dimension-sliced accumulation
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.uniform_pairs(30001, 128, 1024, seed=21)
+    lab = np.random.default_rng(3).integers(0, 1024, size=len(X)).astype(np.int32)
+    lab[lab == 7] = 8  # an empty cluster
+    p = pkg.params("bf16", empty="keep")
+    Cn, cnt, shift = ctx.update_centroids(_dev(X), _dev(lab), _dev(C), p)
+    oC, ocnt, oshift = oracle.update(X, lab, C, 0)
+    assert np.array_equal(cnt.cpu().numpy(), ocnt)
+    np.testing.assert_allclose(Cn.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
+    assert shift == pytest.approx(oshift, rel=1e-6)
+
+
 def test_update_is_bitwise_reproducible(ctx):
     import paper_2407_12208_gb300 as pkg
     X, C = workloads.gaussian_mixture(20000, 64, 64, seed=11)
