@@ -178,6 +178,36 @@ km_status km_get_phase_times(km_ctx* ctx, double* ms, int64_t* counts);
 /* Number of kernels this context has launched since km_init. */
 km_status km_get_launch_count(const km_ctx* ctx, uint64_t* launches);
 
+/* ---- assignment without allocation -------------------------------------- */
+
+/* The paper has no counterpart to this call.  It is km_assign with
+ * low = KM_FP32_DIRECT (the same kernels and the same results: fp32 direct
+ * distances certified by Theorem 4.1, binary64 for the rows whose argmin
+ * they leave open) for callers that cannot allocate device memory when they
+ * assign: a process whose device memory is all held by a caching pool or by
+ * another framework, where a cudaMalloc would fail, and latency-bound loops
+ * that must not call cudaMalloc/cudaFree (cudaFree can synchronise the whole
+ * device).  It takes no workspace.  Its scratch (the device counters and the
+ * list of rows left open, one int32 per row) is a file-scope device array of
+ * the library sized for KM_STATIC_MAX_ROWS rows: 4 MiB + 256 B per device.
+ *  - n > KM_STATIC_MAX_ROWS returns KM_ENOMEM before any launch; the other
+ *    argument errors are km_assign's (d <= 256 as on every direct path).
+ *  - labels (n int32) and min_dist (n doubles) are required device outputs.
+ *  - On success the call allocates nothing, host or device.  A rejected call
+ *    stores its message for km_last_error, as every call does.
+ *  - The first call on each device does one-time set-up: it resolves the
+ *    scratch address with cudaGetSymbolAddress, which may load the
+ *    library's device code.  Make that first call before any stream
+ *    capture begins.
+ *  - Each call clears the scratch counters on `stream` before its kernels.
+ *  - There is one scratch per device and process.  Calls whose work overlaps
+ *    in time on one device (other streams, threads or contexts) race on it
+ *    and give wrong results: order them on one stream or with events.
+ *  - km_get_stats and the phase timers do not report on this call. */
+#define KM_STATIC_MAX_ROWS 1048576
+km_status km_assign_static(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
+                           int32_t* labels, double* min_dist, void* stream);
+
 /* ---- serving (continuous batching on one GPU) ---------------------------- */
 
 /* A job: X (n x d) and C_init (k x d) are HOST pointers, copied into the

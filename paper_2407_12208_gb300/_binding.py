@@ -27,7 +27,8 @@ TEST_NAMES = {"tc": TEST_TC, "paper": TEST_PAPER, "off": TEST_OFF}
 EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_workspace_size",
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
-           "km_get_launch_count"]
+           "km_get_launch_count", "km_assign_static"]
+STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
 
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
         lib.km_poll.argtypes = [vp, c.c_uint64, c.POINTER(Result)]
         lib.km_release.argtypes = [vp, c.c_uint64]
         lib.km_cancel.argtypes = [vp, c.c_uint64]
+        lib.km_assign_static.argtypes = [vp, vp, i64, vp, i32, i32, vp, vp, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -191,6 +193,15 @@ class Context:
                                        _ptr(min_dist), ctypes.byref(nf) if want_flagged else None, _ptr(ws),
                                        ws.numel(), _stream(stream)))
         return labels, min_dist, (nf.value if want_flagged else None)
+
+    def assign_static(self, X, C, labels, min_dist, stream=None):
+        """km_assign_static: the fp32 direct assignment with the library's
+        static scratch (no workspace; the caller provides both outputs)."""
+        n, d = X.shape
+        k = C.shape[0]
+        self._check(self.lib.km_assign_static(self.h, _ptr(X), n, _ptr(C), k, d, _ptr(labels), _ptr(min_dist),
+                                              _stream(stream)))
+        return labels, min_dist
 
     def distances(self, X, C, p: Params, D=None, flag_bits=None, ws=None, stream=None):
         import torch

@@ -720,3 +720,62 @@ km_status km_internal_run_job(km_ctx_view* v, const float* X, int64_t n, int d, 
     }
     return s;
 }
+
+// ---- km_assign_static: the certified fp32 direct assignment with static scratch ----
+// For callers that cannot allocate device memory at assignment time (device
+// memory held by another pool, where cudaMalloc fails; loops that must not
+// pay for cudaMalloc/cudaFree, which can synchronise the device).  The
+// scratch is a file-scope device array: the counters in the first 256 bytes,
+// then the list of rows whose fp32 argmin stayed open.  There is one copy per
+// device, so calls that overlap in time on one device race on it.
+namespace {
+constexpr size_t kStaticCntBytes = 256;
+static_assert(sizeof(DevCounters) <= kStaticCntBytes, "counters exceed their slot");
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices];  // resolved scratch address per device, null until first use
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticCntBytes + (size_t)KM_STATIC_MAX_ROWS * sizeof(int32_t)];
+
+extern "C" km_status km_assign_static(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
+                                      int32_t* labels, double* min_dist, void* stream) {
+    km_status s = check_common(ctx, X, n, C, k, d);
+    if (s != KM_OK) return s;
+    if (!labels || !min_dist) return fail(ctx, KM_EINVAL, "km_assign_static needs labels and min_dist");
+    if (n > (int64_t)KM_STATIC_MAX_ROWS)
+        return fail(ctx, KM_ENOMEM, "km_assign_static: n=%lld exceeds its static scratch of %d rows (use km_assign)",
+                    (long long)n, KM_STATIC_MAX_ROWS);
+    km_params p;
+    km_default_params(&p);
+    p.low = KM_FP32_DIRECT;
+    if ((s = check_params(ctx, &p, d, k)) != KM_OK) return s;
+    if (ctx->device < 0 || ctx->device >= kStaticMaxDevices)
+        return fail(ctx, KM_EUNSUPPORTED, "km_assign_static: device %d out of range", ctx->device);
+    CK(cudaSetDevice(ctx->device));
+    void* base = nullptr;
+    {
+        // one-time set-up per device, with that device current
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_addr[ctx->device]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
+            if (e != cudaSuccess)
+                return fail(ctx, KM_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+            g_static_addr[ctx->device] = ptr;
+        }
+        base = g_static_addr[ctx->device];
+    }
+    DevCounters* cnt = reinterpret_cast<DevCounters*>(base);
+    int32_t* amb_list = reinterpret_cast<int32_t*>(static_cast<char*>(base) + kStaticCntBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    const TestParams tp = make_tp(&p, d);
+    // the counters (amb_count above all) must start at zero; the row list is
+    // written before it is read
+    CK(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), st));
+    KL(1, launch_direct_assign(false, X, n, C, k, d, nullptr, nullptr, labels, min_dist, amb_list, cnt, tp.gamma32,
+                               ctx->num_sms, st));
+    KL(1, launch_rows_full(false, X, C, k, d, amb_list, &cnt->amb_count, labels, min_dist, cnt, tp.gamma32,
+                           ctx->num_sms, st));
+    return KM_OK;
+}
