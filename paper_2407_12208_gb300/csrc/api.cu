@@ -62,7 +62,6 @@ struct PhaseScope {
 
 namespace {
 
-constexpr int kCandSlots = 24;  // per row and epilogue group of the screening kernel
 constexpr int kSumParts = 256;
 
 km_status fail(km_ctx* c, km_status s, const char* fmt, ...) {
@@ -125,6 +124,10 @@ struct AssignWs {
     float* cscale;
     float* qpad;
     uint32_t* cand;
+    int2* pairs;
+    float* v32;
+    int2* rowpair;
+    int64_t pair_cap;
     int4* rowinfo;
     int32_t* ovf_list;
     int32_t* amb_list;
@@ -156,7 +159,11 @@ AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distance
         w.rowinfo = cv.take<int4>((size_t)n * 2);
         w.ovf_list = cv.take<int32_t>((size_t)n);
         if (!distances) {
-            w.cand = cv.take<uint32_t>((size_t)n * 2 * kCandSlots);
+            w.cand = cv.take<uint32_t>((size_t)n * 2 * TC_LIST);
+            w.rowpair = cv.take<int2>((size_t)n);
+            w.pair_cap = std::min<int64_t>((int64_t)n * TC_PAIRS_PER_ROW, (int64_t)INT32_MAX);
+            w.pairs = cv.take<int2>((size_t)w.pair_cap);
+            w.v32 = cv.take<float>((size_t)w.pair_cap);
         } else {
             w.queue = cv.take<int2>((size_t)n * k);
             w.qlen = cv.take<unsigned long long>(1);
@@ -285,14 +292,16 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
     a.kchunks = (ldq * esz + 127) / 128;
     a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
-    a.tp = tp; a.mode = 0; a.L = kCandSlots; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    a.tp = tp; a.mode = 0; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    a.pairs = w.pairs; a.pair_cap = w.pair_cap; a.v32 = w.v32; a.rowpair = w.rowpair;
     {
         PhaseScope ps(ctx, KM_PHASE_SCREEN, st);
         KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
     }
     {
         PhaseScope ps(ctx, KM_PHASE_REFINE, st);
-        KL(1, launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st));
+        CK(cudaMemsetAsync(&w.cnt->npairs, 0, sizeof(unsigned long long), st));
+        KL(3, launch_refine(X, C, a, labels, min_dist, w.ovf_list, ctx->num_sms, st));
     }
     {
         // rows whose candidate list overflowed: full-row fp32 direct, binary64 where uncertified
@@ -452,7 +461,7 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
     a.kchunks = (ldq * esz + 127) / 128;
     a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
-    a.tp = make_tp(p, d); a.mode = 1; a.L = kCandSlots; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    a.tp = make_tp(p, d); a.mode = 1; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
     a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = n * (int64_t)k;
     a.flag_queue_len = w.qlen;
     KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));

@@ -6,6 +6,12 @@
 
 namespace km {
 
+// Candidate-list entries per row and epilogue group of the screening kernel.
+constexpr int TC_LIST = 24;
+// Candidate pairs reserved per row in the workspace; rows past the capacity
+// are recomputed by the full-row kernel.
+constexpr int TC_PAIRS_PER_ROW = 8;
+
 // Per-call device counters (lives in the workspace, zeroed per call).
 struct DevCounters {
     unsigned long long pairs;
@@ -18,6 +24,7 @@ struct DevCounters {
     int amb_count;       // length of the ambiguous-row list
     int ovf_count;       // length of the overflow-row list
     int pad;
+    unsigned long long npairs;  // candidate pairs written by the screening kernel
 };
 
 // Column-side constants of the reliability bound: maxima over centres.
@@ -82,9 +89,12 @@ struct TcArgs {
     const ColMax* colmax;
     TestParams tp;
     int mode;
-    int L;                    // candidate slots per row and epilogue group
-    uint32_t* cand;           // n x 2 x L entries: column j << 16 | 16-bit lower bound of d^
-    int4* rowinfo;            // n x 2: (count, overflow, nflag, d^min bits) per epilogue group
+    uint32_t* cand;           // mode 0: n x 2 x TC_LIST entries, column j << 16 | top 16 bits of d^
+    int4* rowinfo;            // n x 2: (count, overflow, window W bits, d^min bits) per epilogue group
+    int2* pairs;              // refinement: candidate pairs (row, j), each row's pairs contiguous
+    int64_t pair_cap;         // capacity of pairs / v32
+    float* v32;               // fp32 direct value of each pair
+    int2* rowpair;            // n: (offset, count) of the row's pairs, count -1: whole-row recompute
     float* D;                 // mode 1: n x k
     uint32_t* flag_bits;      // mode 1 (nullable)
     int2* flag_queue;         // mode 1: flagged pairs for the fp64 patch
@@ -96,10 +106,11 @@ cudaError_t launch_tc(const void* Xq, const void* Cq, int ldq, const TcArgs& a, 
                       cudaStream_t st);
 size_t tc_smem_bytes(int fmt, int d, int k);
 
-// candidate refinement (warp per row): certified argmin + min_dist
+// candidate refinement: fp32 direct values of the pairs, then certified
+// argmin + min_dist per row; rows left open are appended to full_list
+// (cnt->ovf_count) for the full-row kernel
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels,
-                          double* min_dist, int32_t* ovf_list, int32_t* amb_list, int num_sms,
-                          cudaStream_t st);
+                          double* min_dist, int32_t* full_list, int num_sms, cudaStream_t st);
 // fp64 direct values for flagged pairs of the distance matrix
 cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, const int2* queue,
                                  const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt,

@@ -1,19 +1,22 @@
 // k_refine.cu -- recompute by the direct formula (Section 4.3: from the
 // ORIGINAL data, Eq. (fallback-rule-mp)) and certified argmin.
 //
-// Per row (one warp), from the candidates the screening kernel kept:
-//  1. every candidate j has |d^_j - d_j| <= B_ij (the bound behind the
-//     reliability test), so only those with d^_j - B_ij <= min_l (d^_l + B_il)
-//     can be the nearest centre;
-//  2. those are evaluated by Eq. (dist-direct) in fp32 (lanes over the
-//     coordinates, shuffle reduction); Theorem 4.1 puts each true value in
-//     [v (1 - g), v (1 + g)], g = gamma_{d+2}(2^-24);
-//  3. if more than one fp32 interval can still hold the minimum, those
-//     candidates are evaluated in binary64 (products and sums rounded
-//     separately, coordinates in order: the oracle's own arithmetic) and the
-//     smallest wins, lowest index on ties.
-// The winner's direct value is min_dist.  Rows whose candidate list
-// overflowed are listed for the full-row direct kernel instead.
+// The screening kernel leaves, per row, lists of candidates, from which only
+// the j with d^_j <= d^_min + 2 B_max can still be the nearest centre, where
+// |d^_j - d_j| <= B_ij is the bound behind the reliability test (so no other
+// centre can win).  Those become a flat list of (row, j) pairs, each row's pairs
+// contiguous.
+//  0. k_cand_select: the pairs from the screening kernel's per-row lists
+//     (rowinfo[2 i + g] = (count, overflow, W, d^min) per epilogue group);
+//  1. k_pair_eval: Eq. (dist-direct) in fp32 for every pair, 8 lanes per pair
+//     and 4 pairs per warp (no per-row bookkeeping on this path);
+//  2. k_certify, one thread per row: Theorem 4.1 puts each true value in
+//     [v (1 - g), v (1 + g)], g = gamma_{d+2}(2^-24); when exactly one
+//     interval can hold the minimum, that centre is the argmin and v is
+//     min_dist; otherwise (near-ties) the open candidates are evaluated in
+//     binary64 (products and sums rounded separately, coordinates in order:
+//     the oracle's own arithmetic), lowest index on ties.  Overflowed rows
+//     are listed for the full-row kernel, which evaluates every centre.
 //
 // k_patch_flagged: binary64 direct values for the flagged pairs of the
 // distance matrix (Alg. 2's fallback branch).
@@ -24,318 +27,181 @@
 
 namespace km {
 
-// Candidate r of the row (r < cnt0 + cnt1) is held by lane r.
-KM_DEV void row_candidates(const TcArgs& a, int64_t row, int lane, int4 i0, int4 i1, int& j, float& lo, float& hi,
-                           const float4& xs) {
-    const TestParams& tp = a.tp;
-    const int cnt0 = i0.x, cnt = i0.x + i1.x;
-    const uint32_t c0 = (lane < a.L) ? a.cand[((size_t)row * 2) * a.L + lane] : 0u;
-    const uint32_t c1 = (lane < a.L) ? a.cand[((size_t)row * 2 + 1) * a.L + lane] : 0u;
-    const uint32_t c1s = __shfl_sync(0xffffffffu, c1, (lane - cnt0) & 31);
-    const uint32_t c = (lane < cnt0) ? c0 : c1s;
-    j = 0x7fffffff;
-    lo = INFINITY;
-    hi = INFINITY;
-    if (lane < cnt) {
-        j = (int)(c >> 16);
-        // the entry holds d^ truncated toward zero to 8 significant bits
-        const float t = __uint_as_float(c << 16);
-        const float dl = t - fabsf(t) * (1.0f / 128.0f);
-        const float du = t + fabsf(t) * (1.0f / 128.0f);
-        const float a1 = 2.0f * xs.w, a2 = 2.0f * xs.z, a3 = tp.kacc * xs.z;
-        const float4 cs = a.cstat[j];
-        const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (xs.x + cs.x)) * tp.bsafe;
-        lo = dl - B;
-        hi = du + B;
-    }
+// The entry holds d^ truncated toward zero to 8 significant bits: the true
+// d^ lies within |t| 2^-7 of the truncated value t.
+KM_DEV float cand_lower(uint32_t e) {
+    const float t = __uint_as_float(e << 16);
+    return t - fabsf(t) * (1.0f / 128.0f);
 }
 
-// Vector path: d % 4 == 0 and d <= 256, each lane holds up to two float4 of x.
+// fp32 direct values of the candidate pairs.  NV float4 of a row per lane
+// (lane l of a pair's 8 takes float4 l, l + 8, ...); NV == 0: scalar loads
+// for any d and alignment.
 template <int NV>
-__global__ void __launch_bounds__(256) k_refine_vec(const float* __restrict__ X, const float* __restrict__ C,
-                                                    const TcArgs a, int32_t* __restrict__ labels,
-                                                    double* __restrict__ min_dist, int32_t* __restrict__ ovf_list) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int d = a.d, d4 = d >> 2;
-    const TestParams tp = a.tp;
-    unsigned long long ev32 = 0, ev64 = 0, amb = 0, ovf_rows = 0;
-    for (int64_t row = warp; row < a.n; row += nw) {
-        // round 1: everything that does not depend on anything else
-        const int4 i0 = a.rowinfo[row * 2], i1 = a.rowinfo[row * 2 + 1];
-        const float4 xs = a.xstat[row];
-        const float4* x4 = reinterpret_cast<const float4*>(X + row * d);
-        float4 xv[NV];
-#pragma unroll
-        for (int u = 0; u < NV; u++) {
-            const int c = lane + 32 * u;
-            xv[u] = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const int cnt = i0.x + i1.x;
-        if ((i0.y | i1.y) || cnt > 32) {  // overflowed: whole-row direct evaluation elsewhere
-            if (lane == 0) {
-                int slot = atomicAdd(&a.cnt->ovf_count, 1);
-                ovf_list[slot] = (int32_t)row;
-                ovf_rows++;
-            }
-            continue;
-        }
-        // round 2: the candidates and their column statistics
-        int j;
-        float lo, hi;
-        row_candidates(a, row, lane, i0, i1, j, lo, hi, xs);
-        float U = hi;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) U = fminf(U, __shfl_xor_sync(0xffffffffu, U, off));
-        const unsigned surv = __ballot_sync(0xffffffffu, lane < cnt && lo <= U);
-        const int nsurv = __popc(surv);
-        // round 3: fp32 direct values of the survivors, eight centre rows in flight at a time
-        float v32 = INFINITY;
-        for (unsigned mrem = surv; mrem;) {
-            int rs[8];
-            float4 cv[8][NV];
-            int nb = 0;
-#pragma unroll
-            for (int b = 0; b < 8; b++) {
-                rs[b] = -1;
-                if (mrem) {
-                    const int r = __ffs(mrem) - 1;
-                    mrem &= mrem - 1;
-                    rs[b] = r;
-                    nb++;
-                    const int jr = __shfl_sync(0xffffffffu, j, r);
-                    const float4* c4 = reinterpret_cast<const float4*>(C + (int64_t)jr * d);
-#pragma unroll
-                    for (int u = 0; u < NV; u++) {
-                        const int c = lane + 32 * u;
-                        cv[b][u] = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < 8; b++) {
-                if (rs[b] < 0) break;
-                float sacc = 0.0f;
-#pragma unroll
-                for (int u = 0; u < NV; u++) {
-                    const float t0 = xv[u].x - cv[b][u].x, t1 = xv[u].y - cv[b][u].y;
-                    const float t2 = xv[u].z - cv[b][u].z, t3 = xv[u].w - cv[b][u].w;
-                    sacc = fmaf(t0, t0, sacc);
-                    sacc = fmaf(t1, t1, sacc);
-                    sacc = fmaf(t2, t2, sacc);
-                    sacc = fmaf(t3, t3, sacc);
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-                if (lane == rs[b]) v32 = sacc;
-            }
-            (void)nb;
-        }
-        ev32 += (unsigned long long)nsurv;
-        int win_j;
-        double win_d;
-        const bool in = (surv >> lane) & 1u;
-        if (nsurv == 1) {
-            const int r = __ffs(surv) - 1;
-            win_j = __shfl_sync(0xffffffffu, j, r);
-            win_d = (double)__shfl_sync(0xffffffffu, v32, r);
-        } else {
-            amb++;
-            const float g = tp.gamma32;
-            const float up = in ? v32 * (1.0f + g) : INFINITY;
-            float U2 = up;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) U2 = fminf(U2, __shfl_xor_sync(0xffffffffu, U2, off));
-            const unsigned s2 = __ballot_sync(0xffffffffu, in && v32 * (1.0f - g) <= U2);
-            if (__popc(s2) == 1) {
-                const int r = __ffs(s2) - 1;
-                win_j = __shfl_sync(0xffffffffu, j, r);
-                win_d = (double)__shfl_sync(0xffffffffu, v32, r);
-            } else {
-                // binary64, the oracle's arithmetic (products and sums rounded separately)
-                double v64 = INFINITY;
-                int jj = 0x7fffffff;
-                if ((s2 >> lane) & 1u) {
-                    const float* x = X + row * d;
-                    const float* c = C + (int64_t)j * d;
-                    double sacc = 0.0;
-                    for (int l = 0; l < d; l++) {
-                        const double t = __dsub_rn((double)x[l], (double)c[l]);
-                        sacc = __dadd_rn(sacc, __dmul_rn(t, t));
-                    }
-                    v64 = sacc;
-                    jj = j;
-                }
-                ev64 += (unsigned long long)__popc(s2);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, v64, off);
-                    const int oj = __shfl_xor_sync(0xffffffffu, jj, off);
-                    if (ov < v64 || (ov == v64 && oj < jj)) { v64 = ov; jj = oj; }
-                }
-                win_j = jj;
-                win_d = v64;
-            }
-        }
-        if (lane == 0) {
-            labels[row] = win_j;
-            min_dist[row] = win_d;
-        }
-    }
-    if (lane == 0) {
-        if (ev32) atomicAdd(&a.cnt->fp32_evals, ev32);
-        if (ev64) atomicAdd(&a.cnt->fp64_evals, ev64);
-        if (amb) atomicAdd(&a.cnt->amb_rows, amb);
-        if (ovf_rows) atomicAdd(&a.cnt->ovf_rows, ovf_rows);
-    }
-}
-
-
-// Group path: 8 lanes per row, 4 rows per warp (d % 4 == 0, d <= 256): the
-// reductions take 3 shuffle levels and serve 4 rows at once.  NV float4 of x
-// per lane (x holds d/4 float4: lane l of the group takes l, l+8, ...).
-template <int NV>
-__global__ void __launch_bounds__(256) k_refine_g8(const float* __restrict__ X, const float* __restrict__ C,
-                                                   const TcArgs a, int32_t* __restrict__ labels,
-                                                   double* __restrict__ min_dist, int32_t* __restrict__ ovf_list) {
-    constexpr int NS = 6;  // candidate slots per lane (48 per row at most)
+__global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, const float* __restrict__ C, int d,
+                                                   const int2* __restrict__ pairs,
+                                                   const unsigned long long* __restrict__ npairs, int64_t cap,
+                                                   float* __restrict__ v32) {
     const int lane = threadIdx.x & 31, sl = lane & 7, gbase = lane & ~7;
     const unsigned gmask = 0xFFu << gbase;
     const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane >> 3);
     const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * 4;
-    const int d = a.d, d4 = d >> 2;
-    const TestParams tp = a.tp;
-    unsigned long long ev32 = 0, ev64 = 0, amb = 0, ovf_rows = 0;
-    for (int64_t row = gid; row < a.n; row += ngroups) {
-        const int4 i0 = a.rowinfo[row * 2], i1 = a.rowinfo[row * 2 + 1];
-        const float4 xs = a.xstat[row];
-        const float4* x4 = reinterpret_cast<const float4*>(X + row * d);
-        float4 xv[NV];
+    const int64_t np = min((int64_t)*npairs, cap);
+    const int d4 = d >> 2;
+    for (int64_t pi = gid; pi < np; pi += ngroups) {
+        const int2 pr = pairs[pi];
+        float acc = 0.0f;
+        if (NV > 0) {
+            const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)pr.x * d);
+            const float4* c4 = reinterpret_cast<const float4*>(C + (int64_t)pr.y * d);
+            float4 xv[NV > 0 ? NV : 1], cv[NV > 0 ? NV : 1];
 #pragma unroll
-        for (int u = 0; u < NV; u++) {
-            const int c = sl + 8 * u;
-            xv[u] = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const int cnt0 = i0.x, cnt = i0.x + i1.x;
-        if ((i0.y | i1.y) || cnt > 8 * NS) {  // overflowed: whole-row direct evaluation elsewhere
-            if (sl == 0) {
-                int slot = atomicAdd(&a.cnt->ovf_count, 1);
-                ovf_list[slot] = (int32_t)row;
-                ovf_rows++;
+            for (int u = 0; u < NV; u++) {
+                const int c = sl + 8 * u;
+                xv[u] = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                cv[u] = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            continue;
-        }
-        const float a1 = 2.0f * xs.w, a2 = 2.0f * xs.z, a3 = tp.kacc * xs.z;
-        int jr[NS];
-        float lor[NS], hir[NS];
-        float myU = INFINITY;
 #pragma unroll
-        for (int r = 0; r < NS; r++) {
-            const int sidx = sl + 8 * r;
-            jr[r] = 0x7fffffff;
-            lor[r] = INFINITY;
-            hir[r] = INFINITY;
-            if (sidx < cnt) {
-                const uint32_t c = (sidx < cnt0) ? a.cand[((size_t)row * 2) * a.L + sidx]
-                                                 : a.cand[((size_t)row * 2 + 1) * a.L + (sidx - cnt0)];
-                const int j = (int)(c >> 16);
-                // the entry holds d^ truncated toward zero to 8 significant bits
-                const float t = __uint_as_float(c << 16);
-                const float4 cs = a.cstat[j];
-                const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (xs.x + cs.x)) * tp.bsafe;
-                jr[r] = j;
-                lor[r] = t - fabsf(t) * (1.0f / 128.0f) - B;
-                hir[r] = t + fabsf(t) * (1.0f / 128.0f) + B;
-                myU = fminf(myU, hir[r]);
-            }
-        }
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) myU = fminf(myU, __shfl_xor_sync(gmask, myU, off));
-        const float U = myU;
-        // fp32 direct values of the surviving candidates
-        float v32[NS];
-        int nsurv = 0;
-#pragma unroll
-        for (int r = 0; r < NS; r++) {
-            v32[r] = INFINITY;
-            unsigned b = (__ballot_sync(gmask, lor[r] <= U && jr[r] != 0x7fffffff) >> gbase) & 0xFFu;
-            nsurv += __popc(b);
-            while (b) {
-                const int owner = __ffs(b) - 1;
-                b &= b - 1;
-                const int j = __shfl_sync(gmask, jr[r], gbase + owner);
-                const float4* c4 = reinterpret_cast<const float4*>(C + (int64_t)j * d);
-                float acc = 0.0f;
-#pragma unroll
-                for (int u = 0; u < NV; u++) {
-                    const int c = sl + 8 * u;
-                    const float4 cv = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float t0 = xv[u].x - cv.x, t1 = xv[u].y - cv.y, t2 = xv[u].z - cv.z, t3 = xv[u].w - cv.w;
-                    acc = fmaf(t0, t0, acc);
-                    acc = fmaf(t1, t1, acc);
-                    acc = fmaf(t2, t2, acc);
-                    acc = fmaf(t3, t3, acc);
-                }
-#pragma unroll
-                for (int off = 4; off > 0; off >>= 1) acc += __shfl_xor_sync(gmask, acc, off);
-                if (sl == owner) v32[r] = acc;
-            }
-        }
-        ev32 += (sl == 0) ? (unsigned long long)nsurv : 0ull;
-        // certification by Theorem 4.1's intervals, binary64 where still open
-        const float g = tp.gamma32;
-        float up = INFINITY;
-#pragma unroll
-        for (int r = 0; r < NS; r++) up = fminf(up, v32[r] * (1.0f + g));
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) up = fminf(up, __shfl_xor_sync(gmask, up, off));
-        unsigned s2 = 0;
-#pragma unroll
-        for (int r = 0; r < NS; r++) s2 |= (v32[r] != INFINITY && v32[r] * (1.0f - g) <= up) ? (1u << r) : 0u;
-        int n2 = __popc(s2);
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) n2 += __shfl_xor_sync(gmask, n2, off);
-        double best = INFINITY;
-        int bj = 0x7fffffff;
-        if (n2 == 1) {
-            if (s2) {
-                const int r = __ffs(s2) - 1;
-                float vv = v32[0];
-                int jj = jr[0];
-#pragma unroll
-                for (int q = 1; q < NS; q++)
-                    if (q == r) { vv = v32[q]; jj = jr[q]; }
-                best = (double)vv;
-                bj = jj;
+            for (int u = 0; u < NV; u++) {
+                const float t0 = xv[u].x - cv[u].x, t1 = xv[u].y - cv[u].y;
+                const float t2 = xv[u].z - cv[u].z, t3 = xv[u].w - cv[u].w;
+                acc = fmaf(t0, t0, acc);
+                acc = fmaf(t1, t1, acc);
+                acc = fmaf(t2, t2, acc);
+                acc = fmaf(t3, t3, acc);
             }
         } else {
-            if (sl == 0) amb++;
-            const float* x = X + row * d;
-#pragma unroll
-            for (int r = 0; r < NS; r++) {
-                if ((s2 >> r) & 1u) {
-                    const float* c = C + (int64_t)jr[r] * d;
-                    double sacc = 0.0;
-                    for (int l = 0; l < d; l++) {
-                        const double t = __dsub_rn((double)x[l], (double)c[l]);
-                        sacc = __dadd_rn(sacc, __dmul_rn(t, t));
-                    }
-                    ev64++;
-                    if (sacc < best || (sacc == best && jr[r] < bj)) { best = sacc; bj = jr[r]; }
-                }
+            const float* x = X + (int64_t)pr.x * d;
+            const float* c = C + (int64_t)pr.y * d;
+            for (int l = sl; l < d; l += 8) {
+                const float t = x[l] - c[l];
+                acc = fmaf(t, t, acc);
             }
         }
 #pragma unroll
-        for (int off = 4; off > 0; off >>= 1) {
-            const double ob = __shfl_xor_sync(gmask, best, off);
-            const int oj = __shfl_xor_sync(gmask, bj, off);
-            if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        for (int off = 4; off > 0; off >>= 1) acc += __shfl_xor_sync(gmask, acc, off);
+        if (sl == 0) v32[pi] = acc;
+    }
+}
+
+// Candidate selection, one thread per row: the entries of both epilogue
+// groups' lists inside the window of the row's final d^ minimum (the smaller
+// of the two groups' minima), written out as (row, j) pairs, contiguous per
+// row, one atomic reservation per warp.  Rows whose list overflowed, or that
+// no longer fit in the pair buffer, get count -1 (whole-row recompute).
+__global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ rowinfo,
+                                                     const uint32_t* __restrict__ cand, int64_t n,
+                                                     int2* __restrict__ pairs, int64_t cap,
+                                                     int2* __restrict__ rowpair, DevCounters* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = w0 * 32; r0 < n; r0 += nw * 32) {
+        const int64_t row = r0 + lane;
+        const bool valid = row < n;
+        int c = 0;
+        bool full = false;
+        int4 i0 = make_int4(0, 0, 0, 0), i1 = i0;
+        float lim = 0.0f;
+        const uint32_t* c0 = cand + (size_t)row * 2 * TC_LIST;
+        const uint32_t* c1 = c0 + TC_LIST;
+        if (valid) {
+            i0 = rowinfo[row * 2];
+            i1 = rowinfo[row * 2 + 1];
+            full = (i0.y | i1.y) != 0;
+            lim = fminf(__int_as_float(i0.w), __int_as_float(i1.w)) + __int_as_float(i0.z);
+            if (!full) {
+                for (int s = 0; s < i0.x; s++) c += (cand_lower(c0[s]) <= lim) ? 1 : 0;
+                for (int s = 0; s < i1.x; s++) c += (cand_lower(c1[s]) <= lim) ? 1 : 0;
+            }
         }
-        if (sl == 0) {
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && total) base = atomicAdd(&cnt->npairs, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        const int64_t off0 = (int64_t)base + incl - c;
+        const bool fits = off0 + c <= cap;
+        if (valid) {
+            if (!full && fits) {
+                int w = 0;
+                for (int s = 0; s < i0.x; s++) {
+                    const uint32_t e = c0[s];
+                    if (cand_lower(e) <= lim) pairs[off0 + w++] = make_int2((int)row, (int)(e >> 16));
+                }
+                for (int s = 0; s < i1.x; s++) {
+                    const uint32_t e = c1[s];
+                    if (cand_lower(e) <= lim) pairs[off0 + w++] = make_int2((int)row, (int)(e >> 16));
+                }
+            }
+            rowpair[row] = make_int2(fits ? (int)off0 : 0, (full || !fits) ? -1 : c);
+        }
+    }
+}
+
+// Certification, one thread per row, by Theorem 4.1's intervals: the winner's
+// fp32 value and index; where more than one interval can hold the minimum,
+// those candidates in binary64 (the oracle's arithmetic), lowest index on
+// ties.  Rows with count -1 go on full_list for the full-row kernel.
+__global__ void __launch_bounds__(256) k_certify(const int2* __restrict__ rowpair, int64_t n,
+                                                 const int2* __restrict__ pairs, const float* __restrict__ v32,
+                                                 const float* __restrict__ X, const float* __restrict__ C, int d,
+                                                 float gamma32, int32_t* __restrict__ labels,
+                                                 double* __restrict__ min_dist, int32_t* __restrict__ full_list,
+                                                 DevCounters* cnt) {
+    unsigned long long ev32 = 0, ev64 = 0, amb = 0, ovf_rows = 0;
+    const float g = gamma32;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int2 rp = rowpair[row];
+        if (rp.y < 0) {
+            ovf_rows++;
+            const int slot = atomicAdd(&cnt->ovf_count, 1);
+            full_list[slot] = (int32_t)row;
+            continue;
+        }
+        float up = INFINITY;
+        for (int r = 0; r < rp.y; r++) up = fminf(up, v32[rp.x + r] * (1.0f + g));
+        int open = 0, bj = 0x7fffffff;
+        float bv = INFINITY;
+        for (int r = 0; r < rp.y; r++) {
+            const float v = v32[rp.x + r];
+            if (v * (1.0f - g) <= up) {
+                open++;
+                const int j = pairs[rp.x + r].y;
+                if (v < bv || (v == bv && j < bj)) { bv = v; bj = j; }
+            }
+        }
+        ev32 += (unsigned long long)rp.y;
+        if (open == 1) {
             labels[row] = bj;
-            min_dist[row] = best;
+            min_dist[row] = (double)bv;
+            continue;
         }
+        amb++;
+        const float* x = X + row * d;
+        double best = INFINITY;
+        bj = 0x7fffffff;
+        for (int r = 0; r < rp.y; r++) {
+            if (v32[rp.x + r] * (1.0f - g) <= up) {
+                const int j = pairs[rp.x + r].y;
+                const float* c = C + (int64_t)j * d;
+                double sacc = 0.0;
+                for (int l = 0; l < d; l++) {
+                    const double t = __dsub_rn((double)x[l], (double)c[l]);
+                    sacc = __dadd_rn(sacc, __dmul_rn(t, t));
+                }
+                ev64++;
+                if (sacc < best || (sacc == best && j < bj)) { best = sacc; bj = j; }
+            }
+        }
+        labels[row] = bj;
+        min_dist[row] = best;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -344,113 +210,11 @@ __global__ void __launch_bounds__(256) k_refine_g8(const float* __restrict__ X, 
         amb += __shfl_xor_sync(0xffffffffu, amb, off);
         ovf_rows += __shfl_xor_sync(0xffffffffu, ovf_rows, off);
     }
-    if (lane == 0) {
-        if (ev32) atomicAdd(&a.cnt->fp32_evals, ev32);
-        if (ev64) atomicAdd(&a.cnt->fp64_evals, ev64);
-        if (amb) atomicAdd(&a.cnt->amb_rows, amb);
-        if (ovf_rows) atomicAdd(&a.cnt->ovf_rows, ovf_rows);
-    }
-}
-
-// General path (any d): warp per row, lanes over the coordinates.
-__global__ void k_refine(const float* __restrict__ X, const float* __restrict__ C, const TcArgs a,
-                         int32_t* __restrict__ labels, double* __restrict__ min_dist, int32_t* __restrict__ ovf_list) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int d = a.d;
-    const TestParams tp = a.tp;
-    unsigned long long ev32 = 0, ev64 = 0, amb = 0, ovf_rows = 0;
-    for (int64_t row = warp; row < a.n; row += nw) {
-        const int4 i0 = a.rowinfo[row * 2], i1 = a.rowinfo[row * 2 + 1];
-        const int cnt = i0.x + i1.x;
-        if ((i0.y | i1.y) || cnt > 32) {
-            if (lane == 0) {
-                int slot = atomicAdd(&a.cnt->ovf_count, 1);
-                ovf_list[slot] = (int32_t)row;
-                ovf_rows++;
-            }
-            continue;
-        }
-        const float4 xs = a.xstat[row];
-        int j;
-        float lo, hi;
-        row_candidates(a, row, lane, i0, i1, j, lo, hi, xs);
-        float U = hi;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) U = fminf(U, __shfl_xor_sync(0xffffffffu, U, off));
-        unsigned surv = __ballot_sync(0xffffffffu, lane < cnt && lo <= U);
-        const int nsurv = __popc(surv);
-        // fp32 direct values of the survivors (warp-cooperative)
-        float v32 = INFINITY;
-        const float* x = X + row * d;
-        for (unsigned m = surv; m; m &= m - 1) {
-            const int r = __ffs(m) - 1;
-            const int jr = __shfl_sync(0xffffffffu, j, r);
-            const float* c = C + (int64_t)jr * d;
-            float s = 0.0f;
-            for (int l = lane; l < d; l += 32) {
-                const float t = x[l] - c[l];
-                s = fmaf(t, t, s);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == r) v32 = s;
-        }
-        ev32 += (unsigned long long)nsurv;
-        int win_j;
-        double win_d;
-        const bool in = (surv >> lane) & 1u;
-        if (nsurv == 1) {
-            const int r = __ffs(surv) - 1;
-            win_j = __shfl_sync(0xffffffffu, j, r);
-            win_d = (double)__shfl_sync(0xffffffffu, v32, r);
-        } else {
-            amb++;
-            const float g = tp.gamma32;
-            const float up = in ? v32 * (1.0f + g) : INFINITY;
-            float U2 = up;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) U2 = fminf(U2, __shfl_xor_sync(0xffffffffu, U2, off));
-            const unsigned s2 = __ballot_sync(0xffffffffu, in && v32 * (1.0f - g) <= U2);
-            if (__popc(s2) == 1) {
-                const int r = __ffs(s2) - 1;
-                win_j = __shfl_sync(0xffffffffu, j, r);
-                win_d = (double)__shfl_sync(0xffffffffu, v32, r);
-            } else {
-                double v64 = INFINITY;
-                int jj = 0x7fffffff;
-                if ((s2 >> lane) & 1u) {
-                    const float* c = C + (int64_t)j * d;
-                    double s = 0.0;
-                    for (int l = 0; l < d; l++) {
-                        const double t = __dsub_rn((double)x[l], (double)c[l]);
-                        s = __dadd_rn(s, __dmul_rn(t, t));
-                    }
-                    v64 = s;
-                    jj = j;
-                }
-                ev64 += (unsigned long long)__popc(s2);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, v64, off);
-                    const int oj = __shfl_xor_sync(0xffffffffu, jj, off);
-                    if (ov < v64 || (ov == v64 && oj < jj)) { v64 = ov; jj = oj; }
-                }
-                win_j = jj;
-                win_d = v64;
-            }
-        }
-        if (lane == 0) {
-            labels[row] = win_j;
-            min_dist[row] = win_d;
-        }
-    }
-    if (lane == 0) {
-        if (ev32) atomicAdd(&a.cnt->fp32_evals, ev32);
-        if (ev64) atomicAdd(&a.cnt->fp64_evals, ev64);
-        if (amb) atomicAdd(&a.cnt->amb_rows, amb);
-        if (ovf_rows) atomicAdd(&a.cnt->ovf_rows, ovf_rows);
+    if ((threadIdx.x & 31) == 0) {
+        if (ev32) atomicAdd(&cnt->fp32_evals, ev32);
+        if (ev64) atomicAdd(&cnt->fp64_evals, ev64);
+        if (amb) atomicAdd(&cnt->amb_rows, amb);
+        if (ovf_rows) atomicAdd(&cnt->ovf_rows, ovf_rows);
     }
 }
 
@@ -477,17 +241,29 @@ __global__ void k_patch_flagged(const float* __restrict__ X, const float* __rest
 }
 
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels, double* min_dist,
-                          int32_t* ovf_list, int32_t* /*amb_list*/, int num_sms, cudaStream_t st) {
-    int64_t warps = std::min<int64_t>(a.n, (int64_t)num_sms * 64);
-    int64_t blocks = (warps * 32 + 255) / 256;
-    if (blocks < 1) blocks = 1;
+                          int32_t* full_list, int num_sms, cudaStream_t st) {
+    const int64_t rb = std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, (int64_t)num_sms * 8));
+    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.pairs, a.pair_cap, a.rowpair, a.cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // pair evaluation: a persistent grid of the resident blocks
     const bool vec = (a.d % 4 == 0) && a.d <= 256 && ((uintptr_t)X % 16 == 0) && ((uintptr_t)C % 16 == 0);
-    if (vec && a.d <= 128)
-        k_refine_g8<4><<<(unsigned)blocks, 256, 0, st>>>(X, C, a, labels, min_dist, ovf_list);
-    else if (vec)
-        k_refine_g8<8><<<(unsigned)blocks, 256, 0, st>>>(X, C, a, labels, min_dist, ovf_list);
-    else
-        k_refine<<<(unsigned)blocks, 256, 0, st>>>(X, C, a, labels, min_dist, ovf_list);
+    const void* fn = !vec ? (const void*)k_pair_eval<0>
+                          : (a.d <= 32 ? (const void*)k_pair_eval<1>
+                                       : (a.d <= 128 ? (const void*)k_pair_eval<4> : (const void*)k_pair_eval<8>));
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)num_sms * (unsigned)std::max(per_sm, 1);
+    const unsigned long long* np = &a.cnt->npairs;
+    if (!vec) k_pair_eval<0><<<blocks, 256, 0, st>>>(X, C, a.d, a.pairs, np, a.pair_cap, a.v32);
+    else if (a.d <= 32) k_pair_eval<1><<<blocks, 256, 0, st>>>(X, C, a.d, a.pairs, np, a.pair_cap, a.v32);
+    else if (a.d <= 128) k_pair_eval<4><<<blocks, 256, 0, st>>>(X, C, a.d, a.pairs, np, a.pair_cap, a.v32);
+    else k_pair_eval<8><<<blocks, 256, 0, st>>>(X, C, a.d, a.pairs, np, a.pair_cap, a.v32);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_certify<<<(unsigned)rb, 256, 0, st>>>(a.rowpair, a.n, a.pairs, a.v32, X, C, a.d, a.tp.gamma32, labels, min_dist,
+                                             full_list, a.cnt);
     return cudaGetLastError();
 }
 

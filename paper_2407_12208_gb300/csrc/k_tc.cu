@@ -32,12 +32,12 @@ namespace km {
 
 constexpr int TC_THREADS = 320;
 constexpr int TC_BM = 128;
-constexpr int TC_L = 24;  // candidate slots per row and epilogue group
+constexpr int TC_L = TC_LIST;  // candidate slots per row and epilogue group
 constexpr int SMEM_BUDGET = 227 * 1024;
 
 struct TcLayout {
     int BN, NA, NS, kchunks;
-    size_t a_bytes, b_bytes, q_off, list_off, bar_off, total;
+    size_t a_bytes, b_bytes, list_off, bar_off, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
@@ -46,11 +46,10 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     L.kchunks = kchunks;
     L.a_bytes = (size_t)kchunks * TC_BM * 128;
     L.b_bytes = (size_t)kchunks * BN * 128;
-    const int nt = (k + BN - 1) / BN;
-    const size_t qbytes = (((size_t)nt * BN * 4) + 255) & ~(size_t)255;  // q_j of every column, +inf padded
+    (void)k;
     const size_t lists = (size_t)2 * (TC_L + 1) * TC_BM * 4   // per-row candidate lists (+1 dummy slot) of both groups
                          + (size_t)2 * TC_BM * 8;         // per-row running minimum published by each group
-    const size_t fixed = 1024 /*align slack*/ + qbytes + lists + 256 /*barriers*/;
+    const size_t fixed = 1024 /*align slack*/ + lists + 256 /*barriers*/;
     L.NA = 2;
     size_t rem = (size_t)SMEM_BUDGET - fixed - 2 * L.a_bytes;
     if ((long long)rem < (long long)(2 * L.b_bytes)) {
@@ -59,8 +58,7 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     }
     L.NS = (int)(rem / L.b_bytes);
     if (L.NS > 6) L.NS = 6;
-    L.q_off = (size_t)L.NA * L.a_bytes + (size_t)L.NS * L.b_bytes;
-    L.list_off = L.q_off + qbytes;
+    L.list_off = (size_t)L.NA * L.a_bytes + (size_t)L.NS * L.b_bytes;
     L.bar_off = L.list_off + lists;
     L.total = L.bar_off + 256 + 1024;
     return L;
@@ -143,17 +141,12 @@ KM_DEV int compact_list(uint32_t* list, int cnt, float lim) {
     return w;
 }
 
-// Two fp32 FMAs in one packed instruction.
-KM_DEV float2 ffma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
-        "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
+// Three-input minimum (one instruction on sm_100 and later; no NaN reaches it).
+KM_DEV float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
-
-KM_DEV float fmin3(float a, float b, float c) { return fminf(fminf(a, b), c); }
 
 template <int FMT, int BN, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -163,7 +156,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const TcLayout L = tc_layout(BN, a.kchunks, a.k);
     unsigned char* sA = smem;
     unsigned char* sB = smem + (size_t)L.NA * L.a_bytes;
-    float* qs = reinterpret_cast<float*>(smem + L.q_off);
+    // q_j of every tile column (+inf on the padding: padded columns never win),
+    // read through the read-only cache: one broadcast load per float4
+    const float* __restrict__ qg = a.qpad;
     uint32_t* lists = reinterpret_cast<uint32_t*>(smem + L.list_off);
     float2* mshare = reinterpret_cast<float2*>(smem + L.list_off + (size_t)2 * (TC_L + 1) * TC_BM * 4);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
@@ -197,8 +192,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         fence_barrier_init();
     }
     if (warp == 1) tmem_alloc(tmem_slot, 512);
-    if (warp >= 2) {  // q_j for every tile column (+inf on the padding: padded columns never win)
-        for (int j = threadIdx.x - 64; j < NT * BN; j += TC_THREADS - 64) qs[j] = a.qpad[j];
+    if (warp >= 2) {
         for (int j = threadIdx.x - 64; j < 2 * TC_BM; j += TC_THREADS - 64)
             mshare[j] = make_float2(INFINITY, __int_as_float(-1));
     }
@@ -337,33 +331,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         __syncwarp();
                         tmem_ld32_async(tbase + (uint32_t)(ch * 32), va);
                         tmem_ld32_async(tbase + (uint32_t)(ch * 32 + 32), vb);
-                        const float4* q4 = reinterpret_cast<const float4*>(qs + col0);
+                        const float4* q4 = reinterpret_cast<const float4*>(qg + col0);
                         float4 qv[16];
 #pragma unroll
-                        for (int t4 = 0; t4 < 16; t4++) qv[t4] = q4[t4];
+                        for (int t4 = 0; t4 < 16; t4++) qv[t4] = __ldg(q4 + t4);
                         const float2 mo = mshare[(g ^ 1) * TC_BM + r_in];
                         tmem_wait_ld(va);
                         tmem_wait_ld(vb);
+                        // e = q_j - 2 s g, two columns per packed FMA (each rounded as fmaf)
                         float e[64];
+                        const float2 n2 = make_float2(neg2s, neg2s);
 #pragma unroll
                         for (int t4 = 0; t4 < 16; t4++) {
                             const uint32_t* v = (t4 < 8) ? va : vb;
                             const int o = (t4 & 7) * 4;
                             const float4 qq = qv[t4];
-                            e[4 * t4 + 0] = fmaf(__uint_as_float(v[o + 0]), neg2s, qq.x);
-                            e[4 * t4 + 1] = fmaf(__uint_as_float(v[o + 1]), neg2s, qq.y);
-                            e[4 * t4 + 2] = fmaf(__uint_as_float(v[o + 2]), neg2s, qq.z);
-                            e[4 * t4 + 3] = fmaf(__uint_as_float(v[o + 3]), neg2s, qq.w);
+                            const float2 lo = __ffma2_rn(make_float2(__uint_as_float(v[o + 0]), __uint_as_float(v[o + 1])), n2,
+                                                         make_float2(qq.x, qq.y));
+                            const float2 hi = __ffma2_rn(make_float2(__uint_as_float(v[o + 2]), __uint_as_float(v[o + 3])), n2,
+                                                         make_float2(qq.z, qq.w));
+                            e[4 * t4 + 0] = lo.x;
+                            e[4 * t4 + 1] = lo.y;
+                            e[4 * t4 + 2] = hi.x;
+                            e[4 * t4 + 3] = hi.y;
                         }
                         // quad minima (they steer the slow path) and the minimum of the pair
                         float qm[16];
 #pragma unroll
                         for (int qd = 0; qd < 16; qd++)
-                            qm[qd] = fmin3(e[4 * qd + 0], e[4 * qd + 1], fminf(e[4 * qd + 2], e[4 * qd + 3]));
+                            qm[qd] = fminf(fmin3(e[4 * qd + 0], e[4 * qd + 1], e[4 * qd + 2]), e[4 * qd + 3]);
                         float c4[4];
 #pragma unroll
-                        for (int i = 0; i < 4; i++) c4[i] = fmin3(qm[4 * i], qm[4 * i + 1], fminf(qm[4 * i + 2], qm[4 * i + 3]));
-                        const float cmin = fmin3(c4[0], c4[1], fminf(c4[2], c4[3]));
+                        for (int i = 0; i < 4; i++) c4[i] = fminf(fmin3(qm[4 * i], qm[4 * i + 1], qm[4 * i + 2]), qm[4 * i + 3]);
+                        const float cmin = fminf(fmin3(c4[0], c4[1], c4[2]), c4[3]);
                         m = fminf(m, cmin);
                         // publish this group's running minimum; use the other group's (read
                         // before the TMEM wait): any upper bound of the row minimum keeps the
@@ -375,12 +375,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         unsigned qmask = 0;
 #pragma unroll
                         for (int qd = 0; qd < 16; qd++) qmask |= (qm[qd] <= sthr) ? (1u << qd) : 0u;
-                        // Slow path, warp-uniform: the union over the warp's lanes of the quads
-                        // holding a candidate or a possibly flagged pair is visited quad by quad;
-                        // each lane appends its own candidates with branch-free stores (a lane
-                        // with nothing to add writes the dummy slot).
-                        const unsigned U = __reduce_or_sync(0xffffffffu, qmask);
-                        if (U) {
+                        // Slow path: each lane walks its own quads holding a candidate or a
+                        // possibly flagged pair (the warp iterates as often as its busiest
+                        // lane); the quad's values are picked from registers by a select tree
+                        // on the lane's own quad index, and the appends are branch-free stores
+                        // (a lane with nothing to add writes the dummy slot).
+                        if (__any_sync(0xffffffffu, qmask)) {
                             if (__any_sync(0xffffffffu, cnt > TC_L - 8 && !ovf)) {
                                 // every lane packs its list (dropping entries that left the window)
                                 const int cc = compact_list(list, cnt, p + cthr);
@@ -389,12 +389,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             __syncwarp();
 #pragma unroll
                             for (int half = 0; half < 2; half++) {
-                                unsigned Uh = (U >> (8 * half)) & 0xffu;
+                                unsigned ph = (qmask >> (8 * half)) & 0xffu;
                                 const float* eh = e + 32 * half;
-                                while (Uh) {
-                                    const int qd = __ffs(Uh) - 1;
-                                    Uh &= Uh - 1;
-                                    // the quad's four values, picked from registers by a select tree
+                                while (__any_sync(0xffffffffu, ph)) {
+                                    const bool act = ph != 0;
+                                    const int qd = act ? __ffs(ph) - 1 : 0;
+                                    ph &= ph - 1;
                                     const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
 #pragma unroll
                                     for (int c = 0; c < 4; c++) {
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
                                         const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
                                         const float et = b2 ? t1 : t0;
-                                        const bool pc = (et <= cthr) && !ovf;
+                                        const bool pc = act && (et <= cthr) && !ovf;
                                         const bool room = cnt < TC_L;
                                         const int slot = (pc && room) ? cnt : TC_L;
                                         list[slot * TC_BM] = cand_entry(col0 + 32 * half + 4 * qd + c, p + et);
@@ -428,11 +428,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tmem_ld32_async(tbase + (uint32_t)(ch * 32), v);
                         tmem_wait_ld(v);
                         if (!valid) continue;
-                        const float4* q4 = reinterpret_cast<const float4*>(qs + col0);
+                        const float4* q4 = reinterpret_cast<const float4*>(qg + col0);
                         float e[32];
 #pragma unroll
                         for (int t4 = 0; t4 < 8; t4++) {
-                            const float4 qq = q4[t4];
+                            const float4 qq = __ldg(q4 + t4);
                             e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]), neg2s, qq.x);
                             e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]), neg2s, qq.y);
                             e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]), neg2s, qq.z);
@@ -467,9 +467,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (!ok) break;
             if (valid && MODE == 0) {
+                // the row's list, its window W and this group's d^ minimum
                 uint32_t* crow = a.cand + ((size_t)row * 2 + g) * TC_L;
                 for (int sl = 0; sl < cnt; sl++) crow[sl] = list[sl * TC_BM];
-                a.rowinfo[row * 2 + g] = make_int4(cnt, ovf, nflag, __float_as_int(p + m));
+                a.rowinfo[row * 2 + g] = make_int4(cnt, ovf, __float_as_int(W), __float_as_int(p + m));
             }
             nflag_total += (unsigned long long)nflag;
         }

@@ -28,6 +28,21 @@ KM_DEV int fixed_shift(unsigned amax_bits, int64_t n) {
     return 60 - lgn - E;  // |sum| 2^S < 2^(lgn + E + 1 + S) = 2^61
 }
 
+// v 2^S rounded to the nearest integer.  S lies in [-98, 209]; the scaling
+// is split into two power-of-two factors, each a normal float, and both
+// products are exact whenever the result is a normal float (|v 2^S| < 2^61
+// never overflows); when it is not, |v 2^S| < 2^-126 and the integer is 0
+// either way.  Same integers as rounding ldexpf(v, S).
+struct FixedScale {
+    float f1, f2;
+    KM_DEV explicit FixedScale(int S) {
+        const int s1 = S / 2, s2 = S - s1;
+        f1 = __int_as_float((s1 + 127) << 23);
+        f2 = __int_as_float((s2 + 127) << 23);
+    }
+    KM_DEV long long operator()(float v) const { return __float2ll_rn(__fmul_rn(__fmul_rn(v, f1), f2)); }
+};
+
 __global__ void k_absmax(const float* __restrict__ X, int64_t count, unsigned* out) {
     float m = 0.0f;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
@@ -45,7 +60,7 @@ __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, cons
                              int k, const unsigned* __restrict__ amax_bits, long long* __restrict__ sums,
                              long long* __restrict__ counts) {
     extern __shared__ long long acc[];
-    const int S = fixed_shift(*amax_bits, n);
+    const FixedScale fx(fixed_shift(*amax_bits, n));
     const int64_t kd = (int64_t)k * d;
     if (SMEM) {
         for (int64_t e = threadIdx.x; e < kd + k; e += blockDim.x) acc[e] = 0;
@@ -66,7 +81,7 @@ __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, cons
         const int j = labels[i];
         const float* x = X + i * d;
         for (int l = l_in; l < d; l += (d < 32 ? d : 32)) {
-            const long long v = __float2ll_rn(ldexpf(x[l], S));
+            const long long v = fx(x[l]);
             atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[(int64_t)j * d + l]), (unsigned long long)v);
         }
         if (l_in == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&cacc[j]), 1ull);
@@ -84,7 +99,7 @@ __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, cons
 // Integer (fixed-point) addition is order-independent, so the row order
 // inside a bucket (set by atomic cursors) does not change any bit of the
 // result.
-constexpr int SEG_CHUNK = 256;   // rows per warp work item
+constexpr int SEG_CHUNK = 64;    // rows per warp work item
 constexpr int SCAT_ROWS = 4096;  // rows per block of the histogram / scatter kernels
 
 // per-label counts (block histogram in shared memory, one global add per label)
@@ -170,7 +185,8 @@ template <int NV4>
 __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, const int* __restrict__ off,
                              const int* __restrict__ item_off, const int32_t* __restrict__ perm,
                              const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
-    const int S = fixed_shift(*amax_bits, n);
+    constexpr int RB = 16 / NV4;  // rows in flight per lane
+    const FixedScale fx(fixed_shift(*amax_bits, n));
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -183,28 +199,32 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
         long long acc[NV4][4];
 #pragma unroll
         for (int u = 0; u < NV4; u++) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0;
-        for (int r = r0; r < r1; r += 8) {
-            float4 v[8][NV4];
+        for (int base = r0; base < r1; base += 32) {
+            // the row indices of 32 rows in one coalesced load, then broadcast
+            const int64_t my_i = (base + lane < r1) ? (int64_t)perm[base + lane] : -1;
+#pragma unroll 1
+            for (int b0 = 0; b0 < 32 && base + b0 < r1; b0 += RB) {
+                float4 v[RB][NV4];
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const int rr = r + b;
-                const int64_t i = (rr < r1) ? (int64_t)perm[rr] : -1;
+                for (int b = 0; b < RB; b++) {
+                    const int64_t i = __shfl_sync(0xffffffffu, my_i, b0 + b);
 #pragma unroll
-                for (int u = 0; u < NV4; u++) {
-                    const int cidx = lane + 32 * u;
-                    v[b][u] = (i >= 0 && cidx < d4) ? reinterpret_cast<const float4*>(X + i * d)[cidx]
-                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int u = 0; u < NV4; u++) {
+                        const int cidx = lane + 32 * u;
+                        v[b][u] = (i >= 0 && cidx < d4) ? reinterpret_cast<const float4*>(X + i * d)[cidx]
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
+#pragma unroll
+                for (int b = 0; b < RB; b++)
+#pragma unroll
+                    for (int u = 0; u < NV4; u++) {
+                        acc[u][0] += fx(v[b][u].x);
+                        acc[u][1] += fx(v[b][u].y);
+                        acc[u][2] += fx(v[b][u].z);
+                        acc[u][3] += fx(v[b][u].w);
+                    }
             }
-#pragma unroll
-            for (int b = 0; b < 8; b++)
-#pragma unroll
-                for (int u = 0; u < NV4; u++) {
-                    acc[u][0] += __float2ll_rn(ldexpf(v[b][u].x, S));
-                    acc[u][1] += __float2ll_rn(ldexpf(v[b][u].y, S));
-                    acc[u][2] += __float2ll_rn(ldexpf(v[b][u].z, S));
-                    acc[u][3] += __float2ll_rn(ldexpf(v[b][u].w, S));
-                }
         }
 #pragma unroll
         for (int u = 0; u < NV4; u++) {
@@ -225,7 +245,7 @@ template <int D>
 __global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k, const int* __restrict__ off,
                                    const int* __restrict__ item_off, const int32_t* __restrict__ perm,
                                    const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
-    const int S = fixed_shift(*amax_bits, n);
+    const FixedScale fx(fixed_shift(*amax_bits, n));
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -240,7 +260,7 @@ __global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k
         for (int r = r0 + lane; r < r1; r += 32) {
             const float* x = X + (int64_t)perm[r] * D;
 #pragma unroll
-            for (int l = 0; l < D; l++) acc[l] += __float2ll_rn(ldexpf(x[l], S));
+            for (int l = 0; l < D; l++) acc[l] += fx(x[l]);
         }
 #pragma unroll
         for (int l = 0; l < D; l++) {
@@ -400,8 +420,20 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * hsm));
         if (e != cudaSuccess) return e;
         k_bucket_scatter<<<(unsigned)nblk, 512, 2 * hsm, st>>>(labels, n, k, cursor, perm);
+        // persistent grid: every block resident at once (a partial second wave
+        // would leave SMs idle), the items strided over the warps
         const int64_t items = n / SEG_CHUNK + k + 1;
-        const unsigned blocks = (unsigned)std::min<int64_t>((items * 32 + 255) / 256, (int64_t)num_sms * 16);
+        int per_sm = 1;
+        if (d > 5) {
+            const void* fn = d <= 128 ? (const void*)k_bucket_sum<1> : d <= 256 ? (const void*)k_bucket_sum<2>
+                                                                                 : (const void*)k_bucket_sum<4>;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+            if (e != cudaSuccess) return e;
+        } else {
+            per_sm = 8;
+        }
+        const unsigned blocks =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>((items * 32 + 255) / 256, (int64_t)num_sms * std::max(per_sm, 1)));
         if (d == 1) k_bucket_sum_small<1><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
         else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
         else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
