@@ -301,7 +301,7 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     {
         PhaseScope ps(ctx, KM_PHASE_REFINE, st);
         CK(cudaMemsetAsync(&w.cnt->npairs, 0, sizeof(unsigned long long), st));
-        KL(3, launch_refine(X, C, a, labels, min_dist, w.ovf_list, ctx->num_sms, st));
+        KL(4, launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st));
     }
     {
         // rows whose candidate list overflowed: full-row fp32 direct, binary64 where uncertified

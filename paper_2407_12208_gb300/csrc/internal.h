@@ -89,7 +89,7 @@ struct TcArgs {
     const ColMax* colmax;
     TestParams tp;
     int mode;
-    uint32_t* cand;           // mode 0: n x 2 x TC_LIST entries, column j << 16 | top 16 bits of d^
+    uint32_t* cand;           // mode 0: 2 x TC_LIST x n entries (group, slot, row), column j << 16 | top 16 bits of d^
     int4* rowinfo;            // n x 2: (count, overflow, window W bits, d^min bits) per epilogue group
     int2* pairs;              // refinement: candidate pairs (row, j), each row's pairs contiguous
     int64_t pair_cap;         // capacity of pairs / v32
@@ -110,7 +110,7 @@ size_t tc_smem_bytes(int fmt, int d, int k);
 // argmin + min_dist per row; rows left open are appended to full_list
 // (cnt->ovf_count) for the full-row kernel
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels,
-                          double* min_dist, int32_t* full_list, int num_sms, cudaStream_t st);
+                          double* min_dist, int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st);
 // fp64 direct values for flagged pairs of the distance matrix
 cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, const int2* queue,
                                  const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt,

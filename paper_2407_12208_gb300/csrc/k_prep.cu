@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -106,6 +108,101 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
     }
 }
 
+
+// Group path (d % 4 == 0, padded width <= 256): 8 lanes per row, 4 rows per
+// warp, so the row reductions take 3 shuffle levels and serve 4 rows at once.
+// Lane l of a row's 8 holds float4 l, l + 8, ... (NV of them).
+template <int NV>
+__global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
+                              float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
+                              const float* __restrict__ uscale) {
+    const int lane = threadIdx.x & 31, sl = lane & 7;
+    const unsigned gmask = 0xFFu << (lane & ~7);
+    const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane >> 3);
+    const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * 4;
+    const int d4 = d >> 2, ldq4 = ldq >> 2;
+    for (int64_t i = gid; i < m; i += ngroups) {
+        const float4* a4 = reinterpret_cast<const float4*>(A + i * d);
+        float4 x[NV];
+#pragma unroll
+        for (int u = 0; u < NV; u++) {
+            const int c = sl + 8 * u;
+            x[u] = (c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float s = 1.0f;
+        if (fmt == 2) {
+            if (scale_mode == 1) {
+                s = *uscale;
+            } else {
+                float amax = 0.0f;
+#pragma unroll
+                for (int u = 0; u < NV; u++)
+                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
+#pragma unroll
+                for (int off = 4; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(gmask, amax, off));
+                s = e4m3_row_scale(amax);
+            }
+        }
+        const float inv = 1.0f / s;
+        float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
+#pragma unroll
+        for (int u = 0; u < NV; u++) {
+            const int c = sl + 8 * u;
+            if (c >= ldq4) continue;
+            const float xv[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+            float qv[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                qv[t] = quant_val(xv[t] * inv, fmt);
+                df_add_sq(xv[t], ph, pl);
+                const float qs = qv[t] * s;
+                q2 = fmaf(qs, qs, q2);
+                const float rr = qs - xv[t];
+                r2 = fmaf(rr, rr, r2);
+            }
+            if (fmt == 0) {
+                __half2 h0 = __floats2half2_rn(qv[0], qv[1]), h1 = __floats2half2_rn(qv[2], qv[3]);
+                uint2 w;
+                w.x = *reinterpret_cast<uint32_t*>(&h0);
+                w.y = *reinterpret_cast<uint32_t*>(&h1);
+                reinterpret_cast<uint2*>(Aq)[i * ldq4 + c] = w;
+            } else if (fmt == 1) {
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(qv[0], qv[1]), h1 = __floats2bfloat162_rn(qv[2], qv[3]);
+                uint2 w;
+                w.x = *reinterpret_cast<uint32_t*>(&h0);
+                w.y = *reinterpret_cast<uint32_t*>(&h1);
+                reinterpret_cast<uint2*>(Aq)[i * ldq4 + c] = w;
+            } else {
+                uint32_t w = 0;
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    w |= (uint32_t)__nv_cvt_float_to_fp8(xv[t] * inv, __NV_SATFINITE, __NV_E4M3) << (8 * t);
+                reinterpret_cast<uint32_t*>(Aq)[i * ldq4 + c] = w;
+            }
+        }
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+            float oh = __shfl_xor_sync(gmask, ph, off);
+            float ol = __shfl_xor_sync(gmask, pl, off);
+            df_add(ph, pl, oh, ol);
+            q2 += __shfl_xor_sync(gmask, q2, off);
+            r2 += __shfl_xor_sync(gmask, r2, off);
+        }
+        if (sl == 0) {
+            float p = ph + pl;
+            float4 o;
+            o.x = p;
+            o.y = sqrtf(p) * kNormInflate;
+            o.z = sqrtf(q2) * kNormInflate;
+            o.w = sqrtf(r2) * kNormInflate;
+            // an element that overflowed the low format makes the row unusable
+            // for the expanded formula: an infinite bound flags all its pairs
+            if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
+            stat[i] = o;
+            if (rscale) rscale[i] = s;
+        }
+    }
+}
 
 // Vector path (d % 4 == 0, d <= 512): one warp per row, each lane holds up to
 // four float4 of the row in registers (coalesced 16-byte loads).
@@ -260,7 +357,18 @@ cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, 
     if (blocks < 1) blocks = 1;
     const bool vec = (d % 4 == 0) && (ldq % 4 == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)Aq % 16 == 0);
     const int nv = (ldq / 4 + 31) / 32;
-    if (vec && nv <= 4) {
+    const int nv8 = (ldq / 4 + 7) / 8;
+    if (vec && nv8 <= 8) {
+        blocks = std::min<int64_t>(std::max<int64_t>(1, (m * 8 + 255) / 256), (int64_t)152 * 16);
+        if (nv8 <= 1)
+            k_quantize_g8<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+        else if (nv8 <= 2)
+            k_quantize_g8<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+        else if (nv8 <= 4)
+            k_quantize_g8<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+        else
+            k_quantize_g8<8><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+    } else if (vec && nv <= 4) {
         if (nv == 1)
             k_quantize_vec<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
         else if (nv == 2)

@@ -42,27 +42,30 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
                                                    const int2* __restrict__ pairs,
                                                    const unsigned long long* __restrict__ npairs, int64_t cap,
                                                    float* __restrict__ v32) {
+    constexpr int NVV = NV > 0 ? NV : 1;
     const int lane = threadIdx.x & 31, sl = lane & 7, gbase = lane & ~7;
     const unsigned gmask = 0xFFu << gbase;
     const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane >> 3);
     const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * 4;
     const int64_t np = min((int64_t)*npairs, cap);
     const int d4 = d >> 2;
+    int2 nxt = (gid < np) ? pairs[gid] : make_int2(0, 0);
     for (int64_t pi = gid; pi < np; pi += ngroups) {
-        const int2 pr = pairs[pi];
+        const int2 pr = nxt;
+        if (pi + ngroups < np) nxt = pairs[pi + ngroups];  // the next pair's index, ahead of its use
         float acc = 0.0f;
         if (NV > 0) {
             const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)pr.x * d);
             const float4* c4 = reinterpret_cast<const float4*>(C + (int64_t)pr.y * d);
-            float4 xv[NV > 0 ? NV : 1], cv[NV > 0 ? NV : 1];
+            float4 xv[NVV], cv[NVV];
 #pragma unroll
-            for (int u = 0; u < NV; u++) {
+            for (int u = 0; u < NVV; u++) {
                 const int c = sl + 8 * u;
                 xv[u] = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
                 cv[u] = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < NV; u++) {
+            for (int u = 0; u < NVV; u++) {
                 const float t0 = xv[u].x - cv[u].x, t1 = xv[u].y - cv[u].y;
                 const float t2 = xv[u].z - cv[u].z, t3 = xv[u].w - cv[u].w;
                 acc = fmaf(t0, t0, acc);
@@ -103,18 +106,33 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
         bool full = false;
         int4 i0 = make_int4(0, 0, 0, 0), i1 = i0;
         float lim = 0.0f;
-        const uint32_t* c0 = cand + (size_t)row * 2 * TC_LIST;
-        const uint32_t* c1 = c0 + TC_LIST;
+        // slot s of group g at cand[(g * TC_LIST + s) * n + row]: a warp reads 32 rows side by side
+        const uint32_t* c0 = cand + row;
+        const uint32_t* c1 = c0 + (size_t)TC_LIST * n;
+        unsigned m0 = 0, m1 = 0;  // entries inside the window
         if (valid) {
             i0 = rowinfo[row * 2];
             i1 = rowinfo[row * 2 + 1];
             full = (i0.y | i1.y) != 0;
             lim = fminf(__int_as_float(i0.w), __int_as_float(i1.w)) + __int_as_float(i0.z);
-            if (!full) {
-                for (int s = 0; s < i0.x; s++) c += (cand_lower(c0[s]) <= lim) ? 1 : 0;
-                for (int s = 0; s < i1.x; s++) c += (cand_lower(c1[s]) <= lim) ? 1 : 0;
-            }
         }
+        const int n0 = full ? 0 : i0.x, n1 = full ? 0 : i1.x;
+        // the first 8 slots of both lists in one round of loads, the rest (rare) after
+        constexpr int SPEC = 8;
+        uint32_t e0[SPEC], e1[SPEC];
+#pragma unroll
+        for (int s = 0; s < SPEC; s++) {
+            e0[s] = (s < n0) ? c0[(size_t)s * n] : 0u;
+            e1[s] = (s < n1) ? c1[(size_t)s * n] : 0u;
+        }
+#pragma unroll
+        for (int s = 0; s < SPEC; s++) {
+            m0 |= (s < n0 && cand_lower(e0[s]) <= lim) ? (1u << s) : 0u;
+            m1 |= (s < n1 && cand_lower(e1[s]) <= lim) ? (1u << s) : 0u;
+        }
+        for (int s = SPEC; s < n0; s++) m0 |= (cand_lower(c0[(size_t)s * n]) <= lim) ? (1u << s) : 0u;
+        for (int s = SPEC; s < n1; s++) m1 |= (cand_lower(c1[(size_t)s * n]) <= lim) ? (1u << s) : 0u;
+        c = __popc(m0) + __popc(m1);
         int incl = c;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -130,14 +148,10 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
         if (valid) {
             if (!full && fits) {
                 int w = 0;
-                for (int s = 0; s < i0.x; s++) {
-                    const uint32_t e = c0[s];
-                    if (cand_lower(e) <= lim) pairs[off0 + w++] = make_int2((int)row, (int)(e >> 16));
-                }
-                for (int s = 0; s < i1.x; s++) {
-                    const uint32_t e = c1[s];
-                    if (cand_lower(e) <= lim) pairs[off0 + w++] = make_int2((int)row, (int)(e >> 16));
-                }
+                for (unsigned m = m0; m; m &= m - 1)
+                    pairs[off0 + w++] = make_int2((int)row, (int)(c0[(size_t)(__ffs(m) - 1) * n] >> 16));
+                for (unsigned m = m1; m; m &= m - 1)
+                    pairs[off0 + w++] = make_int2((int)row, (int)(c1[(size_t)(__ffs(m) - 1) * n] >> 16));
             }
             rowpair[row] = make_int2(fits ? (int)off0 : 0, (full || !fits) ? -1 : c);
         }
@@ -153,8 +167,8 @@ __global__ void __launch_bounds__(256) k_certify(const int2* __restrict__ rowpai
                                                  const float* __restrict__ X, const float* __restrict__ C, int d,
                                                  float gamma32, int32_t* __restrict__ labels,
                                                  double* __restrict__ min_dist, int32_t* __restrict__ full_list,
-                                                 DevCounters* cnt) {
-    unsigned long long ev32 = 0, ev64 = 0, amb = 0, ovf_rows = 0;
+                                                 int32_t* __restrict__ amb_list, DevCounters* cnt) {
+    unsigned long long ev32 = 0, amb = 0, ovf_rows = 0;
     const float g = gamma32;
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
          row += (int64_t)gridDim.x * blockDim.x) {
@@ -184,38 +198,97 @@ __global__ void __launch_bounds__(256) k_certify(const int2* __restrict__ rowpai
             continue;
         }
         amb++;
-        const float* x = X + row * d;
-        double best = INFINITY;
-        bj = 0x7fffffff;
-        for (int r = 0; r < rp.y; r++) {
-            if (v32[rp.x + r] * (1.0f - g) <= up) {
-                const int j = pairs[rp.x + r].y;
-                const float* c = C + (int64_t)j * d;
-                double sacc = 0.0;
-                for (int l = 0; l < d; l++) {
-                    const double t = __dsub_rn((double)x[l], (double)c[l]);
-                    sacc = __dadd_rn(sacc, __dmul_rn(t, t));
-                }
-                ev64++;
-                if (sacc < best || (sacc == best && j < bj)) { best = sacc; bj = j; }
-            }
-        }
-        labels[row] = bj;
-        min_dist[row] = best;
+        const int slot = atomicAdd(&cnt->amb_count, 1);
+        amb_list[slot] = (int32_t)row;
     }
+
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         ev32 += __shfl_xor_sync(0xffffffffu, ev32, off);
-        ev64 += __shfl_xor_sync(0xffffffffu, ev64, off);
         amb += __shfl_xor_sync(0xffffffffu, amb, off);
         ovf_rows += __shfl_xor_sync(0xffffffffu, ovf_rows, off);
     }
     if ((threadIdx.x & 31) == 0) {
         if (ev32) atomicAdd(&cnt->fp32_evals, ev32);
-        if (ev64) atomicAdd(&cnt->fp64_evals, ev64);
         if (amb) atomicAdd(&cnt->amb_rows, amb);
         if (ovf_rows) atomicAdd(&cnt->ovf_rows, ovf_rows);
     }
+}
+
+// Near-tie rows (listed by k_certify): one warp per row.  The candidates
+// whose fp32 interval can still hold the minimum are taken AMB_B at a time:
+// the warp stages x and their centre rows in shared memory and forms every
+// binary64 product (x_l - c_l)^2 in parallel (each is one rounding, whatever
+// the order); then one lane per candidate adds its products in coordinate
+// order, one rounding per addition: the oracle's sequential sum.  The warp
+// then takes the smallest value, lowest index on ties.
+constexpr int AMB_B = 4;
+__global__ void __launch_bounds__(256) k_amb_fp64(const int32_t* __restrict__ amb_list, const int* __restrict__ amb_count,
+                                                  const int2* __restrict__ rowpair, const int2* __restrict__ pairs,
+                                                  const float* __restrict__ v32, const float* __restrict__ X,
+                                                  const float* __restrict__ C, int d, float gamma32,
+                                                  int32_t* __restrict__ labels, double* __restrict__ min_dist,
+                                                  DevCounters* cnt) {
+    extern __shared__ double amb_sm[];  // per warp: AMB_B x d products
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double* prod = amb_sm + (size_t)wib * AMB_B * d;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int na = *amb_count;
+    const float g = gamma32;
+    unsigned long long ev64 = 0;
+    for (int64_t t = w0; t < na; t += nw) {
+        const int64_t row = amb_list[t];
+        const int2 rp = rowpair[row];
+        float up = INFINITY;
+        for (int r = lane; r < rp.y; r += 32) up = fminf(up, v32[rp.x + r] * (1.0f + g));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) up = fminf(up, __shfl_xor_sync(0xffffffffu, up, off));
+        const float* x = X + row * d;
+        double best = INFINITY;
+        int bj = 0x7fffffff;
+        // the open candidates, AMB_B per batch (warp-uniform loop over the row's pairs)
+        int r = 0;
+        while (true) {
+            int js[AMB_B] = {};
+            int nb = 0;
+            for (; r < rp.y && nb < AMB_B; r++)
+                if (v32[rp.x + r] * (1.0f - g) <= up) js[nb++] = pairs[rp.x + r].y;
+            if (nb == 0) break;
+            __syncwarp();
+            for (int e = lane; e < nb * d; e += 32) {
+                const int b = e / d, l = e - b * d;
+                const double u = __dsub_rn((double)x[l], (double)C[(int64_t)js[b] * d + l]);
+                prod[e] = __dmul_rn(u, u);
+            }
+            __syncwarp();
+            if (lane < nb) {
+                const double* pp = prod + (size_t)lane * d;
+                double sacc = 0.0;
+                for (int l = 0; l < d; l++) sacc = __dadd_rn(sacc, pp[l]);
+                int j = js[0];
+#pragma unroll
+                for (int q = 1; q < AMB_B; q++)
+                    if (lane == q) j = js[q];
+                ev64++;
+                if (sacc < best || (sacc == best && j < bj)) { best = sacc; bj = j; }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
+            if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        }
+        if (lane == 0) {
+            labels[row] = bj;
+            min_dist[row] = best;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ev64 += __shfl_xor_sync(0xffffffffu, ev64, off);
+    if (lane == 0 && ev64) atomicAdd(&cnt->fp64_evals, ev64);
 }
 
 __global__ void k_patch_flagged(const float* __restrict__ X, const float* __restrict__ C, int k, int d,
@@ -241,7 +314,7 @@ __global__ void k_patch_flagged(const float* __restrict__ X, const float* __rest
 }
 
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels, double* min_dist,
-                          int32_t* full_list, int num_sms, cudaStream_t st) {
+                          int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st) {
     const int64_t rb = std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, (int64_t)num_sms * 8));
     k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.pairs, a.pair_cap, a.rowpair, a.cnt);
     cudaError_t e = cudaGetLastError();
@@ -263,7 +336,14 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_certify<<<(unsigned)rb, 256, 0, st>>>(a.rowpair, a.n, a.pairs, a.v32, X, C, a.d, a.tp.gamma32, labels, min_dist,
-                                             full_list, a.cnt);
+                                             full_list, amb_list, a.cnt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t amb_smem = (size_t)8 * AMB_B * a.d * sizeof(double);  // 8 warps per block
+    e = cudaFuncSetAttribute(k_amb_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amb_smem);
+    if (e != cudaSuccess) return e;
+    k_amb_fp64<<<(unsigned)num_sms, 256, amb_smem, st>>>(amb_list, &a.cnt->amb_count, a.rowpair, a.pairs, a.v32, X, C,
+                                                          a.d, a.tp.gamma32, labels, min_dist, a.cnt);
     return cudaGetLastError();
 }
 

@@ -467,9 +467,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (!ok) break;
             if (valid && MODE == 0) {
-                // the row's list, its window W and this group's d^ minimum
-                uint32_t* crow = a.cand + ((size_t)row * 2 + g) * TC_L;
-                for (int sl = 0; sl < cnt; sl++) crow[sl] = list[sl * TC_BM];
+                // the row's list (slot-major: consecutive rows side by side), its
+                // window W and this group's d^ minimum
+                uint32_t* ccol = a.cand + (size_t)g * TC_L * a.n + row;
+                for (int sl = 0; sl < cnt; sl++) ccol[(size_t)sl * a.n] = list[sl * TC_BM];
                 a.rowinfo[row * 2 + g] = make_int4(cnt, ovf, __float_as_int(W), __float_as_int(p + m));
             }
             nflag_total += (unsigned long long)nflag;

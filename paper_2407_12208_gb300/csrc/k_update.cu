@@ -28,11 +28,20 @@ KM_DEV int fixed_shift(unsigned amax_bits, int64_t n) {
     return 60 - lgn - E;  // |sum| 2^S < 2^(lgn + E + 1 + S) = 2^61
 }
 
-// v 2^S rounded to the nearest integer.  S lies in [-98, 209]; the scaling
-// is split into two power-of-two factors, each a normal float, and both
-// products are exact whenever the result is a normal float (|v 2^S| < 2^61
-// never overflows); when it is not, |v 2^S| < 2^-126 and the integer is 0
-// either way.  Same integers as rounding ldexpf(v, S).
+// v 2^S rounded to the nearest integer, exactly, without 64-bit conversions
+// (float-to-int64 conversion runs on the FP64 pipe, which is narrow here).
+//  - Scaling: S lies in [-98, 209]; it is split into two power-of-two
+//    factors, each a normal float, and both products are exact whenever the
+//    result is a normal float (|v 2^S| < 2^61 never overflows); when it is
+//    not, |v 2^S| < 2^-126 and the integer is 0 either way.
+//  - Rounding: y = v 2^S (|y| < 2^62) is split by round-to-nearest additions
+//    of magic constants into y = p2 + p1 + r0, p2 a multiple of 2^40, p1 of
+//    2^20, |r0| <= 2^19; every step is exact (each remainder fits in 24 bits),
+//    and round(y) = p2 + p1 + round(r0) because p2 + p1 is even.  The three
+//    integers p2 / 2^40, p1 / 2^20 and round(r0) are read off the bits of a
+//    float in [2^23, 2^24) (Split::bits: value + 0x4B400000, the bias removed
+//    once per sum, modulo 2^32).
+// Same integers as rounding ldexpf(v, S) with __float2ll_rn.
 struct FixedScale {
     float f1, f2;
     KM_DEV explicit FixedScale(int S) {
@@ -40,7 +49,32 @@ struct FixedScale {
         f1 = __int_as_float((s1 + 127) << 23);
         f2 = __int_as_float((s2 + 127) << 23);
     }
-    KM_DEV long long operator()(float v) const { return __float2ll_rn(__fmul_rn(__fmul_rn(v, f1), f2)); }
+    static constexpr unsigned kBias = 0x4B400000u;  // bits of 1.5 * 2^23
+    // biased 32-bit parts of round(v 2^S): (b2, b1, b0), value = sum of (b - kBias) 2^(40, 20, 0)
+    KM_DEV void split(float v, unsigned& b2, unsigned& b1, unsigned& b0) const {
+        const float y = __fmul_rn(__fmul_rn(v, f1), f2);
+        const float c40 = 0x1.8p63f;  // ulp 2^40
+        const float c20 = 0x1.8p43f;  // ulp 2^20
+        const float c0 = 0x1.8p23f;   // ulp 1
+        const float p2 = __fsub_rn(__fadd_rn(y, c40), c40);
+        const float r = __fsub_rn(y, p2);
+        const float p1 = __fsub_rn(__fadd_rn(r, c20), c20);
+        const float r0 = __fsub_rn(r, p1);
+        b0 = __float_as_uint(__fadd_rn(r0, c0));
+        b1 = __float_as_uint(__fmaf_rn(p1, 0x1p-20f, c0));
+        b2 = __float_as_uint(__fmaf_rn(p2, 0x1p-40f, c0));
+    }
+    // sum of m split values -> int64 (the biased parts were added modulo 2^32;
+    // each true part sum is below 2^31 in magnitude for m <= 2^10)
+    KM_DEV static long long combine(unsigned s2, unsigned s1, unsigned s0, unsigned m) {
+        const int t2 = (int)(s2 - m * kBias), t1 = (int)(s1 - m * kBias), t0 = (int)(s0 - m * kBias);
+        return (long long)t2 * (1ll << 40) + (long long)t1 * (1ll << 20) + (long long)t0;
+    }
+    KM_DEV long long operator()(float v) const {
+        unsigned b2, b1, b0;
+        split(v, b2, b1, b0);
+        return combine(b2, b1, b0, 1u);
+    }
 };
 
 __global__ void k_absmax(const float* __restrict__ X, int64_t count, unsigned* out) {
@@ -196,9 +230,12 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
         const int j = bucket_of(item_off, k, it);
         const int c = (int)(it - item_off[j]);
         const int r0 = off[j] + c * SEG_CHUNK, r1 = min(off[j + 1], r0 + SEG_CHUNK);
-        long long acc[NV4][4];
+        // biased parts of the fixed-point values, summed modulo 2^32 (SEG_CHUNK rows at most)
+        unsigned a2[NV4][4], a1[NV4][4], a0[NV4][4];
 #pragma unroll
-        for (int u = 0; u < NV4; u++) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0;
+        for (int u = 0; u < NV4; u++)
+#pragma unroll
+            for (int t = 0; t < 4; t++) a2[u][t] = a1[u][t] = a0[u][t] = 0u;
         for (int base = r0; base < r1; base += 32) {
             // the row indices of 32 rows in one coalesced load, then broadcast
             const int64_t my_i = (base + lane < r1) ? (int64_t)perm[base + lane] : -1;
@@ -219,22 +256,31 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
                 for (int b = 0; b < RB; b++)
 #pragma unroll
                     for (int u = 0; u < NV4; u++) {
-                        acc[u][0] += fx(v[b][u].x);
-                        acc[u][1] += fx(v[b][u].y);
-                        acc[u][2] += fx(v[b][u].z);
-                        acc[u][3] += fx(v[b][u].w);
+                        const float xs[4] = {v[b][u].x, v[b][u].y, v[b][u].z, v[b][u].w};
+#pragma unroll
+                        for (int t = 0; t < 4; t++) {
+                            unsigned q2, q1, q0;
+                            fx.split(xs[t], q2, q1, q0);
+                            a2[u][t] += q2;
+                            a1[u][t] += q1;
+                            a0[u][t] += q0;
+                        }
                     }
             }
         }
+        // every row position of the item was split (absent rows and padding as 0.0f)
+        const unsigned m = (unsigned)(((r1 - r0 + RB - 1) / RB) * RB);
 #pragma unroll
         for (int u = 0; u < NV4; u++) {
             const int cidx = lane + 32 * u;
             if (cidx < d4)
 #pragma unroll
-                for (int t = 0; t < 4; t++)
-                    if (acc[u][t])
+                for (int t = 0; t < 4; t++) {
+                    const long long acc = FixedScale::combine(a2[u][t], a1[u][t], a0[u][t], m);
+                    if (acc)
                         atomicAdd(reinterpret_cast<unsigned long long*>(&sums[(int64_t)j * d + 4 * cidx + t]),
-                                  (unsigned long long)acc[u][t]);
+                                  (unsigned long long)acc);
+                }
         }
     }
 }
