@@ -146,9 +146,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        ctx.assign(Xd, Cd, p, labels=labels, min_dist=md, ws=ws, stream=stream, want_flagged=False)
-        ctx.update_centroids(Xd, labels, Cd, p, min_dist=md, C_new=Cn, counts=counts, ws=ws, stream=stream,
-                             want_shift=False)
+        # one iteration of Alg. 3: assignment then centre update (km_lloyd_step)
+        ctx.lloyd_step(Xd, Cd, p, labels=labels, min_dist=md, C_new=Cn, counts=counts, ws=ws, stream=stream,
+                       want_shift=False)
 
     def barrier():
         if world > 1:
@@ -291,7 +291,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": args.low, "data": "synthetic",
             "config": {"workload": args.workload + ": " + desc, "n": n, "d": d, "k": k, "low": args.low,
                        "test": "tc", "rho": 5.0, "parallelism": "replicas" if world > 1 else "single",
-                       "step": "km_assign (quantise, screen, refine, argmin, min_dist) + km_update_centroids",
+                       "step": "km_lloyd_step: quantise X (+ max |x|), screen, refine, certified argmin, min_dist, exact centre update",
                        "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
             "fp64_path": fp64,

@@ -145,6 +145,19 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d,
                               int64_t* counts, double* shift_host, void* ws, size_t ws_bytes,
                               void* stream);
 
+/* One iteration of Alg. 3's loop: the assignment of X to C_old (as
+ * km_assign: labels, min_dist (nullable)) followed by the centre update of
+ * Eq. (center) on those labels (as km_update_centroids: C_new, counts
+ * (nullable), shift_host (nullable, host)).  The two share one pass where
+ * they can: the largest |x|, which fixes the scale of the exact centre
+ * sums, comes out of the quantisation pass.  The results equal km_assign
+ * followed by km_update_centroids bit for bit.  Workspace: as km_lloyd_run
+ * (km_workspace_size). */
+km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_old,
+                        const km_params* p, int32_t* labels, double* min_dist, float* C_new,
+                        int64_t* counts, double* shift_host, void* ws, size_t ws_bytes,
+                        void* stream);
+
 /* Alg. 3: Lloyd's loop with the mixed-precision assignment.  C_out (k x d)
  * receives the final centres, labels (n) the final reassignment.
  * sse_per_iter and eta_per_iter (nullable, host, max_iter + 1 doubles):

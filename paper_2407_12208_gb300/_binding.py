@@ -27,7 +27,7 @@ TEST_NAMES = {"tc": TEST_TC, "paper": TEST_PAPER, "off": TEST_OFF}
 EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_workspace_size",
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
-           "km_get_launch_count", "km_assign_static"]
+           "km_get_launch_count", "km_assign_static", "km_lloyd_step"]
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         lib.km_release.argtypes = [vp, c.c_uint64]
         lib.km_cancel.argtypes = [vp, c.c_uint64]
         lib.km_assign_static.argtypes = [vp, vp, i64, vp, i32, i32, vp, vp, vp]
+        lib.km_lloyd_step.argtypes = [vp, vp, i64, i32, i32, vp, P, vp, vp, vp, vp, c.POINTER(c.c_double), vp, sz, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -217,6 +218,28 @@ class Context:
                                           _ptr(flag_bits), ctypes.byref(nf), _ptr(ws), ws.numel(),
                                           _stream(stream)))
         return D, flag_bits, nf.value
+
+    def lloyd_step(self, X, C_old, p: Params, labels=None, min_dist=None, C_new=None, counts=None, ws=None,
+                   stream=None, want_shift=True):
+        """km_lloyd_step: one assignment + centre update (Alg. 3's loop body)."""
+        import torch
+        n, d = X.shape
+        k = C_old.shape[0]
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32, device=X.device)
+        if min_dist is None:
+            min_dist = torch.empty(n, dtype=torch.float64, device=X.device)
+        if C_new is None:
+            C_new = torch.empty_like(C_old)
+        if counts is None:
+            counts = torch.empty(k, dtype=torch.int64, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p)
+        sh = ctypes.c_double(0.0)
+        self._check(self.lib.km_lloyd_step(self.h, _ptr(X), n, d, k, _ptr(C_old), ctypes.byref(p), _ptr(labels),
+                                           _ptr(min_dist), _ptr(C_new), _ptr(counts),
+                                           ctypes.byref(sh) if want_shift else None, _ptr(ws), ws.numel(),
+                                           _stream(stream)))
+        return labels, min_dist, C_new, counts, (sh.value if want_shift else None)
 
     def update_centroids(self, X, labels, C_old, p: Params, min_dist=None, C_new=None, counts=None, ws=None,
                          stream=None, want_shift=True):

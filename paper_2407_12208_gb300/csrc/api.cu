@@ -256,8 +256,11 @@ TestParams make_tp(const km_params* p, int d) {
 bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
 // One assignment of X against C into labels/min_dist (all device).
+// x_absmax (nullable, zeroed by the caller): max |x| over X, folded out of the
+// quantisation pass (tensor-core paths only).
 km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
-                     int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st) {
+                     int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st,
+                     unsigned* x_absmax = nullptr) {
     const TestParams tp = make_tp(p, d);
     if (p->low == KM_FP64_DIRECT || p->low == KM_FP32_DIRECT) {
         const bool acc64 = p->low == KM_FP64_DIRECT;
@@ -278,7 +281,7 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     const int esz = fmt == 2 ? 1 : 2;
     {
         PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
-        if (!x_prepared) KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
+        if (!x_prepared) KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st, x_absmax));
         if (fmt == 2) {
             KL(1, launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
             KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
@@ -511,6 +514,47 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     return KM_OK;
 }
 
+km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_old,
+                        const km_params* p, int32_t* labels, double* min_dist, float* C_new, int64_t* counts,
+                        double* shift_host, void* ws, size_t ws_bytes, void* stream) {
+    km_status s = check_common(ctx, X, n, C_old, k, d);
+    if (s != KM_OK) return s;
+    if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
+    if (!labels || !C_new || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    AssignWs w = carve_assign(cv, n, d, k, p->low, false);
+    UpdateWs u = carve_update(cv, n, d, k);
+    double* md = min_dist ? min_dist : cv.take<double>((size_t)n);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
+    // assignment (Alg. 3 step 1); the quantisation pass also yields max |x|
+    const bool fused = is_tc(p->low);
+    if (fused) CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
+    s = run_assign(ctx, X, n, C_old, k, d, p, labels, md, w, false, st, fused ? u.absmax : nullptr);
+    if (s != KM_OK) return s;
+    KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
+    // centre update (Eq. (center)) on the labels just computed
+    {
+        PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
+        if (!fused) KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
+        KL(4, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
+        KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts, u.shift,
+                              u.taken, st));
+    }
+    ctx->last_cnt = w.cnt;
+    ctx->last_sse = w.sse;
+    ctx->last_stream = st;
+    ctx->last_pairs = (uint64_t)n * (uint64_t)k;
+    if (shift_host) {
+        if ((s = sync_status(ctx, w.cnt, st)) != KM_OK) return s;
+        CK(cudaMemcpy(shift_host, u.shift, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return KM_OK;
+}
+
 static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                             const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                             double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
@@ -542,13 +586,16 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     CK(cudaSetDevice(ctx->device));
     CK(cudaMemsetAsync(L.a.cnt, 0, sizeof(DevCounters), st));
     CK(cudaMemcpyAsync(L.C0, C_init, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToDevice, st));
-    // the quantised data and its norms are computed once (Section 3.2)
+    // the quantised data and its norms are computed once (Section 3.2), and with
+    // them the largest |x| that fixes the scale of the exact centre sums
     if (is_tc(p->low)) {
         const int fmt = fmt_of(p->low);
         PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
-        KL(1, launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, 0, nullptr, st));
+        CK(cudaMemsetAsync(L.u.absmax, 0, sizeof(unsigned), st));
+        KL(1, launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, 0, nullptr, st, L.u.absmax));
+    } else {
+        KL(1, launch_absmax(X, n * (int64_t)d, L.u.absmax, st));
     }
-    KL(1, launch_absmax(X, n * (int64_t)d, L.u.absmax, st));
     float* cur = L.C0;
     float* nxt = L.C1;
     int t = 0;

@@ -54,8 +54,11 @@ struct TestParams {
 // stride ldq elements; stat[i] = (||a||^2 fp32, ||a||, ||a~||, ||a~ - a||);
 // rscale[i] = per-row scale (e4m3, scale_mode 0) or the uniform scale read
 // from *uscale (scale_mode 1); fp16/bf16 write 1.
+// absmax_out (nullable): max |a| over A folded in with atomicMax on its bits
+// (the caller zeroes it first).
 cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
-                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st);
+                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st,
+                            unsigned* absmax_out = nullptr);
 // amax over all of C (for the uniform E4M3 centre scale): writes the scale.
 cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out, cudaStream_t st);
 // column maxima of the centre statistics

@@ -43,9 +43,26 @@ KM_DEV float e4m3_row_scale(float amax) {
     return s;
 }
 
+// Largest |a| seen by the block's threads, folded into *out with one atomic
+// per block (non-negative floats order like their bit patterns).
+KM_DEV void block_absmax(float v, unsigned* out) {
+    __shared__ float wmax[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wmax[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) m = fmaxf(m, wmax[i]);
+        atomicMax(out, __float_as_uint(m));
+    }
+}
+
 __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
                            float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
-                           const float* __restrict__ uscale) {
+                           const float* __restrict__ uscale, unsigned* __restrict__ absmax_out) {
+    float amx = 0.0f;  // largest |a| of this thread's elements (absmax_out)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -67,6 +84,7 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
         float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
         for (int l = lane; l < ldq; l += 32) {
             float v = (l < d) ? a[l] : 0.0f;
+            amx = fmaxf(amx, fabsf(v));
             float qv = quant_val(v * inv, fmt);  // quantised value of x / s
             if (l < d) {
                 df_add_sq(v, ph, pl);
@@ -106,6 +124,7 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
             if (rscale) rscale[i] = s;
         }
     }
+    if (absmax_out) block_absmax(amx, absmax_out);
 }
 
 
@@ -115,7 +134,8 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
 template <int NV>
 __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
                               float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
-                              const float* __restrict__ uscale) {
+                              const float* __restrict__ uscale, unsigned* __restrict__ absmax_out) {
+    float amx = 0.0f;  // largest |a| of this thread's elements (absmax_out)
     const int lane = threadIdx.x & 31, sl = lane & 7;
     const unsigned gmask = 0xFFu << (lane & ~7);
     const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane >> 3);
@@ -128,6 +148,7 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
         for (int u = 0; u < NV; u++) {
             const int c = sl + 8 * u;
             x[u] = (c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            amx = fmaxf(amx, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
         }
         float s = 1.0f;
         if (fmt == 2) {
@@ -202,6 +223,7 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
             if (rscale) rscale[i] = s;
         }
     }
+    if (absmax_out) block_absmax(amx, absmax_out);
 }
 
 // Vector path (d % 4 == 0, d <= 512): one warp per row, each lane holds up to
@@ -209,7 +231,8 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
 template <int NV>
 __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
                                float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
-                               const float* __restrict__ uscale) {
+                               const float* __restrict__ uscale, unsigned* __restrict__ absmax_out) {
+    float amx = 0.0f;  // largest |a| of this thread's elements (absmax_out)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -221,6 +244,7 @@ __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, in
         for (int u = 0; u < NV; u++) {
             const int c = lane + 32 * u;
             x[u] = (c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            amx = fmaxf(amx, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
         }
         float s = 1.0f;
         if (fmt == 2) {
@@ -293,6 +317,7 @@ __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, in
             if (rscale) rscale[i] = s;
         }
     }
+    if (absmax_out) block_absmax(amx, absmax_out);
 }
 
 __global__ void k_amax_scale(const float* __restrict__ C, int64_t count, float* out) {
@@ -350,7 +375,8 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
 }
 
 cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
-                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st) {
+                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st,
+                            unsigned* absmax_out) {
     // one warp per row, enough warps in flight to cover the memory latency
     int64_t blocks = (m * 32 + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
@@ -361,22 +387,22 @@ cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, 
     if (vec && nv8 <= 8) {
         blocks = std::min<int64_t>(std::max<int64_t>(1, (m * 8 + 255) / 256), (int64_t)152 * 16);
         if (nv8 <= 1)
-            k_quantize_g8<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_g8<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
         else if (nv8 <= 2)
-            k_quantize_g8<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_g8<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
         else if (nv8 <= 4)
-            k_quantize_g8<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_g8<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
         else
-            k_quantize_g8<8><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_g8<8><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
     } else if (vec && nv <= 4) {
         if (nv == 1)
-            k_quantize_vec<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_vec<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
         else if (nv == 2)
-            k_quantize_vec<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_vec<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
         else
-            k_quantize_vec<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+            k_quantize_vec<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
     } else {
-        k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale);
+        k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
     }
     return cudaGetLastError();
 }

@@ -396,18 +396,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     const int qd = act ? __ffs(ph) - 1 : 0;
                                     ph &= ph - 1;
                                     const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
+                                    float et[4];
 #pragma unroll
                                     for (int c = 0; c < 4; c++) {
                                         const float s0 = b0 ? eh[4 + c] : eh[c], s1 = b0 ? eh[12 + c] : eh[8 + c];
                                         const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
                                         const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
-                                        const float et = b2 ? t1 : t0;
-                                        const bool pc = act && (et <= cthr) && !ovf;
+                                        et[c] = b2 ? t1 : t0;
+                                    }
+                                    const bool q0 = et[0] <= cthr, q1 = et[1] <= cthr, q2 = et[2] <= cthr, q3 = et[3] <= cthr;
+                                    const int jq = col0 + 32 * half + 4 * qd;
+                                    // the quad's first candidate: one branch-free append (a lane with
+                                    // nothing to add writes the dummy slot)
+                                    const int c1 = q0 ? 0 : (q1 ? 1 : (q2 ? 2 : 3));
+                                    const float e1 = q0 ? et[0] : (q1 ? et[1] : (q2 ? et[2] : et[3]));
+                                    {
+                                        const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
                                         const bool room = cnt < TC_L;
                                         const int slot = (pc && room) ? cnt : TC_L;
-                                        list[slot * TC_BM] = cand_entry(col0 + 32 * half + 4 * qd + c, p + et);
+                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1);
                                         ovf |= (pc && !room);
                                         cnt += (pc && room) ? 1 : 0;
+                                    }
+                                    // its further candidates (a quad rarely holds more than one)
+                                    const int nq = (int)q0 + (int)q1 + (int)q2 + (int)q3;
+                                    if (__any_sync(0xffffffffu, act && nq > 1 && !ovf)) {
+#pragma unroll
+                                        for (int c = 1; c < 4; c++) {
+                                            const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
+                                            const bool room = cnt < TC_L;
+                                            const int slot = (pc && room) ? cnt : TC_L;
+                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c]);
+                                            ovf |= (pc && !room);
+                                            cnt += (pc && room) ? 1 : 0;
+                                        }
                                     }
                                 }
                             }

@@ -426,12 +426,16 @@ __global__ void k_sum_parts(const double* __restrict__ v, int64_t n, double* __r
     }
     if (threadIdx.x == 0) parts[blockIdx.x] = red[0];
 }
+// One warp, a fixed order: lane l adds parts l, l + 32, ... in turn, then a
+// fixed butterfly (a serial sum over all parts would chain every binary64
+// addition's latency).
 __global__ void k_sum_final(const double* __restrict__ parts, int nparts, double* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nparts; i++) s += parts[i];
-        *out = s;
-    }
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < nparts; i += 32) s += parts[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) *out = s;
 }
 
 cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cudaStream_t st) {

@@ -274,3 +274,29 @@ def test_full_size_bf16_sampled():
     check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MIXED)
     st = c.stats()
     assert st["pairs"] == 1_000_000 * 1024
+
+
+# ------------------------------------------------ one fused Lloyd iteration
+@pytest.mark.parametrize("low,empty,shape", [("bf16", "farthest", (20000, 128, 300)), ("fp16", "keep", (7001, 64, 96)),
+                                             ("e4m3", "farthest", (5000, 64, 40)), ("fp32", "farthest", (3000, 16, 24)),
+                                             ("fp64", "keep", (2000, 8, 9))])
+def test_lloyd_step_equals_assign_then_update(ctx, low, empty, shape):
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = shape
+    X, C = workloads.gaussian_mixture(n, d, k, seed=61)
+    C[-1] = C[-1] + 1e3  # a centre far from every point: an empty cluster
+    Xd, Cd = _dev(X), _dev(C)
+    p = pkg.params(low, empty=empty)
+    lab1, md1, _ = ctx.assign(Xd, Cd, p)
+    Cn1, cnt1, sh1 = ctx.update_centroids(Xd, lab1, Cd, p, min_dist=md1)
+    torch.cuda.synchronize()
+    ref = [t.cpu().numpy() for t in (lab1, md1, Cn1, cnt1)]
+    lab2, md2, Cn2, cnt2, sh2 = ctx.lloyd_step(Xd, Cd, p)
+    torch.cuda.synchronize()
+    got = [t.cpu().numpy() for t in (lab2, md2, Cn2, cnt2)]
+    assert np.array_equal(got[0], ref[0])
+    assert np.array_equal(got[1].view(np.uint64), ref[1].view(np.uint64))
+    assert np.array_equal(got[2].view(np.uint32), ref[2].view(np.uint32))
+    assert np.array_equal(got[3], ref[3])
+    assert sh2 == sh1
+    assert ref[3][-1] == 0 or empty == "farthest"
