@@ -50,15 +50,23 @@ def _measured_peaks():
         return None
 
 
+def screen_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the screening kernel's sources."""
+    csrc = os.path.join(ROOT, "paper_2407_12208_gb300", "csrc")
+    hs = hashlib.sha256()
+    for f in ("k_tc.cu", "common.cuh", "internal.h"):
+        hs.update(open(os.path.join(csrc, f), "rb").read())
+    return hs.hexdigest()[:16]
+
+
 def _profile_traffic(n: int):
     """DRAM bytes per launch of the screening kernel from the committed ncu
     summary, scaled to n rows, if that summary was taken on the current
     kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "k_tc_screen_bf16_c2a.md")
-    src = os.path.join(ROOT, "paper_2407_12208_gb300", "csrc", "k_tc.cu")
     try:
         txt = open(path).read()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = screen_source_hash()
         mh = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
         mb = re.search(r"dram_bytes_per_row:\s*([0-9.eE+]+)", txt)
         if mh and mb and mh.group(1) == h:
@@ -132,6 +140,9 @@ def run_ours(args):
     if rank == 0 or world > 1:
         pbuild.build()
     gen, n, d, k, desc = WORKLOADS[args.workload]
+    if args.n:
+        n = args.n
+        desc += " (first %d rows)" % n
     X, C = getattr(workloads, gen)(n, d, k, seed=15 + rank)
     dev = torch.device("cuda", local)
     Xd = torch.from_numpy(X).to(dev)
@@ -214,11 +225,14 @@ def run_ours(args):
             "kernel": "k_tc (tcgen05 screen)", "algorithmic_flops_per_launch": flops, "peak_source": peak_src}
 
     # ------------------------------------------------------------- end to end
-    Xh = torch.from_numpy(X).pin_memory()
+    e2e = None
+    if args.only_step:
+        args.no_fp64 = args.no_cpu_baseline = True
+    Xh = torch.from_numpy(X).pin_memory() if not args.only_step else None
     Ch = torch.from_numpy(C).pin_memory()
     lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
     md_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = 0 if args.only_step else max(3, min(args.steps, 20))
 
     def e2e_step():
         Xd.copy_(Xh, non_blocking=True)
@@ -227,7 +241,8 @@ def run_ours(args):
         lab_h.copy_(labels, non_blocking=True)
         md_h.copy_(md, non_blocking=True)
 
-    e2e_step()
+    if e2e_steps:
+        e2e_step()
     torch.cuda.synchronize()
     barrier()
     f0 = torch.cuda.Event(enable_timing=True)
@@ -237,15 +252,16 @@ def run_ours(args):
         e2e_step()
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    e2e_ms = f0.elapsed_time(f1) / max(e2e_steps, 1)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e = {"value": pairs_per_step * world / (e2e_ms / 1e3), "unit": "pairs/s",
-           "h2d_bytes_per_step": int(Xh.numel() * 4 + Ch.numel() * 4),
-           "d2h_bytes_per_step": int(lab_h.numel() * 4 + md_h.numel() * 8), "ms_per_step": e2e_ms}
+    if e2e_steps:
+        e2e = {"value": pairs_per_step * world / (e2e_ms / 1e3), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(Xh.numel() * 4 + Ch.numel() * 4),
+               "d2h_bytes_per_step": int(lab_h.numel() * 4 + md_h.numel() * 8), "ms_per_step": e2e_ms}
 
     stats = ctx.stats()
     # ------------------------------------------------- FP64 path, same GPU
@@ -353,6 +369,9 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="rows (profiling a smaller case of the same kernels)")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the step only: no end-to-end, FP64 or CPU legs (for profiler runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.warmup < 1:
