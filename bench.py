@@ -300,6 +300,10 @@ def run_ours(args):
                "sample": "first %d of %d rows x %d centres (assign + centre update, binary64 direct)" % (rows, n, k),
                "seconds": tc}
 
+    serving = None
+    if rank == 0 and not args.only_step and not args.no_serving:
+        serving = serving_leg(args, local)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -310,7 +314,7 @@ def run_ours(args):
                        "step": "km_lloyd_step: quantise X (+ max |x|), screen, refine, certified argmin, min_dist, exact centre update",
                        "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "fp64_path": fp64,
+            "fp64_path": fp64, "serving": serving,
             "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},
             "eta": stats["flagged"] / max(stats["pairs"], 1),
             "assign_stats": {kk: stats[kk] for kk in ("fp32_evals", "fp64_evals", "ambiguous_rows", "overflow_rows")},
@@ -319,6 +323,67 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serving_leg(args, device: int) -> dict:
+    """Served stream through km_submit / km_poll: Lloyd jobs of uneven n, d, k
+    (n log-uniform in [1e3, 1e5], d in {2, 8, 32, 128, 256}, k log-uniform in
+    [4, 1024], Gaussian mixtures, 25 iterations; FP32 direct for d <= 8, BF16
+    below d = 64, E4M3 from d = 64), 80 GB arena budget.  A burst at t = 0
+    gives the saturated throughput; then a Poisson stream at half that job
+    rate.  Latency = submit -> result ready, measured by the library."""
+    import numpy as np
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import workloads
+    specs = workloads.serving_jobs(args.serve_jobs, seed=2024, n_lo=1e3, n_hi=1e5)
+    data = []
+    for i, sp in enumerate(specs):
+        X, C = workloads.gaussian_mixture(sp["n"], sp["d"], sp["k"], seed=3000 + i)
+        low = "fp32" if sp["d"] <= 8 else ("bf16" if sp["d"] < 64 else "e4m3")
+        data.append((X, C, pkg.params(low, max_iter=25, tau=0.0)))
+    ctx = pkg.Context(device, arena_bytes=80 << 30)
+
+    def run(arrivals):
+        ids, t0 = [], time.perf_counter()
+        pending = {}
+        lat = []
+        for (X, C, p), ta in zip(data, arrivals):
+            while time.perf_counter() - t0 < ta:
+                for jid in list(pending):
+                    r = ctx.poll(jid)
+                    if r is not None:
+                        lat.append(r["latency_ms"])
+                        ctx.release(jid)
+                        del pending[jid]
+                time.sleep(0.0005)
+            jid = ctx.submit(X, C, p, kind=0)
+            pending[jid] = True
+        while pending:
+            for jid in list(pending):
+                r = ctx.poll(jid)
+                if r is not None:
+                    assert r["status"] == 0, (r["status"], r["message"])
+                    lat.append(r["latency_ms"])
+                    ctx.release(jid)
+                    del pending[jid]
+            time.sleep(0.0005)
+        return lat, time.perf_counter() - t0
+
+    run([0.0] * min(8, len(data)))  # warm-up: module loading, first launches
+    lat_b, span_b = run([0.0] * len(data))
+    pairs = sum(X.shape[0] * float(C.shape[0]) * 26 for X, C, _ in data)  # 25 iterations + final assignment
+    rate = 0.5 * len(data) / span_b
+    arr = workloads.poisson_arrivals(len(data), rate, seed=7)
+    lat_p, span_p = run(list(arr))
+    ctx.close()
+    pct = lambda v, q: float(np.percentile(np.asarray(v), q))
+    return {"jobs": len(data), "iterations_per_job": 25, "arena_gb": 80,
+            "burst": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99), "pairs_per_s": pairs / span_b,
+                      "makespan_s": span_b},
+            "poisson_half_load": {"rate_jobs_per_s": rate, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                                  "pairs_per_s": pairs / span_p},
+            "sizes": "n log-uniform [1e3, 1e5] (bounded stand-in for [1e3, 1e6]), d in {2, 8, 32, 128, 256}, "
+                     "k log-uniform [4, 1024]"}
 
 
 def run_reference(args):
@@ -370,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="rows (profiling a smaller case of the same kernels)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only: no end-to-end, FP64 or CPU legs (for profiler runs)")
     args = ap.parse_args()

@@ -245,6 +245,7 @@ typedef struct {
     double queue_ms;      /* submit -> admission */
     const float* C;       /* device pointer into the arena (k x d), valid until km_release */
     const int32_t* labels;/* device pointer into the arena (n), valid until km_release */
+    const char* message;  /* why the job failed ("" when it did not), valid until km_release */
 } km_result;
 
 /* Queues a job; it is admitted when its memory fits in the arena.  The host

@@ -61,7 +61,7 @@ class Job(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("sse", ctypes.c_double),
                 ("eta", ctypes.c_double), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
-                ("C", ctypes.c_void_p), ("labels", ctypes.c_void_p)]
+                ("C", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("message", ctypes.c_char_p)]
 
 
 _lib = None
@@ -324,7 +324,8 @@ class Context:
         if rc == KM_ENOTREADY:
             return None
         return {"status": rc, "iters": r.iters, "sse": r.sse, "eta": r.eta, "latency_ms": r.latency_ms,
-                "queue_ms": r.queue_ms, "C": r.C, "labels": r.labels}
+                "queue_ms": r.queue_ms, "C": r.C, "labels": r.labels,
+                "message": (r.message or b"").decode()}
 
     def release(self, job_id: int):
         self._check(self.lib.km_release(self.h, ctypes.c_uint64(job_id)))

@@ -156,10 +156,10 @@ AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distance
         w.cstat = cv.take<float4>((size_t)k);
         w.cscale = cv.take<float>((size_t)k);
         w.qpad = cv.take<float>((size_t)kpad_of(k));
-        w.rowinfo = cv.take<int4>((size_t)n * 2);
+        w.rowinfo = cv.take<int4>((size_t)n * TC_GROUPS);
         w.ovf_list = cv.take<int32_t>((size_t)n);
         if (!distances) {
-            w.cand = cv.take<uint32_t>((size_t)n * 2 * TC_LIST);
+            w.cand = cv.take<uint32_t>((size_t)n * TC_GROUPS * TC_LIST);
             w.rowpair = cv.take<int2>((size_t)n);
             w.pair_cap = std::min<int64_t>((int64_t)n * TC_PAIRS_PER_ROW, (int64_t)INT32_MAX);
             w.pairs = cv.take<int2>((size_t)w.pair_cap);
@@ -304,7 +304,9 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     {
         PhaseScope ps(ctx, KM_PHASE_REFINE, st);
         CK(cudaMemsetAsync(&w.cnt->npairs, 0, sizeof(unsigned long long), st));
-        KL(4, launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st));
+        int nl = 0;
+        CK(launch_refine(X, C, a, labels, min_dist, w.ovf_list, w.amb_list, ctx->num_sms, st, &nl));
+        ctx->launches += (uint64_t)nl;
     }
     {
         // rows whose candidate list overflowed: full-row fp32 direct, binary64 where uncertified

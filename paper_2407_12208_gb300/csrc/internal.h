@@ -6,8 +6,11 @@
 
 namespace km {
 
-// Candidate-list entries per row and epilogue group of the screening kernel.
-constexpr int TC_LIST = 24;
+// Epilogue groups of the screening kernel (four warps each; tile t goes to
+// group t mod TC_GROUPS) and candidate-list entries per row and group (48 per
+// row in all).
+constexpr int TC_GROUPS = 2;
+constexpr int TC_LIST = 48 / TC_GROUPS;
 // Candidate pairs reserved per row in the workspace; rows past the capacity
 // are recomputed by the full-row kernel.
 constexpr int TC_PAIRS_PER_ROW = 8;
@@ -48,6 +51,21 @@ struct TestParams {
     float bsafe;     // relative safety factor applied to B evaluated in fp32
     float gamma32;   // gamma_{d+2}(2^-24) with safety, for fp32 direct certification
 };
+
+// Lets `func` take all the dynamic shared memory a block can have (the
+// per-block maximum less the kernel's static shared memory).  Every call sets
+// the same value: jobs of different shapes launched from several host threads
+// (the serving workers) cannot lower the limit under one another's launches;
+// the launch itself states the bytes it uses.
+constexpr int kMaxBlockSmem = 227 * 1024;
+template <typename F>
+inline cudaError_t allow_max_smem(F* func) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(func));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(reinterpret_cast<const void*>(func), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxBlockSmem - (int)fa.sharedSizeBytes);
+}
 
 // ---- kernels (launch wrappers; all asynchronous on `st`) -----------------
 // quantise rows of A (m x d fp32) to fmt (0 fp16, 1 bf16, 2 e4m3) with row
@@ -92,8 +110,8 @@ struct TcArgs {
     const ColMax* colmax;
     TestParams tp;
     int mode;
-    uint32_t* cand;           // mode 0: 2 x TC_LIST x n entries (group, slot, row), column j << 16 | top 16 bits of d^
-    int4* rowinfo;            // n x 2: (count, overflow, window W bits, d^min bits) per epilogue group
+    uint32_t* cand;           // mode 0: TC_GROUPS x TC_LIST x n entries (group, slot, row), column j << 16 | top 16 bits of d^
+    int4* rowinfo;            // n x TC_GROUPS: (count, overflow, window W bits, d^min bits) per epilogue group
     int2* pairs;              // refinement: candidate pairs (row, j), each row's pairs contiguous
     int64_t pair_cap;         // capacity of pairs / v32
     float* v32;               // fp32 direct value of each pair
@@ -113,7 +131,8 @@ size_t tc_smem_bytes(int fmt, int d, int k);
 // argmin + min_dist per row; rows left open are appended to full_list
 // (cnt->ovf_count) for the full-row kernel
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels,
-                          double* min_dist, int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st);
+                          double* min_dist, int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st,
+                          int* nlaunch);
 // fp64 direct values for flagged pairs of the distance matrix
 cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, const int2* queue,
                                  const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt,

@@ -240,12 +240,12 @@ cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const fl
     if (grid < 1) grid = 1;
     cudaError_t e;
     if (acc64) {
-        e = cudaFuncSetAttribute(k_direct_assign<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = allow_max_smem(k_direct_assign<double>);
         if (e != cudaSuccess) return e;
         k_direct_assign<double><<<(unsigned)grid, DA_ROWS, sm, st>>>(X, n, C, k, d, row_list, row_count, labels,
                                                                      min_dist, amb_list, cnt, gamma32);
     } else {
-        e = cudaFuncSetAttribute(k_direct_assign<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = allow_max_smem(k_direct_assign<float>);
         if (e != cudaSuccess) return e;
         k_direct_assign<float><<<(unsigned)grid, DA_ROWS, sm, st>>>(X, n, C, k, d, row_list, row_count, labels,
                                                                     min_dist, amb_list, cnt, gamma32);
@@ -259,11 +259,11 @@ cudaError_t launch_rows_full(bool fp32_first, const float* X, const float* C, in
     const size_t sm = (size_t)(((d + 3) & ~3) + k) * sizeof(float);
     cudaError_t e;
     if (fp32_first) {
-        e = cudaFuncSetAttribute(k_rows_full<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = allow_max_smem(k_rows_full<true>);
         if (e != cudaSuccess) return e;
         k_rows_full<true><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32);
     } else {
-        e = cudaFuncSetAttribute(k_rows_full<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = allow_max_smem(k_rows_full<false>);
         if (e != cudaSuccess) return e;
         k_rows_full<false><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32);
     }

@@ -7,7 +7,7 @@
 // centre can win).  Those become a flat list of (row, j) pairs, each row's pairs
 // contiguous.
 //  0. k_cand_select: the pairs from the screening kernel's per-row lists
-//     (rowinfo[2 i + g] = (count, overflow, W, d^min) per epilogue group);
+//     (rowinfo[TC_GROUPS i + g] = (count, overflow, W, d^min) per epilogue group);
 //  1. k_pair_eval: Eq. (dist-direct) in fp32 for every pair, 8 lanes per pair
 //     and 4 pairs per warp (no per-row bookkeeping on this path);
 //  2. k_certify, one thread per row: Theorem 4.1 puts each true value in
@@ -104,35 +104,39 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
         const bool valid = row < n;
         int c = 0;
         bool full = false;
-        int4 i0 = make_int4(0, 0, 0, 0), i1 = i0;
+        int cnt_g[TC_GROUPS];
         float lim = 0.0f;
         // slot s of group g at cand[(g * TC_LIST + s) * n + row]: a warp reads 32 rows side by side
         const uint32_t* c0 = cand + row;
-        const uint32_t* c1 = c0 + (size_t)TC_LIST * n;
-        unsigned m0 = 0, m1 = 0;  // entries inside the window
-        if (valid) {
-            i0 = rowinfo[row * 2];
-            i1 = rowinfo[row * 2 + 1];
-            full = (i0.y | i1.y) != 0;
-            lim = fminf(__int_as_float(i0.w), __int_as_float(i1.w)) + __int_as_float(i0.z);
-        }
-        const int n0 = full ? 0 : i0.x, n1 = full ? 0 : i1.x;
-        // the first 8 slots of both lists in one round of loads, the rest (rare) after
-        constexpr int SPEC = 8;
-        uint32_t e0[SPEC], e1[SPEC];
+        unsigned msk[TC_GROUPS];  // entries inside the window, per group
+        {
+            float dmin = INFINITY, W = 0.0f;
 #pragma unroll
-        for (int s = 0; s < SPEC; s++) {
-            e0[s] = (s < n0) ? c0[(size_t)s * n] : 0u;
-            e1[s] = (s < n1) ? c1[(size_t)s * n] : 0u;
+            for (int g = 0; g < TC_GROUPS; g++) {
+                const int4 ig = valid ? rowinfo[row * TC_GROUPS + g] : make_int4(0, 0, 0, __float_as_int(INFINITY));
+                full |= ig.y != 0;
+                cnt_g[g] = ig.x;
+                dmin = fminf(dmin, __int_as_float(ig.w));
+                W = __int_as_float(ig.z);
+            }
+            lim = dmin + W;
         }
+        // the first SPEC slots of every list in one round of loads, the rest (rare) after
+        constexpr int SPEC = (16 / TC_GROUPS < TC_LIST) ? 16 / TC_GROUPS : TC_LIST;
 #pragma unroll
-        for (int s = 0; s < SPEC; s++) {
-            m0 |= (s < n0 && cand_lower(e0[s]) <= lim) ? (1u << s) : 0u;
-            m1 |= (s < n1 && cand_lower(e1[s]) <= lim) ? (1u << s) : 0u;
+        for (int g = 0; g < TC_GROUPS; g++) {
+            const int ng = full ? 0 : cnt_g[g];
+            const uint32_t* cg = c0 + (size_t)g * TC_LIST * n;
+            uint32_t eg[SPEC];
+#pragma unroll
+            for (int s = 0; s < SPEC; s++) eg[s] = (s < ng) ? cg[(size_t)s * n] : 0u;
+            unsigned m = 0;
+#pragma unroll
+            for (int s = 0; s < SPEC; s++) m |= (s < ng && cand_lower(eg[s]) <= lim) ? (1u << s) : 0u;
+            for (int s = SPEC; s < ng; s++) m |= (cand_lower(cg[(size_t)s * n]) <= lim) ? (1u << s) : 0u;
+            msk[g] = m;
+            c += __popc(m);
         }
-        for (int s = SPEC; s < n0; s++) m0 |= (cand_lower(c0[(size_t)s * n]) <= lim) ? (1u << s) : 0u;
-        for (int s = SPEC; s < n1; s++) m1 |= (cand_lower(c1[(size_t)s * n]) <= lim) ? (1u << s) : 0u;
-        c = __popc(m0) + __popc(m1);
         int incl = c;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -148,10 +152,12 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
         if (valid) {
             if (!full && fits) {
                 int w = 0;
-                for (unsigned m = m0; m; m &= m - 1)
-                    pairs[off0 + w++] = make_int2((int)row, (int)(c0[(size_t)(__ffs(m) - 1) * n] >> 16));
-                for (unsigned m = m1; m; m &= m - 1)
-                    pairs[off0 + w++] = make_int2((int)row, (int)(c1[(size_t)(__ffs(m) - 1) * n] >> 16));
+#pragma unroll
+                for (int g = 0; g < TC_GROUPS; g++) {
+                    const uint32_t* cg = c0 + (size_t)g * TC_LIST * n;
+                    for (unsigned m = msk[g]; m; m &= m - 1)
+                        pairs[off0 + w++] = make_int2((int)row, (int)(cg[(size_t)(__ffs(m) - 1) * n] >> 16));
+                }
             }
             rowpair[row] = make_int2(fits ? (int)off0 : 0, (full || !fits) ? -1 : c);
         }
@@ -314,11 +320,12 @@ __global__ void k_patch_flagged(const float* __restrict__ X, const float* __rest
 }
 
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels, double* min_dist,
-                          int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st) {
+                          int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st, int* nlaunch) {
     const int64_t rb = std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, (int64_t)num_sms * 8));
     k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.pairs, a.pair_cap, a.rowpair, a.cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    *nlaunch = 4;
     // pair evaluation: a persistent grid of the resident blocks
     const bool vec = (a.d % 4 == 0) && a.d <= 256 && ((uintptr_t)X % 16 == 0) && ((uintptr_t)C % 16 == 0);
     const void* fn = !vec ? (const void*)k_pair_eval<0>
@@ -340,7 +347,7 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t amb_smem = (size_t)8 * AMB_B * a.d * sizeof(double);  // 8 warps per block
-    e = cudaFuncSetAttribute(k_amb_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amb_smem);
+    e = allow_max_smem(k_amb_fp64);
     if (e != cudaSuccess) return e;
     k_amb_fp64<<<(unsigned)num_sms, 256, amb_smem, st>>>(amb_list, &a.cnt->amb_count, a.rowpair, a.pairs, a.v32, X, C,
                                                           a.d, a.tp.gamma32, labels, min_dist, a.cnt);

@@ -30,7 +30,9 @@
 
 namespace km {
 
-constexpr int TC_THREADS = 320;
+constexpr int TC_NG = TC_GROUPS;             // epilogue groups of four warps
+constexpr int TC_CW = 2;                     // 32-column TMEM chunks per epilogue step
+constexpr int TC_THREADS = 64 + 128 * TC_NG;  // producer warp, MMA warp, epilogue warps
 constexpr int TC_BM = 128;
 constexpr int TC_L = TC_LIST;  // candidate slots per row and epilogue group
 constexpr int SMEM_BUDGET = 227 * 1024;
@@ -47,8 +49,8 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     L.a_bytes = (size_t)kchunks * TC_BM * 128;
     L.b_bytes = (size_t)kchunks * BN * 128;
     (void)k;
-    const size_t lists = (size_t)2 * (TC_L + 1) * TC_BM * 4   // per-row candidate lists (+1 dummy slot) of both groups
-                         + (size_t)2 * TC_BM * 8;         // per-row running minimum published by each group
+    const size_t lists = (size_t)TC_NG * (TC_L + 1) * TC_BM * 4   // per-row candidate lists (+1 dummy slot) of every group
+                         + (size_t)TC_NG * TC_BM * 8;         // per-row running minimum published by each group
     const size_t fixed = 1024 /*align slack*/ + lists + 256 /*barriers*/;
     L.NA = 2;
     size_t rem = (size_t)SMEM_BUDGET - fixed - 2 * L.a_bytes;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // read through the read-only cache: one broadcast load per float4
     const float* __restrict__ qg = a.qpad;
     uint32_t* lists = reinterpret_cast<uint32_t*>(smem + L.list_off);
-    float2* mshare = reinterpret_cast<float2*>(smem + L.list_off + (size_t)2 * (TC_L + 1) * TC_BM * 4);
+    float2* mshare = reinterpret_cast<float2*>(smem + L.list_off + (size_t)TC_NG * (TC_L + 1) * TC_BM * 4);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* a_full = bars;            // [2]
     uint64_t* a_empty = bars + 2;       // [2]
@@ -172,8 +174,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 26);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 27);
     // TMEM holds NBUF accumulators of BN columns (512 columns in all); tile t
-    // uses buffer t % NBUF and is drained by epilogue group t % 2, so each group
-    // owns NBUF / 2 buffers and the MMA can run ahead of both groups.
+    // uses buffer t % NBUF and is drained by epilogue group t % TC_NG, so the
+    // groups work on consecutive tiles at once and the MMA fills the buffers
+    // ahead of them.
     constexpr int NBUF = 512 / BN;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) tmem_alloc(tmem_slot, 512);
     if (warp >= 2) {
-        for (int j = threadIdx.x - 64; j < 2 * TC_BM; j += TC_THREADS - 64)
+        for (int j = threadIdx.x - 64; j < TC_NG * TC_BM; j += TC_THREADS - 64)
             mshare[j] = make_float2(INFINITY, __int_as_float(-1));
     }
     tc_fence_before();
@@ -276,8 +279,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        // Two groups of four warps; group g drains accumulator buffer g, i.e.
-        // the tiles with an index of parity g, so the two groups overlap.
+        // TC_NG groups of four warps; group g drains the tiles t with
+        // t mod TC_NG == g, so the groups overlap.
         const int g = (warp - 2) >> 2;
         const int quarter = warp & 3;  // TMEM lanes this warp may access
         const int r_in = quarter * 32 + lane;
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
             for (int nt = 0; nt < NT; nt++) {
                 const int64_t tc = (int64_t)iter * NT + nt;
-                if ((int)(tc & 1) != g) continue;
+                if ((int)(tc % TC_NG) != g) continue;
                 const int buf = (int)(tc % NBUF);
                 ok = mbar_wait(&acc_full[buf], (uint32_t)((tc / NBUF) & 1), abort_flag, status);
                 if (!ok) break;
@@ -322,73 +325,82 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int nch = min(BN / 32, (a.k - nt * BN + 31) / 32);
                 const uint32_t tbase = tmem_base + lane_addr + (uint32_t)(buf * BN);
                 if (MODE == 0) {
-                    // chunks are taken in pairs (64 columns): twice the independent work
-                    // per dependency chain, and the per-chunk fixed costs halve
-                    const int nch2 = (nch + 1) & ~1;  // padded columns have q = +inf: they never qualify
-                    for (int ch = 0; ch < nch2; ch += 2) {
+                    // TC_CW chunks of 32 columns per step (padded columns have q = +inf:
+                    // they never qualify)
+                    constexpr int NCOL = 32 * TC_CW, NQ = NCOL / 4;
+                    const int nchs = ((nch + TC_CW - 1) / TC_CW) * TC_CW;
+                    for (int ch = 0; ch < nchs; ch += TC_CW) {
                         const int col0 = nt * BN + ch * 32;
-                        uint32_t va[32], vb[32];
+                        uint32_t v[TC_CW][32];
                         __syncwarp();
-                        tmem_ld32_async(tbase + (uint32_t)(ch * 32), va);
-                        tmem_ld32_async(tbase + (uint32_t)(ch * 32 + 32), vb);
-                        const float4* q4 = reinterpret_cast<const float4*>(qg + col0);
-                        float4 qv[16];
 #pragma unroll
-                        for (int t4 = 0; t4 < 16; t4++) qv[t4] = __ldg(q4 + t4);
-                        const float2 mo = mshare[(g ^ 1) * TC_BM + r_in];
-                        tmem_wait_ld(va);
-                        tmem_wait_ld(vb);
+                        for (int c = 0; c < TC_CW; c++) tmem_ld32_async(tbase + (uint32_t)((ch + c) * 32), v[c]);
+                        const float4* q4 = reinterpret_cast<const float4*>(qg + col0);
+                        float4 qv[NQ];
+#pragma unroll
+                        for (int t4 = 0; t4 < NQ; t4++) qv[t4] = __ldg(q4 + t4);
+                        // the other groups' running minima of this row block (read before the wait)
+                        float mo = INFINITY;
+#pragma unroll
+                        for (int h = 0; h < TC_NG; h++) {
+                            const float2 o = mshare[h * TC_BM + r_in];
+                            if (h != g && __float_as_int(o.y) == (int)rb) mo = fminf(mo, o.x);
+                        }
+#pragma unroll
+                        for (int c = 0; c < TC_CW; c++) tmem_wait_ld(v[c]);
                         // e = q_j - 2 s g, two columns per packed FMA (each rounded as fmaf)
-                        float e[64];
+                        float e[NCOL];
                         const float2 n2 = make_float2(neg2s, neg2s);
 #pragma unroll
-                        for (int t4 = 0; t4 < 16; t4++) {
-                            const uint32_t* v = (t4 < 8) ? va : vb;
+                        for (int t4 = 0; t4 < NQ; t4++) {
+                            const uint32_t* vv = v[t4 / 8];
                             const int o = (t4 & 7) * 4;
                             const float4 qq = qv[t4];
-                            const float2 lo = __ffma2_rn(make_float2(__uint_as_float(v[o + 0]), __uint_as_float(v[o + 1])), n2,
+                            const float2 lo = __ffma2_rn(make_float2(__uint_as_float(vv[o + 0]), __uint_as_float(vv[o + 1])), n2,
                                                          make_float2(qq.x, qq.y));
-                            const float2 hi = __ffma2_rn(make_float2(__uint_as_float(v[o + 2]), __uint_as_float(v[o + 3])), n2,
+                            const float2 hi = __ffma2_rn(make_float2(__uint_as_float(vv[o + 2]), __uint_as_float(vv[o + 3])), n2,
                                                          make_float2(qq.z, qq.w));
                             e[4 * t4 + 0] = lo.x;
                             e[4 * t4 + 1] = lo.y;
                             e[4 * t4 + 2] = hi.x;
                             e[4 * t4 + 3] = hi.y;
                         }
-                        // quad minima (they steer the slow path) and the minimum of the pair
-                        float qm[16];
+                        // quad minima (they steer the slow path) and the minimum of the step
+                        float qm[NQ];
 #pragma unroll
-                        for (int qd = 0; qd < 16; qd++)
+                        for (int qd = 0; qd < NQ; qd++)
                             qm[qd] = fminf(fmin3(e[4 * qd + 0], e[4 * qd + 1], e[4 * qd + 2]), e[4 * qd + 3]);
-                        float c4[4];
+                        float c4[NQ / 4];
 #pragma unroll
-                        for (int i = 0; i < 4; i++) c4[i] = fminf(fmin3(qm[4 * i], qm[4 * i + 1], qm[4 * i + 2]), qm[4 * i + 3]);
-                        const float cmin = fminf(fmin3(c4[0], c4[1], c4[2]), c4[3]);
+                        for (int i = 0; i < NQ / 4; i++) c4[i] = fminf(fmin3(qm[4 * i], qm[4 * i + 1], qm[4 * i + 2]), qm[4 * i + 3]);
+                        float cmin = c4[0];
+#pragma unroll
+                        for (int i = 1; i < NQ / 4; i++) cmin = fminf(cmin, c4[i]);
                         m = fminf(m, cmin);
-                        // publish this group's running minimum; use the other group's (read
-                        // before the TMEM wait): any upper bound of the row minimum keeps the
-                        // window a superset of the final one
+                        // publish this group's running minimum; the others' (any upper bound
+                        // of the row minimum keeps the window a superset of the final one)
                         mshare[g * TC_BM + r_in] = make_float2(m, __int_as_float((int)rb));
-                        const float mm = (__float_as_int(mo.y) == (int)rb) ? fminf(m, mo.x) : m;
+                        const float mm = fminf(m, mo);
                         const float cthr = mm + W;
                         const float sthr = valid ? fmaxf(cthr, Fe) : -INFINITY;
                         unsigned qmask = 0;
 #pragma unroll
-                        for (int qd = 0; qd < 16; qd++) qmask |= (qm[qd] <= sthr) ? (1u << qd) : 0u;
+                        for (int qd = 0; qd < NQ; qd++) qmask |= (qm[qd] <= sthr) ? (1u << qd) : 0u;
                         // Slow path: each lane walks its own quads holding a candidate or a
                         // possibly flagged pair (the warp iterates as often as its busiest
                         // lane); the quad's values are picked from registers by a select tree
-                        // on the lane's own quad index, and the appends are branch-free stores
-                        // (a lane with nothing to add writes the dummy slot).
+                        // on the lane's own quad index; one branch-free append per quad (a
+                        // lane with nothing to add writes the dummy slot), the rare further
+                        // candidates of a quad after a warp vote.
                         if (__any_sync(0xffffffffu, qmask)) {
-                            if (__any_sync(0xffffffffu, cnt > TC_L - 8 && !ovf)) {
+                            if (__any_sync(0xffffffffu, cnt > TC_L - 4 * TC_CW && !ovf)) {
                                 // every lane packs its list (dropping entries that left the window)
                                 const int cc = compact_list(list, cnt, p + cthr);
                                 if (!ovf) cnt = cc;
                             }
                             __syncwarp();
 #pragma unroll
-                            for (int half = 0; half < 2; half++) {
+                            for (int half = 0; half < TC_CW; half++) {
                                 unsigned ph = (qmask >> (8 * half)) & 0xffu;
                                 const float* eh = e + 32 * half;
                                 while (__any_sync(0xffffffffu, ph)) {
@@ -406,8 +418,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     }
                                     const bool q0 = et[0] <= cthr, q1 = et[1] <= cthr, q2 = et[2] <= cthr, q3 = et[3] <= cthr;
                                     const int jq = col0 + 32 * half + 4 * qd;
-                                    // the quad's first candidate: one branch-free append (a lane with
-                                    // nothing to add writes the dummy slot)
                                     const int c1 = q0 ? 0 : (q1 ? 1 : (q2 ? 2 : 3));
                                     const float e1 = q0 ? et[0] : (q1 ? et[1] : (q2 ? et[2] : et[3]));
                                     {
@@ -418,7 +428,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         ovf |= (pc && !room);
                                         cnt += (pc && room) ? 1 : 0;
                                     }
-                                    // its further candidates (a quad rarely holds more than one)
                                     const int nq = (int)q0 + (int)q1 + (int)q2 + (int)q3;
                                     if (__any_sync(0xffffffffu, act && nq > 1 && !ovf)) {
 #pragma unroll
@@ -435,7 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
                             if (__any_sync(0xffffffffu, p + cmin <= F)) {
 #pragma unroll
-                                for (int t = 0; t < 64; t++) {
+                                for (int t = 0; t < NCOL; t++) {
                                     const float dh = p + e[t];
                                     if (dh <= F) nflag += pair_flagged(tp, a.cstat, col0 + t, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
                                 }
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // window W and this group's d^ minimum
                 uint32_t* ccol = a.cand + (size_t)g * TC_L * a.n + row;
                 for (int sl = 0; sl < cnt; sl++) ccol[(size_t)sl * a.n] = list[sl * TC_BM];
-                a.rowinfo[row * 2 + g] = make_int4(cnt, ovf, __float_as_int(W), __float_as_int(p + m));
+                a.rowinfo[row * TC_NG + g] = make_int4(cnt, ovf, __float_as_int(W), __float_as_int(p + m));
             }
             nflag_total += (unsigned long long)nflag;
         }
@@ -557,7 +566,7 @@ static cudaError_t launch_one(const CUtensorMap& mx, const CUtensorMap& mc, cons
                               cudaStream_t st) {
     TcLayout L = tc_layout(BN, a.kchunks, a.k);
     if (L.NS < 2) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_tc<FMT, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    cudaError_t e = allow_max_smem(k_tc<FMT, BN, MODE>);
     if (e != cudaSuccess) return e;
     const int64_t nrb = (a.n + TC_BM - 1) / TC_BM;
     const int grid = (int)std::min<int64_t>(nrb, (int64_t)num_sms);

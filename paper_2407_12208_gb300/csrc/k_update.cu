@@ -463,11 +463,11 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         e = cudaMemsetAsync(cnt32, 0, sizeof(int) * (size_t)k, st);
         if (e != cudaSuccess) return e;
         const int64_t nblk = (n + SCAT_ROWS - 1) / SCAT_ROWS;
-        e = cudaFuncSetAttribute(k_label_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        e = allow_max_smem(k_label_hist);
         if (e != cudaSuccess) return e;
         k_label_hist<<<(unsigned)nblk, 512, hsm, st>>>(labels, n, k, cnt32);
         k_bucket_scan<<<1, 1024, 0, st>>>(cnt32, k, off, cursor, item_off, counts);
-        e = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * hsm));
+        e = allow_max_smem(k_bucket_scatter);
         if (e != cudaSuccess) return e;
         k_bucket_scatter<<<(unsigned)nblk, 512, 2 * hsm, st>>>(labels, n, k, cursor, perm);
         // persistent grid: every block resident at once (a partial second wave
@@ -498,7 +498,7 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
     const size_t smem = sizeof(long long) * ((size_t)k * d + k);
     const int64_t total = n * d;
     if (smem <= 200 * 1024) {
-        e = cudaFuncSetAttribute(k_accumulate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_max_smem(k_accumulate<true>);
         if (e != cudaSuccess) return e;
         const int64_t blk = std::min<int64_t>((int64_t)num_sms, (total + 511) / 512);
         k_accumulate<true><<<(unsigned)std::max<int64_t>(blk, 1), 512, smem, st>>>(X, n, d, labels, k, absmax_bits,

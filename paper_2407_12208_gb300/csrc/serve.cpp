@@ -61,6 +61,7 @@ struct km_serve {
     int device = 0, num_sms = 148;
     char* arena = nullptr;
     size_t arena_bytes = 0;
+    size_t arena_usable = 0;  // the aligned part of the arena: no job larger than this ever fits
     std::mutex mu;
     std::condition_variable cv;
     std::map<size_t, size_t> free_blocks;  // offset -> size
@@ -189,6 +190,7 @@ km_status serve_create(km_serve** out, int device, int num_sms, void* arena, siz
     const uintptr_t a0 = (uintptr_t)arena, a1 = up256(a0);
     if (arena_bytes <= (a1 - a0) + 256) { delete s; return KM_EINVAL; }
     s->free_blocks[a1 - a0] = (arena_bytes - (a1 - a0)) & ~(size_t)255;
+    s->arena_usable = (arena_bytes - (a1 - a0)) & ~(size_t)255;
     if (const char* e = std::getenv("MPKM_SERVE_WORKERS")) {
         int v = std::atoi(e);
         if (v >= 1 && v <= 64) s->n_workers = v;
@@ -217,6 +219,12 @@ km_status serve_submit(km_serve* s, const km_job* job, uint64_t* job_id, std::st
                         up256(sizeof(int32_t) * (size_t)job->n);
     const size_t ws = km_internal_ws_bytes(job->n, job->d, job->k, &job->p);
     const size_t bytes = up256(data + ws);
+    // a job larger than the whole arena can never be admitted (checked before
+    // the host arrays are copied)
+    if (bytes > s->arena_usable) {
+        if (err) *err = "job needs more memory than the arena holds";
+        return KM_ENOMEM;
+    }
     Job* j = new Job();
     j->spec = *job;
     j->bytes = bytes;
@@ -224,16 +232,6 @@ km_status serve_submit(km_serve* s, const km_job* job, uint64_t* job_id, std::st
     j->C.assign(job->C_init, job->C_init + (size_t)job->k * job->d);
     j->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
-    // a job larger than the whole arena can never be admitted
-    size_t total = 0;
-    for (auto& kv : s->free_blocks) total += kv.second;
-    for (auto& kv : s->jobs)
-        if (kv.second->has_mem) total += kv.second->bytes;
-    if (bytes > total) {
-        delete j;
-        if (err) *err = "job needs more memory than the arena holds";
-        return KM_ENOMEM;
-    }
     j->id = s->next_id++;
     s->jobs[j->id] = j;
     s->pending.push_back(j);
@@ -250,6 +248,7 @@ km_status serve_poll(km_serve* s, uint64_t job_id, km_result* out) {
     if (j->state == JobState::Queued || j->state == JobState::Running) return KM_ENOTREADY;
     std::memset(out, 0, sizeof *out);
     out->status = j->status;
+    out->message = j->err.c_str();
     out->iters = j->iters;
     out->sse = j->sse;
     out->eta = j->eta;

@@ -1,0 +1,101 @@
+"""GPU tests of the serving engine (km_submit / km_poll / km_release /
+km_cancel): jobs of uneven n, d, k submitted together overlap on the device,
+and each result equals the same job run alone through the synchronous calls,
+bit for bit; admission refuses a job that can never fit the arena."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2407_12208_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sctx():
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import build
+    build.build()
+    c = pkg.Context(0, arena_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+def _wait(ctx, jid, timeout=120.0):
+    t0 = time.time()
+    while True:
+        r = ctx.poll(jid)
+        if r is not None:
+            return r
+        assert time.time() - t0 < timeout, "job %d did not finish" % jid
+        time.sleep(0.002)
+
+
+def _jobs():
+    """A mix: Lloyd runs and single assignments, 16-bit, E4M3 and direct paths."""
+    specs = [(0, "bf16", 20000, 128, 64), (1, "bf16", 30001, 32, 200), (0, "fp16", 9000, 64, 37),
+             (0, "e4m3", 12000, 64, 16), (1, "fp32", 8000, 8, 10), (0, "fp64", 3000, 2, 5),
+             (0, "bf16", 5000, 256, 128), (1, "fp16", 40000, 128, 1024)]
+    out = []
+    for i, (kind, low, n, d, k) in enumerate(specs):
+        X, C = workloads.gaussian_mixture(n, d, k, seed=100 + i)
+        out.append(dict(kind=kind, low=low, X=X, C=C))
+    return out
+
+
+def test_serving_mix_equals_alone(sctx):
+    import paper_2407_12208_gb300 as pkg
+    jobs = _jobs()
+    ids = []
+    for jb in jobs:
+        p = pkg.params(jb["low"], max_iter=6)
+        ids.append(sctx.submit(jb["X"], jb["C"], p, kind=jb["kind"]))
+    results = [_wait(sctx, j) for j in ids]
+    for jb, jid, r in zip(jobs, ids, results):
+        assert r["status"] == pkg._binding.KM_OK
+        n, d = jb["X"].shape
+        k = jb["C"].shape[0]
+        lab_s = pkg.device_array(r["labels"], (n,), "<i4").cpu().numpy()
+        C_s = pkg.device_array(r["C"], (k, d), "<f4").cpu().numpy()
+        p = pkg.params(jb["low"], max_iter=6)
+        Xd = torch.from_numpy(jb["X"]).cuda()
+        Cd = torch.from_numpy(jb["C"]).cuda()
+        if jb["kind"] == 0:
+            C_a, lab_a, _, _, _ = sctx.lloyd_run(Xd, Cd, p)
+            torch.cuda.synchronize()
+            assert np.array_equal(C_s.view(np.uint32), C_a.cpu().numpy().view(np.uint32))
+        else:
+            lab_a, _, _ = sctx.assign(Xd, Cd, p)
+            torch.cuda.synchronize()
+            assert np.array_equal(C_s.view(np.uint32), jb["C"].view(np.uint32))  # centres returned as given
+        assert np.array_equal(lab_s, lab_a.cpu().numpy())
+        assert r["latency_ms"] >= r["queue_ms"] >= 0.0
+        sctx.release(jid)
+
+
+def test_serving_refuses_a_job_that_never_fits(sctx):
+    import paper_2407_12208_gb300 as pkg
+    X = np.zeros((20_000_000, 16), dtype=np.float32)  # 1.3 GB of points alone: more than the 1 GB arena
+    C = np.zeros((4, 16), dtype=np.float32)
+    with pytest.raises(pkg.KmError) as ei:
+        sctx.submit(X, C, pkg.params("bf16"), kind=1)
+    assert ei.value.status == pkg._binding.KM_ENOMEM
+
+
+def test_serving_cancel_and_release(sctx):
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.gaussian_mixture(50000, 64, 64, seed=7)
+    jid = sctx.submit(X, C, pkg.params("bf16", max_iter=200, tau=0.0), kind=0)
+    sctx.cancel(jid)
+    r = _wait(sctx, jid)
+    assert r["status"] in (pkg._binding.KM_ECANCELLED, pkg._binding.KM_OK)
+    sctx.release(jid)
+    # the arena is free again: a job of half its size is admitted and finishes
+    X2, C2 = workloads.gaussian_mixture(200000, 128, 32, seed=8)
+    j2 = sctx.submit(X2, C2, pkg.params("bf16", max_iter=2), kind=0)
+    r2 = _wait(sctx, j2)
+    assert r2["status"] == pkg._binding.KM_OK
+    sctx.release(j2)
