@@ -43,6 +43,23 @@ def _dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself when there is one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units processed by all ranks (weak scaling: the same work per rank) per second."""
+    return units_per_rank * world / seconds
+
+
 def _measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -195,15 +212,10 @@ def run_ours(args):
     ctx.set_profiling(False)
     phases = ctx.phase_times()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_per_step = ms / args.steps
     pairs_per_step = float(n) * k
-    value = pairs_per_step * world / (ms_per_step / 1e3)
+    value = whole_job_rate(pairs_per_step, world, ms_per_step / 1e3)
 
     # ------------------------------------------------ roofline of the screen kernel
     peaks = _measured_peaks()
@@ -252,14 +264,9 @@ def run_ours(args):
         e2e_step()
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / max(e2e_steps, 1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / max(e2e_steps, 1), world, dev)
     if e2e_steps:
-        e2e = {"value": pairs_per_step * world / (e2e_ms / 1e3), "unit": "pairs/s",
+        e2e = {"value": whole_job_rate(pairs_per_step, world, e2e_ms / 1e3), "unit": "pairs/s",
                "h2d_bytes_per_step": int(Xh.numel() * 4 + Ch.numel() * 4),
                "d2h_bytes_per_step": int(lab_h.numel() * 4 + md_h.numel() * 8), "ms_per_step": e2e_ms}
 

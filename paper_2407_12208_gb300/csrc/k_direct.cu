@@ -130,10 +130,11 @@ template <bool FP32_FIRST>
 __global__ void __launch_bounds__(256) k_rows_full(const float* __restrict__ X, const float* __restrict__ C, int k,
                                                    int d, const int32_t* __restrict__ row_list,
                                                    const int* __restrict__ row_count, int32_t* __restrict__ labels,
-                                                   double* __restrict__ min_dist, DevCounters* cnt, float gamma32) {
+                                                   double* __restrict__ min_dist, DevCounters* cnt, float gamma32,
+                                                   int keep_vals) {
     extern __shared__ float sh[];
     float* xs = sh;                      // d
-    float* vs = sh + ((d + 3) & ~3);     // k fp32 values
+    float* vs = sh + ((d + 3) & ~3);     // k fp32 values when they fit (keep_vals), else recomputed
     __shared__ Top2 red[8];
     __shared__ double rv[8];
     __shared__ int rj[8];
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(256) k_rows_full(const float* __restrict__ X, 
                     const float u = xs[l] - c[l];
                     s = fmaf(u, u, s);
                 }
-                vs[j] = s;
+                if (keep_vals) vs[j] = s;
                 ev32++;
                 if (s < t.b1) { t.b2 = t.b1; t.b1 = s; t.j1 = j; }
                 else if (s < t.b2) t.b2 = s;
@@ -189,7 +190,20 @@ __global__ void __launch_bounds__(256) k_rows_full(const float* __restrict__ X, 
             double best = INFINITY;
             int arg = 0x7fffffff;
             for (int j = tid; j < k; j += 256) {
-                if (FP32_FIRST && !(vs[j] * (1.0f - gamma32) <= thr)) continue;
+                if (FP32_FIRST) {
+                    float v;
+                    if (keep_vals) {
+                        v = vs[j];
+                    } else {  // the same loop as above: the same value
+                        const float* c = C + (int64_t)j * d;
+                        v = 0.0f;
+                        for (int l = 0; l < d; l++) {
+                            const float u = xs[l] - c[l];
+                            v = fmaf(u, u, v);
+                        }
+                    }
+                    if (!(v * (1.0f - gamma32) <= thr)) continue;
+                }
                 const double s = direct64(xs, C + (int64_t)j * d, d);
                 ev64++;
                 if (s < best) { best = s; arg = j; }
@@ -256,16 +270,25 @@ cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const fl
 cudaError_t launch_rows_full(bool fp32_first, const float* X, const float* C, int k, int d, const int32_t* row_list,
                              const int* row_count, int32_t* labels, double* min_dist, DevCounters* cnt,
                              float gamma32, int num_sms, cudaStream_t st) {
-    const size_t sm = (size_t)(((d + 3) & ~3) + k) * sizeof(float);
-    cudaError_t e;
+    // x in shared memory, and the k fp32 values of the first pass when they fit
+    const void* fn = fp32_first ? (const void*)k_rows_full<true> : (const void*)k_rows_full<false>;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const size_t xs_bytes = (size_t)((d + 3) & ~3) * sizeof(float);
+    const size_t avail = (size_t)kMaxBlockSmem - fa.sharedSizeBytes;
+    const int keep = fp32_first && xs_bytes + (size_t)k * sizeof(float) <= avail;
+    const size_t sm = xs_bytes + (keep ? (size_t)k * sizeof(float) : 0);
     if (fp32_first) {
         e = allow_max_smem(k_rows_full<true>);
         if (e != cudaSuccess) return e;
-        k_rows_full<true><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32);
+        k_rows_full<true><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32,
+                                                        keep);
     } else {
         e = allow_max_smem(k_rows_full<false>);
         if (e != cudaSuccess) return e;
-        k_rows_full<false><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32);
+        k_rows_full<false><<<num_sms * 2, 256, sm, st>>>(X, C, k, d, row_list, row_count, labels, min_dist, cnt, gamma32,
+                                                         0);
     }
     return cudaGetLastError();
 }

@@ -300,3 +300,27 @@ def test_lloyd_step_equals_assign_then_update(ctx, low, empty, shape):
     assert np.array_equal(got[3], ref[3])
     assert sh2 == sh1
     assert ref[3][-1] == 0 or empty == "farthest"
+
+
+def test_tc_large_k_full_row_path(ctx):
+    """k = 57344: the full-row kernel's per-centre values no longer fit in
+    shared memory and are recomputed in its binary64 pass.  In the
+    cancellation regime every pair fails the reliability test, so every row
+    goes through that kernel; a duplicated centre makes ties that only the
+    binary64 pass decides (lowest index)."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = 60000, 16, 57344
+    X, C = workloads.cancellation(n, d, k, seed=71)
+    C[1] = C[0]
+    lab, md, nf, st = _run_assign(ctx, X, C, "bf16")
+    assert st["overflow_rows"] + st["ambiguous_rows"] > 0
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([rng.choice(n, 48, replace=False), np.nonzero((X == C[0]).all(1))[0]]))
+    olab, od1, od2 = oracle.assign(X[rows], C)
+    margin = np.where(np.isfinite(od2), (od2 - od1) / np.maximum(od2, 1e-300), np.inf)
+    sel = margin > MARGIN
+    assert np.array_equal(lab[rows][sel], olab[sel])
+    ties = ~sel
+    if ties.any():  # exact ties: lowest index, as the oracle
+        assert np.array_equal(lab[rows][ties], olab[ties])
+    np.testing.assert_allclose(md[rows], od1, rtol=RTOL_MIXED, atol=1e-30)
