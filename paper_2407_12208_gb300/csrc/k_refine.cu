@@ -97,10 +97,10 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
                                                      int2* __restrict__ pairs, int64_t cap,
                                                      int2* __restrict__ rowpair, DevCounters* cnt) {
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r0 = w0 * 32; r0 < n; r0 += nw * 32) {
-        const int64_t row = r0 + lane;
+    // rounds of blockDim rows per block, the same count in every warp (the
+    // reservation synchronises the block)
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = b0 + threadIdx.x;
         const bool valid = row < n;
         int c = 0;
         bool full = false;
@@ -137,17 +137,27 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
             msk[g] = m;
             c += __popc(m);
         }
+        // one reservation per block: lane prefix sums, then warp totals through
+        // shared memory (every warp of the block takes part in each round)
         int incl = c;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int o = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += o;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 31 && total) base = atomicAdd(&cnt->npairs, (unsigned long long)total);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        const int64_t off0 = (int64_t)base + incl - c;
+        __shared__ int wtot[8];
+        __shared__ unsigned long long bbase;
+        const int wib = threadIdx.x >> 5;
+        if (lane == 31) wtot[wib] = incl;
+        __syncthreads();
+        int wpre = 0, btot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            wpre += (w < wib) ? wtot[w] : 0;
+            btot += wtot[w];
+        }
+        if (threadIdx.x == 0) bbase = btot ? atomicAdd(&cnt->npairs, (unsigned long long)btot) : 0ull;
+        __syncthreads();
+        const int64_t off0 = (int64_t)bbase + wpre + incl - c;
         const bool fits = off0 + c <= cap;
         if (valid) {
             if (!full && fits) {
@@ -321,7 +331,15 @@ __global__ void k_patch_flagged(const float* __restrict__ X, const float* __rest
 
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels, double* min_dist,
                           int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st, int* nlaunch) {
-    const int64_t rb = std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, (int64_t)num_sms * 8));
+    // persistent grids: the resident blocks only
+    int sel_per_sm = 1, cert_per_sm = 1;
+    cudaError_t e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sel_per_sm, k_cand_select, 256, 0);
+    if (e0 != cudaSuccess) return e0;
+    e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cert_per_sm, k_certify, 256, 0);
+    if (e0 != cudaSuccess) return e0;
+    const int64_t rows_blocks = std::max<int64_t>(1, (a.n + 255) / 256);
+    const int64_t rb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(sel_per_sm, 1));
+    const int64_t cb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(cert_per_sm, 1));
     k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.pairs, a.pair_cap, a.rowpair, a.cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -342,7 +360,7 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     else k_pair_eval<8><<<blocks, 256, 0, st>>>(X, C, a.d, a.pairs, np, a.pair_cap, a.v32);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_certify<<<(unsigned)rb, 256, 0, st>>>(a.rowpair, a.n, a.pairs, a.v32, X, C, a.d, a.tp.gamma32, labels, min_dist,
+    k_certify<<<(unsigned)cb, 256, 0, st>>>(a.rowpair, a.n, a.pairs, a.v32, X, C, a.d, a.tp.gamma32, labels, min_dist,
                                              full_list, amb_list, a.cnt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
