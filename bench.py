@@ -32,6 +32,12 @@ WORKLOADS = {
             "dist+argmin, X uniform[0,1) 1e6 x 128 fp32, C = 1024 distinct rows of X"),
     "c2b": ("cancellation", 1_000_000, 128, 1024,
             "dist+argmin, X = 1e3 + N(0, 1e-2^2) 1e6 x 128 fp32, C = 1024 distinct rows of X"),
+    "c3": ("gaussian_mixture", 4_000_000, 64, 256,
+           "Lloyd iteration, Gaussian mixture 4e6 x 64 fp32, k = 256 (centre coordinates N(0, 25), cluster std "
+           "log-uniform [0.1, 2]), C = 256 distinct rows of X"),
+    "c4": ("voronoi_image", 4096 * 4096, 5, 16,
+           "Lloyd iteration, 4096 x 4096 Voronoi image (16 regions, colour + N(0, 0.02^2)), features RGB + xy, "
+           "d = 5, k = 16"),
 }
 METRIC = "point-center pairs/s (dist+argmin)"
 
@@ -160,12 +166,17 @@ def run_ours(args):
     if args.n:
         n = args.n
         desc += " (first %d rows)" % n
-    X, C = getattr(workloads, gen)(n, d, k, seed=15 + rank)
+    if gen == "voronoi_image":
+        X, C = workloads.voronoi_image(4096, 4096, 16, k, seed=15 + rank)
+        X = X[:n]
+    else:
+        X, C = getattr(workloads, gen)(n, d, k, seed=15 + rank)
     dev = torch.device("cuda", local)
     Xd = torch.from_numpy(X).to(dev)
     Cd = torch.from_numpy(C).to(dev)
     ctx = pkg.Context(local)
     p = pkg.params(args.low, "tc", rho=5.0)
+    tensor_path = args.low in ("bf16", "fp16", "e4m3")
     labels = torch.empty(n, dtype=torch.int32, device=dev)
     md = torch.empty(n, dtype=torch.float64, device=dev)
     Cn = torch.empty_like(Cd)
@@ -233,8 +244,20 @@ def run_ours(args):
         peak = peak * 2.0
         peak_src += " x2 (nominal fp8/bf16 ratio)"
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": _profile_traffic(n),
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": _profile_traffic(n) if (args.workload == "c2a" and args.low == "bf16") else None,
             "kernel": "k_tc (tcgen05 screen)", "algorithmic_flops_per_launch": flops, "peak_source": peak_src}
+    if not tensor_path:
+        # direct-formula assignment (small d): bound by HBM, X read once, labels
+        # and min_dist written
+        dir_ms, dir_cnt = phases["direct"]
+        nbytes = n * d * 4.0 + n * 12.0
+        gbs = nbytes / (dir_ms / max(dir_cnt, 1) / 1e3) / 1e9 if dir_cnt else None
+        hbm = (peaks or {}).get("hbm_gbs") or 6800.0
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if gbs else None,
+                "traffic": None, "kernel": "k_direct_assign<%s>" % ("float" if args.low == "fp32" else "double"),
+                "algorithmic_bytes_per_launch": nbytes,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
 
     # ------------------------------------------------------------- end to end
     e2e = None
@@ -436,7 +459,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2a")
-    ap.add_argument("--low", choices=["bf16", "fp16", "e4m3"], default="bf16")
+    ap.add_argument("--low", choices=["bf16", "fp16", "e4m3", "fp32", "fp64"], default="bf16")
     ap.add_argument("--cpu-rows", type=int, default=100_000)
     ap.add_argument("--ref-rows", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -62,7 +62,7 @@ struct PhaseScope {
 
 namespace {
 
-constexpr int kSumParts = 256;
+constexpr int kSumParts = 1024;
 
 km_status fail(km_ctx* c, km_status s, const char* fmt, ...) {
     if (c) {
@@ -257,7 +257,7 @@ bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
 // One assignment of X against C into labels/min_dist (all device).
 // x_absmax (nullable, zeroed by the caller): max |x| over X, folded out of the
-// quantisation pass (tensor-core paths only).
+// quantisation pass (tensor-core paths) or of the direct distances.
 km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
                      int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st,
                      unsigned* x_absmax = nullptr) {
@@ -267,7 +267,7 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
         {
             PhaseScope ps(ctx, KM_PHASE_DIRECT, st);
             KL(1, launch_direct_assign(acc64, X, n, C, k, d, nullptr, nullptr, labels, min_dist, w.amb_list, w.cnt,
-                                       tp.gamma32, ctx->num_sms, st));
+                                       tp.gamma32, ctx->num_sms, st, x_absmax));
         }
         if (!acc64) {
             PhaseScope ps(ctx, KM_PHASE_FULLROW, st);
@@ -309,10 +309,21 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
         ctx->launches += (uint64_t)nl;
     }
     {
-        // rows whose candidate list overflowed: full-row fp32 direct, binary64 where uncertified
+        // rows whose candidate list overflowed (all of them when every pair fails
+        // the reliability test): fp32 direct distances to every centre with
+        // Theorem 4.1's certificate, then binary64 for the rows left open.  The
+        // near-tie list was consumed by the refinement and now takes those rows.
         PhaseScope ps(ctx, KM_PHASE_FULLROW, st);
-        KL(1, launch_rows_full(true, X, C, k, d, w.ovf_list, &w.cnt->ovf_count, labels, min_dist, w.cnt, tp.gamma32,
-                               ctx->num_sms, st));
+        if (d <= 256) {  // the direct kernel's row tile fits in shared memory
+            CK(cudaMemsetAsync(&w.cnt->amb_count, 0, sizeof(int), st));
+            KL(1, launch_direct_assign(false, X, n, C, k, d, w.ovf_list, &w.cnt->ovf_count, labels, min_dist,
+                                       w.amb_list, w.cnt, tp.gamma32, ctx->num_sms, st));
+            KL(1, launch_rows_full(false, X, C, k, d, w.amb_list, &w.cnt->amb_count, labels, min_dist, w.cnt,
+                                   tp.gamma32, ctx->num_sms, st));
+        } else {  // one block per row
+            KL(1, launch_rows_full(true, X, C, k, d, w.ovf_list, &w.cnt->ovf_count, labels, min_dist, w.cnt,
+                                   tp.gamma32, ctx->num_sms, st));
+        }
     }
     (void)esz;
     return KM_OK;
@@ -532,16 +543,15 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
     CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
-    // assignment (Alg. 3 step 1); the quantisation pass also yields max |x|
-    const bool fused = is_tc(p->low);
-    if (fused) CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
-    s = run_assign(ctx, X, n, C_old, k, d, p, labels, md, w, false, st, fused ? u.absmax : nullptr);
+    // assignment (Alg. 3 step 1); its pass over X (quantisation, or the direct
+    // distances) also yields max |x|
+    CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
+    s = run_assign(ctx, X, n, C_old, k, d, p, labels, md, w, false, st, u.absmax);
     if (s != KM_OK) return s;
     KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
     // centre update (Eq. (center)) on the labels just computed
     {
         PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-        if (!fused) KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
         KL(4, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
         KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts, u.shift,
                               u.taken, st));

@@ -39,6 +39,9 @@ struct ColMax {
     float ncq2;  // max ||c~_j||^2
     float cscale;  // uniform power-of-two scale of the quantised centres (E4M3), 1 otherwise
     float pad[2];
+    // minima of the same statistics: a lower bound of every pair's threshold
+    float nc_min, nrc_min, ncq_min, q_min, ncq2_min;
+    float pad2[3];
 };
 
 // Parameters of the reliability test / candidate window, host-computed.
@@ -88,10 +91,11 @@ cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMa
 // (the plain FP64 path) else fp32 with certification; rows = all n, or the
 // device list row_list[0 .. *row_count).  Uncertified fp32 rows are appended
 // to amb_list / cnt->amb_count.
+// absmax_out (nullable, zeroed by the caller): max |x| over the rows read.
 cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const float* C, int k, int d,
                                  const int32_t* row_list, const int* row_count, int32_t* labels,
                                  double* min_dist, int32_t* amb_list, DevCounters* cnt, float gamma32,
-                                 int num_sms, cudaStream_t st);
+                                 int num_sms, cudaStream_t st, unsigned* absmax_out = nullptr);
 // exact argmin of the rows of a device list, one block per row: fp32 direct
 // values of all centres, certified, binary64 where still open (fp32_first),
 // or binary64 for all centres.

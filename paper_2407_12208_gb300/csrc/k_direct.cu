@@ -9,6 +9,8 @@
 //    (warp per row, lanes over centres), exact argmin with the lowest index
 //    on ties.  Products and sums are rounded separately (no FMA) so the
 //    values equal the CPU oracle's bit for bit.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -25,9 +27,14 @@ __global__ void __launch_bounds__(DA_ROWS) k_direct_assign(const float* __restri
                                                            int32_t* __restrict__ labels,
                                                            double* __restrict__ min_dist,
                                                            int32_t* __restrict__ amb_list, DevCounters* cnt,
-                                                           float gamma32) {
+                                                           float gamma32, unsigned* __restrict__ absmax_out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int ldx = d + 1;  // odd row stride: conflict-free per-thread row reads
+    float amx = 0.0f;  // largest |x| this thread stages (absmax_out)
+    // fp32 with d % 4 == 0: rows read four coordinates at a time, row stride
+    // d + 4 (16-byte aligned; consecutive rows 16 bytes apart modulo the 128
+    // banks-bytes when d % 32 == 0: conflict-free); else an odd stride
+    const bool vec4 = sizeof(T) == 4 && (d % 4) == 0;
+    const int ldx = vec4 ? d + 4 : d + 1;
     float* Xs = reinterpret_cast<float*>(smem);
     T* Cs = reinterpret_cast<T*>(smem + (((size_t)DA_ROWS * ldx * sizeof(float) + 15) & ~(size_t)15));
     const int64_t nrows = row_list ? (int64_t)(*row_count) : n;
@@ -39,7 +46,9 @@ __global__ void __launch_bounds__(DA_ROWS) k_direct_assign(const float* __restri
         for (int e = tid; e < rows_here * d; e += DA_ROWS) {
             const int r = e / d, l = e - r * d;
             const int64_t gi = row_list ? (int64_t)row_list[base + r] : base + r;
-            Xs[r * ldx + l] = X[gi * d + l];
+            const float xv = X[gi * d + l];
+            amx = fmaxf(amx, fabsf(xv));
+            Xs[r * ldx + l] = xv;
         }
         T b1 = (T)INFINITY, b2 = (T)INFINITY;
         int j1 = 0;
@@ -53,13 +62,36 @@ __global__ void __launch_bounds__(DA_ROWS) k_direct_assign(const float* __restri
 #pragma unroll
                 for (int c = 0; c < DA_TC; c++) acc[c] = (T)0;
                 const float* xr = Xs + tid * ldx;
-                for (int l = 0; l < d; l++) {
-                    const T xl = (T)xr[l];
+                if (sizeof(T) == 4 && vec4) {
+                    // four coordinates per shared-memory load on both sides (the same
+                    // order of operations per centre as the scalar loop below)
+                    for (int l = 0; l < d; l += 4) {
+                        const float4 x4 = *reinterpret_cast<const float4*>(xr + l);
 #pragma unroll
-                    for (int c = 0; c < DA_TC; c++) {
-                        if (c < tc) {
-                            const T t = xl - Cs[c * d + l];
-                            acc[c] = fma(t, t, acc[c]);
+                        for (int c = 0; c < DA_TC; c++) {
+                            if (c < tc) {
+                                const float4 c4 = *reinterpret_cast<const float4*>(
+                                    reinterpret_cast<const float*>(Cs) + c * d + l);
+                                T t = (T)x4.x - (T)c4.x;
+                                acc[c] = fma(t, t, acc[c]);
+                                t = (T)x4.y - (T)c4.y;
+                                acc[c] = fma(t, t, acc[c]);
+                                t = (T)x4.z - (T)c4.z;
+                                acc[c] = fma(t, t, acc[c]);
+                                t = (T)x4.w - (T)c4.w;
+                                acc[c] = fma(t, t, acc[c]);
+                            }
+                        }
+                    }
+                } else {
+                    for (int l = 0; l < d; l++) {
+                        const T xl = (T)xr[l];
+#pragma unroll
+                        for (int c = 0; c < DA_TC; c++) {
+                            if (c < tc) {
+                                const T t = xl - Cs[c * d + l];
+                                acc[c] = fma(t, t, acc[c]);
+                            }
                         }
                     }
                 }
@@ -96,6 +128,82 @@ __global__ void __launch_bounds__(DA_ROWS) k_direct_assign(const float* __restri
         __syncthreads();
     }
     if (local_amb) atomicAdd(&cnt->amb_rows, local_amb);
+    if (absmax_out) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
+        if ((threadIdx.x & 31) == 0) atomicMax(absmax_out, __float_as_uint(amx));
+    }
+}
+
+// Small d (d <= 8) with C small enough to stay in shared memory for the
+// whole launch: one thread per row, the row in registers, every centre from
+// shared memory (all lanes read the same centre: a broadcast).  The same
+// fp32 operations, in the same order, and the same certificate as the tiled
+// kernel above, so the two give the same results.
+template <int D>
+__global__ void __launch_bounds__(256) k_direct_small(const float* __restrict__ X, int64_t n,
+                                                      const float* __restrict__ C, int k,
+                                                      const int32_t* __restrict__ row_list,
+                                                      const int* __restrict__ row_count,
+                                                      int32_t* __restrict__ labels, double* __restrict__ min_dist,
+                                                      int32_t* __restrict__ amb_list, DevCounters* cnt,
+                                                      float gamma32, unsigned* __restrict__ absmax_out) {
+    extern __shared__ __align__(16) float Csm[];
+    float amx = 0.0f;  // largest |x| of this thread's rows (absmax_out)
+    for (int e = threadIdx.x; e < k * D; e += blockDim.x) Csm[e] = C[e];
+    __syncthreads();
+    const int64_t nrows = row_list ? (int64_t)(*row_count) : n;
+    const float g = gamma32;
+    unsigned long long rows_done = 0, local_amb = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gi = row_list ? (int64_t)row_list[r] : r;
+        float x[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+            x[l] = X[gi * D + l];
+            amx = fmaxf(amx, fabsf(x[l]));
+        }
+        float b1 = INFINITY, b2 = INFINITY;
+        int j1 = 0;
+        for (int j = 0; j < k; j++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < D; l++) {
+                const float t = x[l] - Csm[j * D + l];
+                acc = fmaf(t, t, acc);
+            }
+            if (acc < b1) {
+                b2 = b1;
+                b1 = acc;
+                j1 = j;
+            } else if (acc < b2) {
+                b2 = acc;
+            }
+        }
+        labels[gi] = j1;
+        min_dist[gi] = (double)b1;
+        rows_done++;
+        // Theorem 4.1: true values lie in [v (1 - g), v (1 + g)]
+        if (!(b2 * (1.0f - g) > b1 * (1.0f + g))) {
+            const int slot = atomicAdd(&cnt->amb_count, 1);
+            amb_list[slot] = (int32_t)gi;
+            local_amb++;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        rows_done += __shfl_xor_sync(0xffffffffu, rows_done, off);
+        local_amb += __shfl_xor_sync(0xffffffffu, local_amb, off);
+    }
+    if (absmax_out) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (rows_done) atomicAdd(&cnt->fp32_evals, rows_done * (unsigned long long)k);
+        if (local_amb) atomicAdd(&cnt->amb_rows, local_amb);
+        if (absmax_out) atomicMax(absmax_out, __float_as_uint(amx));
+    }
 }
 
 // Exact argmin of listed rows, one 256-thread block per row.  Thread t takes
@@ -238,14 +346,37 @@ __global__ void __launch_bounds__(256) k_rows_full(const float* __restrict__ X, 
 }
 
 static size_t direct_smem(bool acc64, int d) {
-    size_t xs = (((size_t)DA_ROWS * (d + 1) * sizeof(float)) + 15) & ~(size_t)15;
+    const int ldx = (!acc64 && d % 4 == 0) ? d + 4 : d + 1;
+    size_t xs = (((size_t)DA_ROWS * ldx * sizeof(float)) + 15) & ~(size_t)15;
     return xs + (size_t)DA_TC * d * (acc64 ? 8 : 4);
 }
 
 cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const float* C, int k, int d,
                                  const int32_t* row_list, const int* row_count, int32_t* labels,
                                  double* min_dist, int32_t* amb_list, DevCounters* cnt, float gamma32,
-                                 int num_sms, cudaStream_t st) {
+                                 int num_sms, cudaStream_t st, unsigned* absmax_out) {
+    if (!acc64 && d <= 8 && (size_t)k * d * sizeof(float) <= 32 * 1024) {
+        // small d: C resident in shared memory, one thread per row, persistent grid
+        const size_t csm = (size_t)k * d * sizeof(float);
+        int per_sm = 1;
+        const void* fns[9] = {nullptr, (const void*)k_direct_small<1>, (const void*)k_direct_small<2>,
+                              (const void*)k_direct_small<3>, (const void*)k_direct_small<4>,
+                              (const void*)k_direct_small<5>, (const void*)k_direct_small<6>,
+                              (const void*)k_direct_small<7>, (const void*)k_direct_small<8>};
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[d], 256, csm);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * std::max(per_sm, 1)));
+        switch (d) {
+#define KM_SMALL(DD)                                                                                                  \
+    case DD:                                                                                                          \
+        k_direct_small<DD><<<(unsigned)grid, 256, csm, st>>>(X, n, C, k, row_list, row_count, labels, min_dist,      \
+                                                              amb_list, cnt, gamma32, absmax_out);                                \
+        break;
+            KM_SMALL(1) KM_SMALL(2) KM_SMALL(3) KM_SMALL(4) KM_SMALL(5) KM_SMALL(6) KM_SMALL(7) KM_SMALL(8)
+#undef KM_SMALL
+        }
+        return cudaGetLastError();
+    }
     size_t sm = direct_smem(acc64, d);
     int64_t blocks_needed = (n + DA_ROWS - 1) / DA_ROWS;
     int per_sm = (int)max((size_t)1, (size_t)(200 * 1024) / sm);
@@ -257,12 +388,12 @@ cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const fl
         e = allow_max_smem(k_direct_assign<double>);
         if (e != cudaSuccess) return e;
         k_direct_assign<double><<<(unsigned)grid, DA_ROWS, sm, st>>>(X, n, C, k, d, row_list, row_count, labels,
-                                                                     min_dist, amb_list, cnt, gamma32);
+                                                                     min_dist, amb_list, cnt, gamma32, absmax_out);
     } else {
         e = allow_max_smem(k_direct_assign<float>);
         if (e != cudaSuccess) return e;
         k_direct_assign<float><<<(unsigned)grid, DA_ROWS, sm, st>>>(X, n, C, k, d, row_list, row_count, labels,
-                                                                    min_dist, amb_list, cnt, gamma32);
+                                                                    min_dist, amb_list, cnt, gamma32, absmax_out);
     }
     return cudaGetLastError();
 }

@@ -340,8 +340,9 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
                          float* __restrict__ qpad, int kpad) {
     // q_j for the screening kernel, +inf on the padding so padded columns never win
     for (int j = threadIdx.x; j < kpad; j += blockDim.x) qpad[j] = (j < k) ? cstat[j].x : INFINITY;
-    __shared__ float red[5][32];
+    __shared__ float red[10][32];
     float a = 0, b = 0, c = 0, q = 0, c2 = 0;
+    float an = INFINITY, bn = INFINITY, cn = INFINITY, qn = INFINITY, c2n = INFINITY;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         float4 s = cstat[j];
         a = fmaxf(a, s.y);
@@ -349,6 +350,11 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
         c = fmaxf(c, s.z);
         q = fmaxf(q, s.x);
         c2 = fmaxf(c2, s.z * s.z);
+        an = fminf(an, s.y);
+        bn = fminf(bn, s.w);
+        cn = fminf(cn, s.z);
+        qn = fminf(qn, s.x);
+        c2n = fminf(c2n, s.z * s.z);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -357,19 +363,31 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
         c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
         q = fmaxf(q, __shfl_xor_sync(0xffffffffu, q, off));
         c2 = fmaxf(c2, __shfl_xor_sync(0xffffffffu, c2, off));
+        an = fminf(an, __shfl_xor_sync(0xffffffffu, an, off));
+        bn = fminf(bn, __shfl_xor_sync(0xffffffffu, bn, off));
+        cn = fminf(cn, __shfl_xor_sync(0xffffffffu, cn, off));
+        qn = fminf(qn, __shfl_xor_sync(0xffffffffu, qn, off));
+        c2n = fminf(c2n, __shfl_xor_sync(0xffffffffu, c2n, off));
     }
     const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    if (ln == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = c; red[3][w] = q; red[4][w] = c2; }
+    if (ln == 0) {
+        red[0][w] = a; red[1][w] = b; red[2][w] = c; red[3][w] = q; red[4][w] = c2;
+        red[5][w] = an; red[6][w] = bn; red[7][w] = cn; red[8][w] = qn; red[9][w] = c2n;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 1; i < (int)(blockDim.x / 32); i++) {
             a = fmaxf(a, red[0][i]); b = fmaxf(b, red[1][i]); c = fmaxf(c, red[2][i]);
             q = fmaxf(q, red[3][i]); c2 = fmaxf(c2, red[4][i]);
+            an = fminf(an, red[5][i]); bn = fminf(bn, red[6][i]); cn = fminf(cn, red[7][i]);
+            qn = fminf(qn, red[8][i]); c2n = fminf(c2n, red[9][i]);
         }
         ColMax o;
         o.nc = a; o.nrc = b; o.ncq = c; o.q = q; o.ncq2 = c2;
         o.cscale = cscale ? *cscale : 1.0f;
         o.pad[0] = o.pad[1] = 0.0f;
+        o.nc_min = an; o.nrc_min = bn; o.ncq_min = cn; o.q_min = qn; o.ncq2_min = c2n;
+        o.pad2[0] = o.pad2[1] = o.pad2[2] = 0.0f;
         *out = o;
     }
 }

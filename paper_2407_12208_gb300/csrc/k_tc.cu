@@ -311,6 +311,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             else F = -INFINITY;
             if (!valid) F = -INFINITY;  // rows past n: no flags, no candidates
             const float Fe = (F == -INFINITY) ? -INFINITY : F - p + fabsf(F) * 1e-6f;  // in e = d^ - p units
+            // every pair with d^ <= Fall is flagged whatever its column: the smallest
+            // threshold over the centres, less a margin for its fp32 evaluation
+            float Fall;
+            if (tp.test == 0)
+                Fall = tp.rho * (a1 * cm.nc_min + a2 * cm.nrc_min + a3 * cm.ncq_min + tp.kn * (p + cm.q_min)) * tp.bsafe;
+            else if (tp.test == 1)
+                Fall = tp.paper_coef * (xs.z * xs.z + cm.ncq2_min);
+            else
+                Fall = -INFINITY;
+            Fall = valid ? Fall * (1.0f - 1.0f / 65536.0f) - fabsf(Fall) * 1e-6f : -INFINITY;
             const float W = 2.0f * bmax * 1.001f + 1e-30f;      // candidate window
             float m = INFINITY;
             int cnt = 0, ovf = 0, nflag = 0;
@@ -443,10 +453,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 }
                             }
                             if (__any_sync(0xffffffffu, p + cmin <= F)) {
+                                // a step whose largest d^ is under every column's threshold is
+                                // flagged whole (padded columns hold +inf: never taken here)
+                                float cmax = e[0];
 #pragma unroll
-                                for (int t = 0; t < NCOL; t++) {
-                                    const float dh = p + e[t];
-                                    if (dh <= F) nflag += pair_flagged(tp, a.cstat, col0 + t, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
+                                for (int t = 1; t < NCOL; t++) cmax = fmaxf(cmax, e[t]);
+                                if (p + cmax <= Fall) {
+                                    nflag += NCOL;
+                                } else {
+#pragma unroll
+                                    for (int t = 0; t < NCOL; t++) {
+                                        const float dh = p + e[t];
+                                        if (dh <= F) nflag += pair_flagged(tp, a.cstat, col0 + t, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
+                                    }
                                 }
                             }
                         }

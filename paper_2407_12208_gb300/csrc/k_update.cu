@@ -318,6 +318,81 @@ __global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k
     }
 }
 
+// Small d and small k * d: rows in their natural order (one per lane,
+// coalesced), each warp keeps the 32-bit parts of every cluster's fixed-point
+// sum (and its count) in shared memory.  A segmented inclusive scan over the
+// warp's runs of equal labels (five shuffle levels, whatever the labels: an
+// image's pixels come in long runs) leaves each run's total in its last
+// lane, which adds it with a shared atomic.  Every AS_CHUNK rows the
+// accumulators are folded into the global int64 sums.  Integer additions
+// throughout: the order does not matter.
+constexpr int AS_CHUNK = 1024;   // rows per warp between folds (keeps each 32-bit part sum below 2^31)
+constexpr int AS_MAX_KD = 512;   // k * d bound of this path
+template <int D>
+__global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X, int64_t n, int k,
+                                                     const int32_t* __restrict__ labels,
+                                                     const unsigned* __restrict__ amax_bits,
+                                                     long long* __restrict__ sums, long long* __restrict__ counts) {
+    extern __shared__ unsigned acc_sm[];  // per warp: 3 * k * D parts, then k counts
+    const FixedScale fx(fixed_shift(*amax_bits, n));
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int kd = k * D;
+    unsigned* a = acc_sm + (size_t)wib * (3 * kd + k);
+    unsigned* cntw = a + 3 * kd;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c0 = w0 * AS_CHUNK; c0 < n; c0 += nw * AS_CHUNK) {
+        for (int e = lane; e < 3 * kd + k; e += 32) a[e] = 0u;
+        __syncwarp();
+        const int64_t c1 = min(n, c0 + AS_CHUNK);
+        for (int64_t base = c0; base < c1; base += 32) {
+            const int64_t i = base + lane;
+            const bool valid = i < c1;
+            const int j = valid ? labels[i] : -1;
+            unsigned v[3 * D + 1];  // true (unbiased) parts modulo 2^32, then the row count
+#pragma unroll
+            for (int l = 0; l < D; l++) {
+                unsigned b2 = FixedScale::kBias, b1 = FixedScale::kBias, b0 = FixedScale::kBias;
+                if (valid) fx.split(X[i * D + l], b2, b1, b0);
+                v[3 * l + 0] = b2 - FixedScale::kBias;
+                v[3 * l + 1] = b1 - FixedScale::kBias;
+                v[3 * l + 2] = b0 - FixedScale::kBias;
+            }
+            v[3 * D] = 1u;
+            const int jp = __shfl_up_sync(0xffffffffu, j, 1);
+            const bool head = lane == 0 || j != jp;
+            bool f = head;  // segment flag of the scan
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const bool fu = __shfl_up_sync(0xffffffffu, f, off);
+                const bool take = lane >= off && !f;
+#pragma unroll
+                for (int t = 0; t <= 3 * D; t++) {
+                    const unsigned u = __shfl_up_sync(0xffffffffu, v[t], off);
+                    if (take) v[t] += u;
+                }
+                if (take) f = fu;
+            }
+            const bool next_head = __shfl_down_sync(0xffffffffu, head, 1);
+            const bool tail = lane == 31 || next_head;
+            if (valid && tail) {
+                unsigned* aj = a + 3 * j * D;
+#pragma unroll
+                for (int t = 0; t < 3 * D; t++) atomicAdd(&aj[t], v[t]);
+                atomicAdd(&cntw[j], v[3 * D]);
+            }
+        }
+        __syncwarp();
+        for (int e = lane; e < kd; e += 32) {
+            const long long s64 = FixedScale::combine(a[3 * e + 0], a[3 * e + 1], a[3 * e + 2], 0u);
+            if (s64) atomicAdd(reinterpret_cast<unsigned long long*>(&sums[e]), (unsigned long long)s64);
+        }
+        for (int jj = lane; jj < k; jj += 32)
+            if (cntw[jj]) atomicAdd(reinterpret_cast<unsigned long long*>(&counts[jj]), (unsigned long long)cntw[jj]);
+        __syncwarp();
+    }
+}
+
 // mean = sum 2^-S / m in binary64, stored in fp32 (the working precision).
 __global__ void k_means(const long long* __restrict__ sums, const long long* __restrict__ counts,
                         const unsigned* __restrict__ amax_bits, int64_t n, int k, int d,
@@ -452,6 +527,24 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
                               int32_t* perm, int num_sms, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(long long) * (size_t)k * d, st);
     if (e != cudaSuccess) return e;
+    if (d <= 8 && (int64_t)k * d <= AS_MAX_KD) {
+        // small d: rows in order, per-warp shared accumulators
+        e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);
+        if (e != cudaSuccess) return e;
+        const size_t sm = (size_t)8 * (3 * (size_t)k * d + k) * sizeof(unsigned);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 8, (n + 8 * AS_CHUNK - 1) / (8 * AS_CHUNK)));
+        switch (d) {
+#define KM_ACC(DD)                                                                                                  \
+    case DD:                                                                                                        \
+        e = allow_max_smem(k_accum_small<DD>);                                                                      \
+        if (e != cudaSuccess) return e;                                                                             \
+        k_accum_small<DD><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, sums, counts);          \
+        break;
+            KM_ACC(1) KM_ACC(2) KM_ACC(3) KM_ACC(4) KM_ACC(5) KM_ACC(6) KM_ACC(7) KM_ACC(8)
+#undef KM_ACC
+        }
+        return cudaGetLastError();
+    }
     const size_t hsm = sizeof(int) * (size_t)k;
     const bool vec = d % 4 == 0 && ((uintptr_t)X % 16) == 0;
     const bool bucket = 2 * hsm <= 200 * 1024 && (d == 1 || d == 2 || d == 3 || d == 5 || (vec && d <= 512));
