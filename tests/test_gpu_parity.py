@@ -324,3 +324,20 @@ def test_tc_large_k_full_row_path(ctx):
     if ties.any():  # exact ties: lowest index, as the oracle
         assert np.array_equal(lab[rows][ties], olab[ties])
     np.testing.assert_allclose(md[rows], od1, rtol=RTOL_MIXED, atol=1e-30)
+
+
+def test_update_small_d_long_label_runs(ctx):
+    """The small-d centre sums: labels in long runs (as an image's pixels) and
+    enough rows that every warp folds its shared accumulators several times."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = 12_000_000, 1, 3
+    rng = np.random.default_rng(9)
+    X = (rng.standard_normal((n, d)) * 10.0).astype(np.float32)
+    lab = ((np.arange(n) // 1000) % k).astype(np.int32)
+    lab[::7777] = 1  # a few short runs inside the long ones
+    C = np.zeros((k, d), dtype=np.float32)
+    p = pkg.params("fp64", empty="keep")
+    Cn, cnt, _ = ctx.update_centroids(_dev(X), _dev(lab), _dev(C), p, min_dist=None)
+    oC, ocnt, _ = oracle.update(X, lab, C, 0, np.zeros(n))
+    assert np.array_equal(cnt.cpu().numpy(), ocnt)
+    np.testing.assert_allclose(Cn.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
