@@ -39,10 +39,13 @@ constexpr int SMEM_BUDGET = 227 * 1024;
 
 struct TcLayout {
     int BN, NA, NS, kchunks;
-    size_t a_bytes, b_bytes, list_off, bar_off, total;
+    size_t a_bytes, b_bytes, list_off, stage_off, bar_off, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
+// stg: each epilogue warp's staging area for its lanes' e values (16 float4
+// per lane, 8 KB per warp)
+constexpr size_t TC_STAGE_BYTES = (size_t)TC_NG * 4 * 16 * 32 * 16;
+__host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k, bool stg) {
     TcLayout L;
     L.BN = BN;
     L.kchunks = kchunks;
@@ -51,7 +54,8 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     (void)k;
     const size_t lists = (size_t)TC_NG * (TC_L + 1) * TC_BM * 4   // per-row candidate lists (+1 dummy slot) of every group
                          + (size_t)TC_NG * TC_BM * 8;         // per-row running minimum published by each group
-    const size_t fixed = 1024 /*align slack*/ + lists + 256 /*barriers*/;
+    const size_t stage = stg ? TC_STAGE_BYTES : 0;
+    const size_t fixed = 1024 /*align slack*/ + lists + stage + 256 /*barriers*/;
     L.NA = 2;
     size_t rem = (size_t)SMEM_BUDGET - fixed - 2 * L.a_bytes;
     if ((long long)rem < (long long)(2 * L.b_bytes)) {
@@ -61,7 +65,8 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k) {
     L.NS = (int)(rem / L.b_bytes);
     if (L.NS > 6) L.NS = 6;
     L.list_off = (size_t)L.NA * L.a_bytes + (size_t)L.NS * L.b_bytes;
-    L.bar_off = L.list_off + lists;
+    L.stage_off = L.list_off + lists;
+    L.bar_off = L.stage_off + stage;
     L.total = L.bar_off + 256 + 1024;
     return L;
 }
@@ -150,12 +155,12 @@ KM_DEV float fmin3(float a, float b, float c) {
     return r;
 }
 
-template <int FMT, int BN, int MODE>
+template <int FMT, int BN, int MODE, bool STG>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, const TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const TcLayout L = tc_layout(BN, a.kchunks, a.k);
+    const TcLayout L = tc_layout(BN, a.kchunks, a.k, STG);
     unsigned char* sA = smem;
     unsigned char* sB = smem + (size_t)L.NA * L.a_bytes;
     // q_j of every tile column (+inf on the padding: padded columns never win),
@@ -409,6 +414,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 if (!ovf) cnt = cc;
                             }
                             __syncwarp();
+                            if (STG) {
+                                // the lane's values staged in shared memory (quad-major: the
+                                // 32 lanes of a quad side by side, conflict-free both ways),
+                                // then one loop over all its quads: a 16-byte read per quad
+                                float4* stg = reinterpret_cast<float4*>(smem + L.stage_off) + (size_t)(warp - 2) * NQ * 32 + lane;
+#pragma unroll
+                                for (int qd = 0; qd < NQ; qd++)
+                                    stg[qd * 32] = make_float4(e[4 * qd], e[4 * qd + 1], e[4 * qd + 2], e[4 * qd + 3]);
+                                unsigned ph = qmask;
+                                while (__any_sync(0xffffffffu, ph)) {
+                                    const bool act = ph != 0;
+                                    const int qd = act ? __ffs(ph) - 1 : 0;
+                                    ph &= ph - 1;
+                                    const float4 ev = stg[qd * 32];
+                                    const float et[4] = {ev.x, ev.y, ev.z, ev.w};
+                                    const int jq = col0 + 4 * qd;
+                                    const bool q0 = et[0] <= cthr, q1 = et[1] <= cthr, q2 = et[2] <= cthr, q3 = et[3] <= cthr;
+                                    const int c1 = q0 ? 0 : (q1 ? 1 : (q2 ? 2 : 3));
+                                    const float e1 = q0 ? et[0] : (q1 ? et[1] : (q2 ? et[2] : et[3]));
+                                    {
+                                        const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
+                                        const bool room = cnt < TC_L;
+                                        const int slot = (pc && room) ? cnt : TC_L;
+                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1);
+                                        ovf |= (pc && !room);
+                                        cnt += (pc && room) ? 1 : 0;
+                                    }
+                                    const int nq = (int)q0 + (int)q1 + (int)q2 + (int)q3;
+                                    if (__any_sync(0xffffffffu, act && nq > 1 && !ovf)) {
+#pragma unroll
+                                        for (int c = 1; c < 4; c++) {
+                                            const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
+                                            const bool room = cnt < TC_L;
+                                            const int slot = (pc && room) ? cnt : TC_L;
+                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c]);
+                                            ovf |= (pc && !room);
+                                            cnt += (pc && room) ? 1 : 0;
+                                        }
+                                    }
+                                }
+                            } else {
 #pragma unroll
                             for (int half = 0; half < TC_CW; half++) {
                                 unsigned ph = (qmask >> (8 * half)) & 0xffu;
@@ -451,6 +497,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         }
                                     }
                                 }
+                            }
                             }
                             if (__any_sync(0xffffffffu, p + cmin <= F)) {
                                 // a step whose largest d^ is under every column's threshold is
@@ -575,29 +622,33 @@ size_t tc_smem_bytes(int fmt, int d, int k) {
     const int ldq = (fmt == 2) ? ((d + 15) / 16) * 16 : ((d + 7) / 8) * 8;
     const int kchunks = (ldq * esize + 127) / 128;
     const int bn = pick_bn(kchunks, k);
-    TcLayout L = tc_layout(bn, kchunks, k);
+    TcLayout L = tc_layout(bn, kchunks, k, kchunks <= 2);
     if (L.NS < 2) return 0;
     return L.total;
 }
 
-template <int FMT, int BN, int MODE>
+template <int FMT, int BN, int MODE, bool STG>
 static cudaError_t launch_one(const CUtensorMap& mx, const CUtensorMap& mc, const TcArgs& a, int num_sms,
                               cudaStream_t st) {
-    TcLayout L = tc_layout(BN, a.kchunks, a.k);
+    TcLayout L = tc_layout(BN, a.kchunks, a.k, STG);
     if (L.NS < 2) return cudaErrorInvalidConfiguration;
-    cudaError_t e = allow_max_smem(k_tc<FMT, BN, MODE>);
+    cudaError_t e = allow_max_smem(k_tc<FMT, BN, MODE, STG>);
     if (e != cudaSuccess) return e;
     const int64_t nrb = (a.n + TC_BM - 1) / TC_BM;
     const int grid = (int)std::min<int64_t>(nrb, (int64_t)num_sms);
-    k_tc<FMT, BN, MODE><<<grid, TC_THREADS, L.total, st>>>(mx, mc, a);
+    k_tc<FMT, BN, MODE, STG><<<grid, TC_THREADS, L.total, st>>>(mx, mc, a);
     return cudaGetLastError();
 }
 
 template <int FMT, int MODE>
 static cudaError_t launch_fmt(const CUtensorMap& mx, const CUtensorMap& mc, const TcArgs& a, int bn, int num_sms,
                               cudaStream_t st) {
-    if (bn == 256) return launch_one<FMT, 256, MODE>(mx, mc, a, num_sms, st);
-    return launch_one<FMT, 128, MODE>(mx, mc, a, num_sms, st);
+    (void)bn;  // 128-column tiles: four TMEM accumulators
+    // assign mode stages the epilogue's values when K fits two 128-byte atoms
+    if constexpr (MODE == 0) {
+        if (a.kchunks <= 2) return launch_one<FMT, 128, MODE, true>(mx, mc, a, num_sms, st);
+    }
+    return launch_one<FMT, 128, MODE, false>(mx, mc, a, num_sms, st);
 }
 
 cudaError_t launch_tc(const void* Xq, const void* Cq, int ldq, const TcArgs& a, int num_sms, cudaStream_t st) {
