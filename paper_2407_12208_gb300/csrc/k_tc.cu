@@ -3,20 +3,22 @@
 // Section 4.3 and the running argmin fused into the epilogue.  The n x k
 // distance matrix is never written to HBM in assign mode.
 //
-// Persistent CTAs (one per SM, 192 threads):
+// Persistent CTAs (one per SM, 64 + 128 x TC_NG threads):
 //   warp 0      TMA producer: a 128-row block of X~ (all of K, 128-byte
-//               swizzled atoms) per row block, and BN-row tiles of C~ through
+//               swizzled atoms) per row block, and 128-row tiles of C~ through
 //               an NS-stage ring.
-//   warp 1      allocates TMEM (2 x BN fp32 columns) and issues
-//               tcgen05.mma (M=128, N=BN) from one elected lane into one of
-//               two TMEM accumulators, so the epilogue of tile t overlaps the
-//               MMAs of tile t+1.
-//   warps 2..5  epilogue: thread = row (TMEM lane).  Per pair:
-//               e = q_j - 2 s g (one FMA), chunk minimum, and only when the
-//               chunk can hold a candidate or a flagged pair, the slow path:
-//               d^ = p + e, the exact reliability test, and a candidate
-//               append.  Candidates: every j with d^_j <= d^_min + 2 B_max,
-//               the only centres that can be the true argmin.
+//   warp 1      allocates TMEM (4 accumulators of 128 fp32 columns) and issues
+//               tcgen05.mma (M=128, N=128) from one elected lane, so the
+//               epilogues of earlier tiles overlap the MMAs of later ones.
+//   warps 2..   TC_NG epilogue groups of four warps; group g drains the tiles
+//               t with t mod TC_NG == g, and the groups share their running
+//               row minima.  Thread = row (TMEM lane).  Per pair e = q_j - 2 s g
+//               (one packed FMA per two columns); per quad of columns its
+//               minimum; only the quads that can hold a candidate or a flagged
+//               pair take the slow path: d^ = p + e, the exact reliability
+//               test, and a candidate append.  Candidates: every j with
+//               d^_j <= d^_min + 2 B_max, the only centres that can be the true
+//               argmin.
 //
 // All waits are bounded (common.cuh); a timeout sets the status word and the
 // CTA winds down.
@@ -159,7 +161,10 @@ template <int FMT, int BN, int MODE, bool STG>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, const TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned base, derived from the shared array by an offset so that
+    // every pointer below stays in the shared state space (LDS/STS, not generic)
+    const uint32_t sraw = smem_u32(smem_raw);
+    unsigned char* smem = smem_raw + (((sraw + 1023u) & ~1023u) - sraw);
     const TcLayout L = tc_layout(BN, a.kchunks, a.k, STG);
     unsigned char* sA = smem;
     unsigned char* sB = smem + (size_t)L.NA * L.a_bytes;
@@ -415,6 +420,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
                             __syncwarp();
                             if (STG) {
+                                // Possibly flagged pairs (d^ <= F) lie in the qualifying quads:
+                                // they are counted in the walk below, value by value (every
+                                // d^ <= Fall is flagged whatever its column); a lane whose
+                                // whole step lies under Fall counts the step at once.
+                                const bool fstep = __any_sync(0xffffffffu, p + cmin <= F);
+                                bool fwhole = false;
+                                if (fstep && __any_sync(0xffffffffu, p + e[0] <= Fall)) {
+                                    float cmax = e[0];
+#pragma unroll
+                                    for (int t = 1; t < NCOL; t++) cmax = fmaxf(cmax, e[t]);
+                                    fwhole = p + cmax <= Fall;  // padded columns hold +inf: never taken
+                                    nflag += fwhole ? NCOL : 0;
+                                }
                                 // the lane's values staged in shared memory (quad-major: the
                                 // 32 lanes of a quad side by side, conflict-free both ways),
                                 // then one loop over all its quads: a 16-byte read per quad
@@ -451,6 +469,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                             list[slot * TC_BM] = cand_entry(jq + c, p + et[c]);
                                             ovf |= (pc && !room);
                                             cnt += (pc && room) ? 1 : 0;
+                                        }
+                                    }
+                                    if (fstep) {
+#pragma unroll
+                                        for (int c = 0; c < 4; c++) {
+                                            const float dh = p + et[c];
+                                            if (act && !fwhole && dh <= F)
+                                                nflag += (dh <= Fall || pair_flagged(tp, a.cstat, jq + c, dh, a1, a2, a3, p, xs.z)) ? 1 : 0;
                                         }
                                     }
                                 }
@@ -499,7 +525,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 }
                             }
                             }
-                            if (__any_sync(0xffffffffu, p + cmin <= F)) {
+                            if (!STG && __any_sync(0xffffffffu, p + cmin <= F)) {
                                 // a step whose largest d^ is under every column's threshold is
                                 // flagged whole (padded columns hold +inf: never taken here)
                                 float cmax = e[0];
