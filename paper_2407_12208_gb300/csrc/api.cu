@@ -296,6 +296,8 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     a.kchunks = (ldq * esz + 127) / 128;
     a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
     a.tp = tp; a.mode = 0; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    a.cbits = 1;
+    while ((1 << a.cbits) < k) a.cbits++;  // column bits of a candidate entry (k <= 65535: at most 16)
     a.pairs = w.pairs; a.pair_cap = w.pair_cap; a.v32 = w.v32; a.rowpair = w.rowpair;
     {
         PhaseScope ps(ctx, KM_PHASE_SCREEN, st);

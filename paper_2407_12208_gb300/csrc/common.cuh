@@ -21,6 +21,18 @@ namespace km {
 
 KM_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Candidate entry: the fp32 bit pattern of d^ with its low cbits mantissa bits
+// replaced by the column index j < 2^cbits (cbits <= 16).  The stored value t
+// is d^ truncated toward zero to 24 - cbits significant bits, so the true d^
+// is at least t - |t| 2^(cbits - 23).
+KM_DEV uint32_t cand_entry(int j, float dh, uint32_t cmask) { return (__float_as_uint(dh) & ~cmask) | (uint32_t)j; }
+KM_DEV int cand_col(uint32_t e, uint32_t cmask) { return (int)(e & cmask); }
+// lscale = 2^(cbits - 23)
+KM_DEV float cand_lower(uint32_t e, uint32_t cmask, float lscale) {
+    const float t = __uint_as_float(e & ~cmask);
+    return t - fabsf(t) * lscale;
+}
+
 // ---------------------------------------------------------------- mbarrier
 KM_DEV void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));

@@ -114,7 +114,8 @@ struct TcArgs {
     const ColMax* colmax;
     TestParams tp;
     int mode;
-    uint32_t* cand;           // mode 0: TC_GROUPS x TC_LIST x n entries (group, slot, row), column j << 16 | top 16 bits of d^
+    uint32_t* cand;           // mode 0: TC_GROUPS x TC_LIST x n entries (group, slot, row): d^'s bits with the low cbits replaced by j
+    int cbits;                // bits of the column index in a candidate entry: ceil(log2 k), at least 1
     int4* rowinfo;            // n x TC_GROUPS: (count, overflow, window W bits, d^min bits) per epilogue group
     int2* pairs;              // refinement: candidate pairs (row, j), each row's pairs contiguous
     int64_t pair_cap;         // capacity of pairs / v32

@@ -27,13 +27,6 @@
 
 namespace km {
 
-// The entry holds d^ truncated toward zero to 8 significant bits: the true
-// d^ lies within |t| 2^-7 of the truncated value t.
-KM_DEV float cand_lower(uint32_t e) {
-    const float t = __uint_as_float(e << 16);
-    return t - fabsf(t) * (1.0f / 128.0f);
-}
-
 // fp32 direct values of the candidate pairs.  NV float4 of a row per lane
 // (lane l of a pair's 8 takes float4 l, l + 8, ...); NV == 0: scalar loads
 // for any d and alignment.
@@ -93,10 +86,12 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
 // row, one atomic reservation per warp.  Rows whose list overflowed, or that
 // no longer fit in the pair buffer, get count -1 (whole-row recompute).
 __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ rowinfo,
-                                                     const uint32_t* __restrict__ cand, int64_t n,
+                                                     const uint32_t* __restrict__ cand, int64_t n, int cbits,
                                                      int2* __restrict__ pairs, int64_t cap,
                                                      int2* __restrict__ rowpair, DevCounters* cnt) {
     const int lane = threadIdx.x & 31;
+    const uint32_t cmask = (1u << cbits) - 1u;
+    const float lscale = __uint_as_float((uint32_t)(127 + cbits - 23) << 23);  // 2^(cbits - 23)
     // rounds of blockDim rows per block, the same count in every warp (the
     // reservation synchronises the block)
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += (int64_t)gridDim.x * blockDim.x) {
@@ -132,8 +127,8 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
             for (int s = 0; s < SPEC; s++) eg[s] = (s < ng) ? cg[(size_t)s * n] : 0u;
             unsigned m = 0;
 #pragma unroll
-            for (int s = 0; s < SPEC; s++) m |= (s < ng && cand_lower(eg[s]) <= lim) ? (1u << s) : 0u;
-            for (int s = SPEC; s < ng; s++) m |= (cand_lower(cg[(size_t)s * n]) <= lim) ? (1u << s) : 0u;
+            for (int s = 0; s < SPEC; s++) m |= (s < ng && cand_lower(eg[s], cmask, lscale) <= lim) ? (1u << s) : 0u;
+            for (int s = SPEC; s < ng; s++) m |= (cand_lower(cg[(size_t)s * n], cmask, lscale) <= lim) ? (1u << s) : 0u;
             msk[g] = m;
             c += __popc(m);
         }
@@ -166,7 +161,7 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
                 for (int g = 0; g < TC_GROUPS; g++) {
                     const uint32_t* cg = c0 + (size_t)g * TC_LIST * n;
                     for (unsigned m = msk[g]; m; m &= m - 1)
-                        pairs[off0 + w++] = make_int2((int)row, (int)(cg[(size_t)(__ffs(m) - 1) * n] >> 16));
+                        pairs[off0 + w++] = make_int2((int)row, cand_col(cg[(size_t)(__ffs(m) - 1) * n], cmask));
                 }
             }
             rowpair[row] = make_int2(fits ? (int)off0 : 0, (full || !fits) ? -1 : c);
@@ -340,7 +335,7 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     const int64_t rows_blocks = std::max<int64_t>(1, (a.n + 255) / 256);
     const int64_t rb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(sel_per_sm, 1));
     const int64_t cb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(cert_per_sm, 1));
-    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.pairs, a.pair_cap, a.rowpair, a.cnt);
+    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.cbits, a.pairs, a.pair_cap, a.rowpair, a.cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *nlaunch = 4;

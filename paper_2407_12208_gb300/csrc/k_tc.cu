@@ -127,23 +127,17 @@ __device__ __noinline__ bool pair_flagged(const TestParams& tp, const float4* cs
 // Candidate entry: column j (16 bits) and the top 16 bits of d^'s fp32
 // encoding (d^ truncated toward zero to 8 significant bits); the true d^ lies
 // within |t| 2^-7 of the truncated value t.
-KM_DEV uint32_t cand_entry(int j, float dh) { return __byte_perm((uint32_t)j, __float_as_uint(dh), 0x1076); }
-KM_DEV float cand_dh_lower(uint32_t e) {
-    const float t = __uint_as_float(e << 16);
-    return t - fabsf(t) * (1.0f / 128.0f);
-}
-
 // Keep only the list entries still inside the window (slot-major layout):
 // all slots are read first (independent loads), then packed with predicated
 // stores.
-KM_DEV int compact_list(uint32_t* list, int cnt, float lim) {
+KM_DEV int compact_list(uint32_t* list, int cnt, float lim, uint32_t cmask, float lscale) {
     uint32_t c[TC_L];
 #pragma unroll
     for (int r = 0; r < TC_L; r++) c[r] = list[r * TC_BM];
     int w = 0;
 #pragma unroll
     for (int r = 0; r < TC_L; r++) {
-        const bool keep = r < cnt && cand_dh_lower(c[r]) <= lim;
+        const bool keep = r < cnt && cand_lower(c[r], cmask, lscale) <= lim;
         if (keep) list[w * TC_BM] = c[r];
         w += keep ? 1 : 0;
     }
@@ -298,6 +292,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t* list = lists + (size_t)g * (TC_L + 1) * TC_BM + r_in;  // slot s at list[s * TC_BM]; slot TC_L is a dummy
         const ColMax cm = *a.colmax;
         const TestParams tp = a.tp;
+        const uint32_t cmask = (1u << a.cbits) - 1u;
+        const float lscale = __uint_as_float((uint32_t)(127 + a.cbits - 23) << 23);  // 2^(cbits - 23)
         unsigned long long nflag_total = 0;
         bool ok = true;
         int iter = 0;
@@ -415,7 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (__any_sync(0xffffffffu, qmask)) {
                             if (__any_sync(0xffffffffu, cnt > TC_L - 4 * TC_CW && !ovf)) {
                                 // every lane packs its list (dropping entries that left the window)
-                                const int cc = compact_list(list, cnt, p + cthr);
+                                const int cc = compact_list(list, cnt, p + cthr, cmask, lscale);
                                 if (!ovf) cnt = cc;
                             }
                             __syncwarp();
@@ -455,7 +451,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
                                         const bool room = cnt < TC_L;
                                         const int slot = (pc && room) ? cnt : TC_L;
-                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1);
+                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1, cmask);
                                         ovf |= (pc && !room);
                                         cnt += (pc && room) ? 1 : 0;
                                     }
@@ -466,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                             const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
                                             const bool room = cnt < TC_L;
                                             const int slot = (pc && room) ? cnt : TC_L;
-                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c]);
+                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c], cmask);
                                             ovf |= (pc && !room);
                                             cnt += (pc && room) ? 1 : 0;
                                         }
@@ -506,7 +502,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
                                         const bool room = cnt < TC_L;
                                         const int slot = (pc && room) ? cnt : TC_L;
-                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1);
+                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1, cmask);
                                         ovf |= (pc && !room);
                                         cnt += (pc && room) ? 1 : 0;
                                     }
@@ -517,7 +513,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                             const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
                                             const bool room = cnt < TC_L;
                                             const int slot = (pc && room) ? cnt : TC_L;
-                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c]);
+                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c], cmask);
                                             ovf |= (pc && !room);
                                             cnt += (pc && room) ? 1 : 0;
                                         }
