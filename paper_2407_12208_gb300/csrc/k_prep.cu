@@ -141,13 +141,29 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
     const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane >> 3);
     const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * 4;
     const int d4 = d >> 2, ldq4 = ldq >> 2;
-    for (int64_t i = gid; i < m; i += ngroups) {
-        const float4* a4 = reinterpret_cast<const float4*>(A + i * d);
+    // R rows per group and round, all their loads issued first: at least four
+    // 16-byte loads in flight per lane
+    constexpr int R = NV >= 4 ? 1 : 4 / NV;
+    for (int64_t i0 = gid; i0 < m; i0 += ngroups * R) {
+        float4 xr[R][NV];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int64_t ir = i0 + (int64_t)r * ngroups;
+            const float4* a4 = reinterpret_cast<const float4*>(A + ir * d);
+#pragma unroll
+            for (int u = 0; u < NV; u++) {
+                const int c = sl + 8 * u;
+                xr[r][u] = (ir < m && c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+        const int64_t i = i0 + (int64_t)r * ngroups;
+        if (i >= m) break;  // the same row for the group's eight lanes
         float4 x[NV];
 #pragma unroll
         for (int u = 0; u < NV; u++) {
-            const int c = sl + 8 * u;
-            x[u] = (c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[u] = xr[r][u];
             amx = fmaxf(amx, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
         }
         float s = 1.0f;
@@ -221,6 +237,7 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
             if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
             stat[i] = o;
             if (rscale) rscale[i] = s;
+        }
         }
     }
     if (absmax_out) block_absmax(amx, absmax_out);

@@ -212,16 +212,20 @@ KM_DEV int bucket_of(const int* __restrict__ item_off, int k, int64_t it) {
     return lo;
 }
 
-// One warp per work item (bucket j, rows [c*CHUNK, (c+1)*CHUNK) of it); lanes
-// over the coordinates (NV4 float4 each, d % 4 == 0), exact int64 sums in
-// registers, one atomic add per coordinate per item.
-template <int NV4>
+// One warp per work item (bucket j, rows [c*CHUNK, (c+1)*CHUNK) of it); each
+// row is spread over LPR lanes (NV4 float4 each, d % 4 == 0), so a warp reads
+// 32 / LPR rows per load; exact sums in registers, folded across the row
+// groups of the warp at the end, one atomic add per coordinate per item.
+template <int NV4, int LPR>
 __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, const int* __restrict__ off,
                              const int* __restrict__ item_off, const int32_t* __restrict__ perm,
                              const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
-    constexpr int RB = 16 / NV4;  // rows in flight per lane
+    static_assert(LPR == 32 || NV4 == 1, "rows narrower than a warp take one float4 per lane");
+    constexpr int G = 32 / LPR;                            // rows per warp load
+    constexpr int RB = (16 / NV4) < (32 / G) ? 16 / NV4 : 32 / G;  // loads in flight per lane
+    constexpr int STEP = RB * G;                           // rows per round (divides 32)
     const FixedScale fx(fixed_shift(*amax_bits, n));
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane / LPR, cl = lane % LPR;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nitems = item_off[k];
@@ -236,18 +240,20 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
         for (int u = 0; u < NV4; u++)
 #pragma unroll
             for (int t = 0; t < 4; t++) a2[u][t] = a1[u][t] = a0[u][t] = 0u;
+        unsigned rounds = 0;
         for (int base = r0; base < r1; base += 32) {
             // the row indices of 32 rows in one coalesced load, then broadcast
             const int64_t my_i = (base + lane < r1) ? (int64_t)perm[base + lane] : -1;
 #pragma unroll 1
-            for (int b0 = 0; b0 < 32 && base + b0 < r1; b0 += RB) {
+            for (int b0 = 0; b0 < 32 && base + b0 < r1; b0 += STEP) {
+                rounds++;
                 float4 v[RB][NV4];
 #pragma unroll
                 for (int b = 0; b < RB; b++) {
-                    const int64_t i = __shfl_sync(0xffffffffu, my_i, b0 + b);
+                    const int64_t i = __shfl_sync(0xffffffffu, my_i, b0 + b * G + sub);
 #pragma unroll
                     for (int u = 0; u < NV4; u++) {
-                        const int cidx = lane + 32 * u;
+                        const int cidx = cl + LPR * u;
                         v[b][u] = (i >= 0 && cidx < d4) ? reinterpret_cast<const float4*>(X + i * d)[cidx]
                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
@@ -268,12 +274,23 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
                     }
             }
         }
-        // every row position of the item was split (absent rows and padding as 0.0f)
-        const unsigned m = (unsigned)(((r1 - r0 + RB - 1) / RB) * RB);
+        // the row groups' sums of the same coordinates (modulo 2^32 like the sums)
+#pragma unroll
+        for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+            for (int u = 0; u < NV4; u++)
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    a2[u][t] += __shfl_xor_sync(0xffffffffu, a2[u][t], o);
+                    a1[u][t] += __shfl_xor_sync(0xffffffffu, a1[u][t], o);
+                    a0[u][t] += __shfl_xor_sync(0xffffffffu, a0[u][t], o);
+                }
+        // every row slot of every round was split (absent rows and padding as 0.0f)
+        const unsigned m = rounds * (unsigned)STEP;
 #pragma unroll
         for (int u = 0; u < NV4; u++) {
-            const int cidx = lane + 32 * u;
-            if (cidx < d4)
+            const int cidx = cl + LPR * u;
+            if (sub == 0 && cidx < d4)
 #pragma unroll
                 for (int t = 0; t < 4; t++) {
                     const long long acc = FixedScale::combine(a2[u][t], a1[u][t], a0[u][t], m);
@@ -568,8 +585,11 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         const int64_t items = n / SEG_CHUNK + k + 1;
         int per_sm = 1;
         if (d > 5) {
-            const void* fn = d <= 128 ? (const void*)k_bucket_sum<1> : d <= 256 ? (const void*)k_bucket_sum<2>
-                                                                                 : (const void*)k_bucket_sum<4>;
+            const void* fn = d <= 32    ? (const void*)k_bucket_sum<1, 8>
+                             : d <= 64  ? (const void*)k_bucket_sum<1, 16>
+                             : d <= 128 ? (const void*)k_bucket_sum<1, 32>
+                             : d <= 256 ? (const void*)k_bucket_sum<2, 32>
+                                        : (const void*)k_bucket_sum<4, 32>;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
             if (e != cudaSuccess) return e;
         } else {
@@ -581,9 +601,11 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
         else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
         else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 128) k_bucket_sum<1><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 256) k_bucket_sum<2><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
-        else k_bucket_sum<4><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 32) k_bucket_sum<1, 8><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 64) k_bucket_sum<1, 16><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 128) k_bucket_sum<1, 32><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 256) k_bucket_sum<2, 32><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        else k_bucket_sum<4, 32><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
         return cudaGetLastError();
     }
     e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);

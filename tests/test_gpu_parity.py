@@ -186,7 +186,8 @@ def test_update_centroids(ctx, policy):
     assert shift == pytest.approx(oshift, rel=1e-6)
 
 
-@pytest.mark.parametrize("n,d,k", [(20011, 5, 16), (3001, 7, 9), (10000, 64, 256), (5000, 2, 1)])
+@pytest.mark.parametrize("n,d,k", [(20011, 5, 16), (3001, 7, 9), (10000, 64, 256), (5000, 2, 1),
+                                   (4099, 32, 50), (3000, 48, 7), (2500, 12, 300)])
 def test_update_shapes(ctx, n, d, k):
     import paper_2407_12208_gb300 as pkg
     X, C = workloads.gaussian_mixture(n, d, k, seed=n + d)
