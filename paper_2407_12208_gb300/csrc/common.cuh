@@ -21,6 +21,18 @@ namespace km {
 
 KM_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Shared-memory accesses through 32-bit shared addresses (the screen's
+// per-lane staging and candidate lists: plain 32-bit address arithmetic).
+KM_DEV void st_shared_v4(uint32_t a, float x, float y, float z, float w) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+KM_DEV float4 ld_shared_v4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+    return v;
+}
+KM_DEV void st_shared_u32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory"); }
+
 // Candidate entry: the fp32 bit pattern of d^ with its low cbits mantissa bits
 // replaced by the column index j < 2^cbits (cbits <= 16).  The stored value t
 // is d^ truncated toward zero to 24 - cbits significant bits, so the true d^

@@ -1,9 +1,10 @@
 // k_direct.cu -- direct-formula assignment kernels, Eq. (dist-direct).
 //
 //  * k_direct_assign<double>: the plain FP64 path (every pair in binary64).
-//  * k_direct_assign<float>:  fp32 direct distances for small d (image pixels)
-//    and for rows whose tensor-core candidate list overflowed.  Theorem 4.1
-//    bounds each value's relative error by gamma_{d+2}(2^-24); a row whose
+//  * k_direct_tiled (d % 4 == 0, 16 <= d <= 128), k_direct_small (d <= 8)
+//    and k_direct_assign<float> (other d): fp32 direct distances for the fp32
+//    path and for rows whose tensor-core candidate list overflowed.  Theorem
+//    4.1 bounds each value's relative error by gamma_{d+2}(2^-24); a row whose
 //    best and second-best intervals overlap is not certified and goes to
 //  * k_rows_fp64: binary64 direct distances of one row against all centres
 //    (warp per row, lanes over centres), exact argmin with the lowest index
@@ -132,6 +133,164 @@ __global__ void __launch_bounds__(DA_ROWS) k_direct_assign(const float* __restri
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
         if ((threadIdx.x & 31) == 0) atomicMax(absmax_out, __float_as_uint(amx));
+    }
+}
+
+// Tiled fp32 direct distances, Eq. (dist-direct), for d % 4 == 0 and
+// 16 <= d <= 128 (rows whose candidate list overflowed, the fp32 direct path,
+// km_assign_static): 128 rows per round resident in shared memory, the
+// centres streamed through it in tiles of 64 (cp.async, two buffers).  Each
+// thread holds 4 rows x 8 centres and takes two coordinates per packed
+// instruction: the even and the odd coordinates are summed separately and
+// then added, a summation order Theorem 4.1's bound covers like any other.
+// Per row the smallest and second-smallest value and the first index of the
+// smallest (ties: lowest index), merged over the 8 threads of the row; the
+// certificate and the list of open rows as in k_direct_assign.
+constexpr int DT_R = 128;  // rows per round
+constexpr int DT_C = 64;   // centres per tile
+
+KM_DEV void cp_async16(uint32_t dst, const void* src, bool full) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(full ? 16 : 0) : "memory");
+}
+KM_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+KM_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(256, 1) k_direct_tiled(const float* __restrict__ X, int64_t n,
+                                                         const float* __restrict__ C, int k, int d,
+                                                         const int32_t* __restrict__ row_list,
+                                                         const int* __restrict__ row_count,
+                                                         int32_t* __restrict__ labels, double* __restrict__ min_dist,
+                                                         int32_t* __restrict__ amb_list, DevCounters* cnt,
+                                                         float gamma32, unsigned* __restrict__ absmax_out) {
+    extern __shared__ __align__(16) float dts[];
+    const int ldx = d + 4;  // row stride: 16-byte rows, consecutive rows 4 banks apart
+    float* Xs = dts;
+    const uint32_t cs0 = smem_u32(dts + DT_R * ldx);  // [2][DT_C][ldx]
+    const float* Cs = dts + DT_R * ldx;
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int64_t nrows = row_list ? (int64_t)(*row_count) : n;
+    const int d4 = d >> 2;
+    const int ntile = (k + DT_C - 1) / DT_C;
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    const float g = gamma32;
+    float amx = 0.0f;
+    unsigned long long local_amb = 0;
+    for (int64_t base = (int64_t)blockIdx.x * DT_R; base < nrows; base += (int64_t)gridDim.x * DT_R) {
+        const int rows_here = (int)min((int64_t)DT_R, nrows - base);
+        __syncthreads();  // the previous round's readers are done with both buffers
+        for (int e = tid; e < DT_R * d4; e += blockDim.x) {
+            const int r = e / d4, l4 = e - r * d4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < rows_here) {
+                const int64_t gi = row_list ? (int64_t)row_list[base + r] : base + r;
+                v = reinterpret_cast<const float4*>(X + gi * d)[l4];
+                amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            }
+            *reinterpret_cast<float4*>(Xs + r * ldx + 4 * l4) = v;
+        }
+        auto load_tile = [&](int t, int buf) {
+            const int c0 = t * DT_C;
+            for (int e = tid; e < DT_C * d4; e += blockDim.x) {
+                const int c = e / d4, l4 = e - c * d4;
+                const bool ok = c0 + c < k;
+                cp_async16(cs0 + (uint32_t)(((buf * DT_C + c) * ldx + 4 * l4) * 4),
+                           ok ? (const void*)(C + (int64_t)(c0 + c) * d + 4 * l4) : (const void*)C, ok);
+            }
+            cp_async_commit();
+        };
+        load_tile(0, 0);
+        float b1[4], b2[4];
+        int j1[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) { b1[i] = INFINITY; b2[i] = INFINITY; j1[i] = 0; }
+        for (int t = 0; t < ntile; t++) {
+            const int buf = t & 1;
+            cp_async_wait_all();
+            __syncthreads();  // tile t is in place; tile t - 1's buffer is free
+            if (t + 1 < ntile) load_tile(t + 1, buf ^ 1);
+            float2 acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int c = 0; c < 8; c++) acc[i][c] = make_float2(0.f, 0.f);
+            const float* xb = Xs + ty * ldx;                     // rows ty + 32 i
+            const float* cb = Cs + (size_t)(buf * DT_C + tx) * ldx;  // centres tx + 8 c
+            for (int l = 0; l < d; l += 4) {
+                float4 xv[4], cv[8];
+#pragma unroll
+                for (int i = 0; i < 4; i++) xv[i] = *reinterpret_cast<const float4*>(xb + 32 * i * ldx + l);
+#pragma unroll
+                for (int c = 0; c < 8; c++) cv[c] = *reinterpret_cast<const float4*>(cb + 8 * c * ldx + l);
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                        const float2 t0 = __ffma2_rn(make_float2(cv[c].x, cv[c].y), neg1, make_float2(xv[i].x, xv[i].y));
+                        acc[i][c] = __ffma2_rn(t0, t0, acc[i][c]);
+                        const float2 t1 = __ffma2_rn(make_float2(cv[c].z, cv[c].w), neg1, make_float2(xv[i].z, xv[i].w));
+                        acc[i][c] = __ffma2_rn(t1, t1, acc[i][c]);
+                    }
+            }
+            const int c0 = t * DT_C;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const int j = c0 + tx + 8 * c;  // ascending in c: the first of equal values keeps its place
+                if (j < k)
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const float v = acc[i][c].x + acc[i][c].y;
+                        if (v < b1[i]) {
+                            b2[i] = b1[i];
+                            b1[i] = v;
+                            j1[i] = j;
+                        } else if (v < b2[i]) {
+                            b2[i] = v;
+                        }
+                    }
+            }
+        }
+        // the 8 threads of each row: smallest (lowest index on ties) and second smallest
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+                const float ob1 = __shfl_xor_sync(0xffffffffu, b1[i], off);
+                const float ob2 = __shfl_xor_sync(0xffffffffu, b2[i], off);
+                const int oj = __shfl_xor_sync(0xffffffffu, j1[i], off);
+                if (ob1 < b1[i] || (ob1 == b1[i] && oj < j1[i])) {
+                    b2[i] = fminf(b1[i], ob2);
+                    b1[i] = ob1;
+                    j1[i] = oj;
+                } else {
+                    b2[i] = fminf(b2[i], ob1);
+                }
+            }
+        if (tx == 0)
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int r = ty + 32 * i;
+                if (r < rows_here) {
+                    const int64_t gi = row_list ? (int64_t)row_list[base + r] : base + r;
+                    labels[gi] = j1[i];
+                    min_dist[gi] = (double)b1[i];
+                    // Theorem 4.1: true values lie in [v (1 - g), v (1 + g)]
+                    if (!(b2[i] * (1.0f - g) > b1[i] * (1.0f + g))) {
+                        const int slot = atomicAdd(&cnt->amb_count, 1);
+                        amb_list[slot] = (int32_t)gi;
+                        local_amb++;
+                    }
+                }
+            }
+        if (tid == 0) atomicAdd(&cnt->fp32_evals, (unsigned long long)rows_here * (unsigned long long)k);
+    }
+    cp_async_wait_all();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local_amb += __shfl_xor_sync(0xffffffffu, local_amb, off);
+    if ((tid & 31) == 0 && local_amb) atomicAdd(&cnt->amb_rows, local_amb);
+    if (absmax_out) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
+        if ((tid & 31) == 0) atomicMax(absmax_out, __float_as_uint(amx));
     }
 }
 
@@ -375,6 +534,15 @@ cudaError_t launch_direct_assign(bool acc64, const float* X, int64_t n, const fl
             KM_SMALL(1) KM_SMALL(2) KM_SMALL(3) KM_SMALL(4) KM_SMALL(5) KM_SMALL(6) KM_SMALL(7) KM_SMALL(8)
 #undef KM_SMALL
         }
+        return cudaGetLastError();
+    }
+    if (!acc64 && d % 4 == 0 && d >= 16 && d <= 128 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)C % 16) == 0) {
+        const size_t tsm = (size_t)(DT_R + 2 * DT_C) * (d + 4) * sizeof(float);
+        cudaError_t e = allow_max_smem(k_direct_tiled);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((n + DT_R - 1) / DT_R, (int64_t)num_sms));
+        k_direct_tiled<<<(unsigned)grid, 256, tsm, st>>>(X, n, C, k, d, row_list, row_count, labels, min_dist, amb_list,
+                                                          cnt, gamma32, absmax_out);
         return cudaGetLastError();
     }
     size_t sm = direct_smem(acc64, d);

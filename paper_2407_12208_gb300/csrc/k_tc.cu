@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int r_in = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         uint32_t* list = lists + (size_t)g * (TC_L + 1) * TC_BM + r_in;  // slot s at list[s * TC_BM]; slot TC_L is a dummy
+        const uint32_t lbase = smem_u32(list);                            // the same as a shared address
         const ColMax cm = *a.colmax;
         const TestParams tp = a.tp;
         const uint32_t cmask = (1u << a.cbits) - 1u;
@@ -432,16 +433,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 // the lane's values staged in shared memory (quad-major: the
                                 // 32 lanes of a quad side by side, conflict-free both ways),
                                 // then one loop over all its quads: a 16-byte read per quad
-                                float4* stg = reinterpret_cast<float4*>(smem + L.stage_off) + (size_t)(warp - 2) * NQ * 32 + lane;
+                                const uint32_t stg = smem_u32(smem) + (uint32_t)L.stage_off + (uint32_t)(((warp - 2) * NQ * 32 + lane) * 16);
 #pragma unroll
                                 for (int qd = 0; qd < NQ; qd++)
-                                    stg[qd * 32] = make_float4(e[4 * qd], e[4 * qd + 1], e[4 * qd + 2], e[4 * qd + 3]);
+                                    st_shared_v4(stg + qd * 512, e[4 * qd], e[4 * qd + 1], e[4 * qd + 2], e[4 * qd + 3]);
                                 unsigned ph = qmask;
                                 while (__any_sync(0xffffffffu, ph)) {
                                     const bool act = ph != 0;
                                     const int qd = act ? __ffs(ph) - 1 : 0;
                                     ph &= ph - 1;
-                                    const float4 ev = stg[qd * 32];
+                                    const float4 ev = ld_shared_v4(stg + qd * 512);
                                     const float et[4] = {ev.x, ev.y, ev.z, ev.w};
                                     const int jq = col0 + 4 * qd;
                                     const bool q0 = et[0] <= cthr, q1 = et[1] <= cthr, q2 = et[2] <= cthr, q3 = et[3] <= cthr;
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
                                         const bool room = cnt < TC_L;
                                         const int slot = (pc && room) ? cnt : TC_L;
-                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1, cmask);
+                                        st_shared_u32(lbase + slot * (TC_BM * 4), cand_entry(jq + c1, p + e1, cmask));
                                         ovf |= (pc && !room);
                                         cnt += (pc && room) ? 1 : 0;
                                     }
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                             const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
                                             const bool room = cnt < TC_L;
                                             const int slot = (pc && room) ? cnt : TC_L;
-                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c], cmask);
+                                            st_shared_u32(lbase + slot * (TC_BM * 4), cand_entry(jq + c, p + et[c], cmask));
                                             ovf |= (pc && !room);
                                             cnt += (pc && room) ? 1 : 0;
                                         }

@@ -44,7 +44,8 @@ def test_fp64_direct_blobs(ctx):
     assert nf == 0
 
 
-@pytest.mark.parametrize("n,d,k", [(5000, 5, 16), (1000, 16, 8), (777, 33, 40), (300, 2, 300)])
+@pytest.mark.parametrize("n,d,k", [(5000, 5, 16), (1000, 16, 8), (777, 33, 40), (300, 2, 300),
+                                   (3001, 128, 300), (2000, 64, 1000), (129, 96, 65)])
 def test_fp32_direct_certified(ctx, n, d, k):
     if d == 5:
         X, C = workloads.voronoi_image(50, 100, 16, k, seed=2)
