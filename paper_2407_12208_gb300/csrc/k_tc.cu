@@ -112,21 +112,22 @@ KM_DEV void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
 }
 
-// Reliability test of one pair (rare path): tc form rho * B(x, c) or Alg. 2's
-// rho c_A gamma^l_{d+2} (||x~||^2 + ||c~||^2).
-__device__ __noinline__ bool pair_flagged(const TestParams& tp, const float4* cstat, int j, float dh, float a1,
-                                          float a2, float a3, float p, float nxq) {
+// Reliability test of one pair (rare path, kept out of line so the hot loop
+// stays small; scalar arguments, so nothing goes through the stack): tc form
+// rho * B(x, c) or Alg. 2's rho c_A gamma^l_{d+2} (||x~||^2 + ||c~||^2).
+__device__ __noinline__ bool pair_flagged(int test, float rho, float kn, float bsafe, float paper_coef,
+                                          const float4* cstat, int j, float dh, float a1, float a2, float a3, float p,
+                                          float nxq) {
     const float4 cs = cstat[j];
-    if (tp.test == 0) {
-        const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + tp.kn * (p + cs.x)) * tp.bsafe;
-        return dh <= tp.rho * B;
+    if (test == 0) {
+        const float B = (a1 * cs.y + a2 * cs.w + a3 * cs.z + kn * (p + cs.x)) * bsafe;
+        return dh <= rho * B;
     }
-    return dh <= tp.paper_coef * (nxq * nxq + cs.z * cs.z);
+    return dh <= paper_coef * (nxq * nxq + cs.z * cs.z);
 }
+#define KM_PAIR_FLAGGED(j, dh) \
+    pair_flagged(tp.test, tp.rho, tp.kn, tp.bsafe, tp.paper_coef, a.cstat, (j), (dh), a1, a2, a3, p, xs.z)
 
-// Candidate entry: column j (16 bits) and the top 16 bits of d^'s fp32
-// encoding (d^ truncated toward zero to 8 significant bits); the true d^ lies
-// within |t| 2^-7 of the truncated value t.
 // Keep only the list entries still inside the window (slot-major layout):
 // all slots are read first (independent loads), then packed with predicated
 // stores.
@@ -430,6 +431,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     fwhole = p + cmax <= Fall;  // padded columns hold +inf: never taken
                                     nflag += fwhole ? NCOL : 0;
                                 }
+                                // A row whose list overflowed takes no more candidates: it walks
+                                // its quads only while flagged pairs remain to be counted one by one.
+                                unsigned ph = (ovf && !(fstep && !fwhole)) ? 0u : qmask;
                                 // the lane's values staged in shared memory (quad-major: the
                                 // 32 lanes of a quad side by side, conflict-free both ways),
                                 // then one loop over all its quads: a 16-byte read per quad
@@ -437,7 +441,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                                 for (int qd = 0; qd < NQ; qd++)
                                     st_shared_v4(stg + qd * 512, e[4 * qd], e[4 * qd + 1], e[4 * qd + 2], e[4 * qd + 3]);
-                                unsigned ph = qmask;
                                 while (__any_sync(0xffffffffu, ph)) {
                                     const bool act = ph != 0;
                                     const int qd = act ? __ffs(ph) - 1 : 0;
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         for (int c = 0; c < 4; c++) {
                                             const float dh = p + et[c];
                                             if (act && !fwhole && dh <= F)
-                                                nflag += (dh <= Fall || pair_flagged(tp, a.cstat, jq + c, dh, a1, a2, a3, p, xs.z)) ? 1 : 0;
+                                                nflag += (dh <= Fall || KM_PAIR_FLAGGED(jq + c, dh)) ? 1 : 0;
                                         }
                                     }
                                 }
@@ -534,7 +537,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                                     for (int t = 0; t < NCOL; t++) {
                                         const float dh = p + e[t];
-                                        if (dh <= F) nflag += pair_flagged(tp, a.cstat, col0 + t, dh, a1, a2, a3, p, xs.z) ? 1 : 0;
+                                        if (dh <= F) nflag += KM_PAIR_FLAGGED(col0 + t, dh) ? 1 : 0;
                                     }
                                 }
                             }
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int j = col0 + t;
                             if (j < a.k) {
                                 const float dh = fmaxf(p + e[t], 0.0f);
-                                const bool fl = (dh <= F) && pair_flagged(tp, a.cstat, j, dh, a1, a2, a3, p, xs.z);
+                                const bool fl = (dh <= F) && KM_PAIR_FLAGGED(j, dh);
                                 drow[j] = dh;
                                 if (fl) {
                                     nflag++;
