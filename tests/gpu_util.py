@@ -11,7 +11,8 @@ def check_assign(lab, md, X, C, oracle, rtol):
     exceeds MARGIN; elsewhere the GPU label must still be a minimiser within
     tolerance.  min_dist within rtol of the oracle's best distance."""
     olab, od1, od2 = oracle.assign(X, C)
-    margin = np.where(np.isfinite(od2), (od2 - od1) / np.maximum(od2, 1e-300), np.inf)
+    with np.errstate(invalid="ignore", divide="ignore"):  # k = 1: od2 is inf (the other branch)
+        margin = np.where(np.isfinite(od2), (od2 - od1) / np.maximum(od2, 1e-300), np.inf)
     sel = margin > MARGIN
     bad = np.nonzero(sel & (lab != olab))[0]
     assert bad.size == 0, "label mismatch at rows %s (gpu %s oracle %s)" % (bad[:5], lab[bad[:5]], olab[bad[:5]])

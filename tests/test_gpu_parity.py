@@ -278,6 +278,36 @@ def test_full_size_bf16_sampled():
     assert st["pairs"] == 1_000_000 * 1024
 
 
+@pytest.mark.parametrize("wl,n,d,k,low", [
+    ("cancellation", 1_000_000, 128, 1024, "bf16"),      # every pair flagged, every list overflows
+    ("gaussian_mixture", 4_000_000, 64, 256, "bf16"),     # the mixed Lloyd iteration shape
+    ("voronoi", 4096 * 4096, 5, 16, "fp32"),              # the image shape, fp32 direct
+])
+def test_full_size_lloyd_step_sampled(wl, n, d, k, low):
+    """One km_lloyd_step at the full benchmark sizes (the bench's launch
+    configuration): labels and min_dist on 2000 sampled rows against the
+    oracle; the new centres against the oracle's update from the GPU's own
+    labels (exact fixed-point sums: within one ulp of binary64 summation)."""
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    if wl == "voronoi":
+        X, C = workloads.voronoi_image(4096, 4096, 16, k, seed=7)
+    else:
+        X, C = getattr(workloads, wl)(n, d, k, seed=15)
+    assert X.shape == (n, d)
+    p = pkg.params(low)
+    lab, md, Cn, cnt, _ = c.lloyd_step(_dev(X), _dev(C), p)
+    torch.cuda.synchronize()
+    lab, md, Cn, cnt = lab.cpu().numpy(), md.cpu().numpy(), Cn.cpu().numpy(), cnt.cpu().numpy()
+    assert lab.min() >= 0 and lab.max() < k
+    rows = np.random.default_rng(1).choice(n, 2000, replace=False)
+    check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MIXED)
+    oC, ocnt, _ = oracle.update(X, lab, C, 1, md)
+    assert np.array_equal(cnt, ocnt)
+    np.testing.assert_allclose(Cn, oC, rtol=2 ** -22, atol=1e-30)
+    assert c.stats()["pairs"] == n * k
+
+
 # ------------------------------------------------ one fused Lloyd iteration
 @pytest.mark.parametrize("low,empty,shape", [("bf16", "farthest", (20000, 128, 300)), ("fp16", "keep", (7001, 64, 96)),
                                              ("e4m3", "farthest", (5000, 64, 40)), ("fp32", "farthest", (3000, 16, 24)),
