@@ -267,14 +267,16 @@ def run_ours(args):
     Ch = torch.from_numpy(C).pin_memory()
     lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
     md_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    Cn_h = torch.empty((k, d), dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty(k, dtype=torch.int64).pin_memory()
     e2e_steps = 0 if args.only_step else max(3, min(args.steps, 20))
+    hws = ctx.host_workspace(n, d, k, p) if e2e_steps else None
 
     def e2e_step():
-        Xd.copy_(Xh, non_blocking=True)
-        Cd.copy_(Ch, non_blocking=True)
-        step()
-        lab_h.copy_(labels, non_blocking=True)
-        md_h.copy_(md, non_blocking=True)
+        # the public host-buffer call: X and C from pinned host memory, labels,
+        # min_dist, the new centres and counts back to it (km_lloyd_step_host)
+        ctx.lloyd_step_host(Xh, Ch, p, labels=lab_h, min_dist=md_h, C_new=Cn_h, counts=cnt_h, ws=hws, stream=stream,
+                            want_shift=False)
 
     if e2e_steps:
         e2e_step()
@@ -291,7 +293,8 @@ def run_ours(args):
     if e2e_steps:
         e2e = {"value": whole_job_rate(pairs_per_step, world, e2e_ms / 1e3), "unit": "pairs/s",
                "h2d_bytes_per_step": int(Xh.numel() * 4 + Ch.numel() * 4),
-               "d2h_bytes_per_step": int(lab_h.numel() * 4 + md_h.numel() * 8), "ms_per_step": e2e_ms}
+               "d2h_bytes_per_step": int(lab_h.numel() * 4 + md_h.numel() * 8 + Cn_h.numel() * 4 + cnt_h.numel() * 8),
+               "ms_per_step": e2e_ms, "call": "km_lloyd_step_host"}
 
     stats = ctx.stats()
     # ------------------------------------------------- FP64 path, same GPU

@@ -158,6 +158,28 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
                         int64_t* counts, double* shift_host, void* ws, size_t ws_bytes,
                         void* stream);
 
+/* km_lloyd_step on HOST buffers (no paper counterpart: the transfer around
+ * one iteration of Alg. 3's loop body, for callers whose data lives in host
+ * memory).  X_host (n x d fp32), C_host (k x d) are read, and labels_host
+ * (n int32), min_dist_host (nullable, n doubles), C_new_host (k x d),
+ * counts_host (nullable, k int64) and shift_host (nullable) written, all in
+ * host memory; the call returns when they are there (it synchronises
+ * `stream`).  The rows travel in up to four chunks of whole 128-row blocks on
+ * two copy streams owned by the context: each chunk is assigned as soon as
+ * it has arrived and its labels go back while the next chunk is assigned;
+ * the centre update follows the last chunk.  With pinned (page-locked) host
+ * buffers the copies overlap the kernels; pageable ones still give the same
+ * results.  The results equal km_lloyd_step on device copies of the same
+ * inputs bit for bit.  ws: device memory of km_host_workspace_size bytes
+ * (256-byte aligned), holding the device copies and the step's workspace.
+ * Errors as km_lloyd_step. */
+km_status km_host_workspace_size(const km_ctx* ctx, int64_t n, int d, int k, const km_params* p,
+                                 size_t* bytes);
+km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d, int k,
+                             const float* C_host, const km_params* p, int32_t* labels_host,
+                             double* min_dist_host, float* C_new_host, int64_t* counts_host,
+                             double* shift_host, void* ws, size_t ws_bytes, void* stream);
+
 /* Alg. 3: Lloyd's loop with the mixed-precision assignment.  C_out (k x d)
  * receives the final centres, labels (n) the final reassignment.
  * sse_per_iter and eta_per_iter (nullable, host, max_iter + 1 doubles):

@@ -27,7 +27,8 @@ TEST_NAMES = {"tc": TEST_TC, "paper": TEST_PAPER, "off": TEST_OFF}
 EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_workspace_size",
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
-           "km_get_launch_count", "km_assign_static", "km_lloyd_step"]
+           "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
+           "km_lloyd_step_host"]
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -99,6 +100,9 @@ def load(path: str = LIB_PATH):
         lib.km_cancel.argtypes = [vp, c.c_uint64]
         lib.km_assign_static.argtypes = [vp, vp, i64, vp, i32, i32, vp, vp, vp]
         lib.km_lloyd_step.argtypes = [vp, vp, i64, i32, i32, vp, P, vp, vp, vp, vp, c.POINTER(c.c_double), vp, sz, vp]
+        lib.km_host_workspace_size.argtypes = [vp, i64, i32, i32, P, c.POINTER(sz)]
+        lib.km_lloyd_step_host.argtypes = [vp, vp, i64, i32, i32, vp, P, vp, vp, vp, vp, c.POINTER(c.c_double), vp,
+                                           sz, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -151,6 +155,7 @@ class Context:
             raise KmError(rc, "km_init failed")
         self.h = h
         self._ws = None
+        self._hws = None
 
     def close(self):
         if getattr(self, "h", None):
@@ -239,6 +244,37 @@ class Context:
                                            _ptr(min_dist), _ptr(C_new), _ptr(counts),
                                            ctypes.byref(sh) if want_shift else None, _ptr(ws), ws.numel(),
                                            _stream(stream)))
+        return labels, min_dist, C_new, counts, (sh.value if want_shift else None)
+
+    def host_workspace(self, n, d, k, p: Params):
+        """A cached device workspace for km_lloyd_step_host."""
+        import torch
+        b = ctypes.c_size_t()
+        self._check(self.lib.km_host_workspace_size(self.h, int(n), int(d), int(k), ctypes.byref(p), ctypes.byref(b)))
+        if self._hws is None or self._hws.numel() < b.value:
+            self._hws = torch.empty(b.value, dtype=torch.uint8, device="cuda:%d" % self.device)
+        return self._hws
+
+    def lloyd_step_host(self, X, C_old, p: Params, labels=None, min_dist=None, C_new=None, counts=None, ws=None,
+                        stream=None, want_shift=True):
+        """km_lloyd_step_host: X, C_old and the outputs are CPU tensors (pin
+        them for overlapped copies); returns when the outputs are written."""
+        import torch
+        assert X.device.type == "cpu" and C_old.device.type == "cpu"
+        X = X.contiguous()
+        C_old = C_old.contiguous()
+        n, d = X.shape
+        k = C_old.shape[0]
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32).pin_memory()
+        if C_new is None:
+            C_new = torch.empty((k, d), dtype=torch.float32).pin_memory()
+        ws = ws if ws is not None else self.host_workspace(n, d, k, p)
+        sh = ctypes.c_double(0.0)
+        self._check(self.lib.km_lloyd_step_host(self.h, _ptr(X), n, d, k, _ptr(C_old), ctypes.byref(p), _ptr(labels),
+                                                _ptr(min_dist), _ptr(C_new), _ptr(counts),
+                                                ctypes.byref(sh) if want_shift else None, _ptr(ws), ws.numel(),
+                                                _stream(stream)))
         return labels, min_dist, C_new, counts, (sh.value if want_shift else None)
 
     def update_centroids(self, X, labels, C_old, p: Params, min_dist=None, C_new=None, counts=None, ws=None,

@@ -36,9 +36,16 @@ struct km_ctx {
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[KM_NUM_PHASES];
     uint64_t launches = 0;
+    // km_lloyd_step_host: two copy streams and the events that order them
+    // against the caller's stream (created on first use)
+    cudaStream_t copy_st[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> host_ev;
     ~km_ctx() {
         for (auto& v : ev)
             for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        for (cudaEvent_t e : host_ev) cudaEventDestroy(e);
+        for (cudaStream_t c : copy_st)
+            if (c) cudaStreamDestroy(c);
     }
 };
 
@@ -191,6 +198,26 @@ UpdateWs carve_update(Carve& cv, int64_t n, int d, int k) {
     u.iscratch = cv.take<int>((size_t)4 * k + 2);
     u.perm = cv.take<int32_t>((size_t)n);
     return u;
+}
+
+// Device copies of the inputs and outputs of km_lloyd_step_host.
+struct HostWs {
+    float* X;
+    float* C;
+    int32_t* labels;
+    double* min_dist;
+    float* C_new;
+    int64_t* counts;
+};
+HostWs carve_host(Carve& cv, int64_t n, int d, int k) {
+    HostWs h{};
+    h.X = cv.take<float>((size_t)n * d);
+    h.C = cv.take<float>((size_t)k * d);
+    h.labels = cv.take<int32_t>((size_t)n);
+    h.min_dist = cv.take<double>((size_t)n);
+    h.C_new = cv.take<float>((size_t)k * d);
+    h.counts = cv.take<int64_t>((size_t)k);
+    return h;
 }
 
 struct LloydWs {
@@ -566,6 +593,96 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
         if ((s = sync_status(ctx, w.cnt, st)) != KM_OK) return s;
         CK(cudaMemcpy(shift_host, u.shift, sizeof(double), cudaMemcpyDeviceToHost));
     }
+    return KM_OK;
+}
+
+km_status km_host_workspace_size(const km_ctx* cctx, int64_t n, int d, int k, const km_params* p, size_t* bytes) {
+    km_ctx* ctx = const_cast<km_ctx*>(cctx);
+    if (!ctx || !bytes || !p) return KM_EINVAL;
+    if (n < 1 || d < 1 || k < 1) return fail(ctx, KM_EINVAL, "need n, d, k >= 1");
+    Carve a{nullptr};
+    carve_host(a, n, d, k);
+    carve_assign(a, n, d, k, p->low, false);
+    carve_update(a, n, d, k);
+    *bytes = a.off + 256;
+    return KM_OK;
+}
+
+km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d, int k, const float* C_host,
+                             const km_params* p, int32_t* labels_host, double* min_dist_host, float* C_new_host,
+                             int64_t* counts_host, double* shift_host, void* ws, size_t ws_bytes, void* stream) {
+    km_status s = check_common(ctx, X_host, n, C_host, k, d);
+    if (s != KM_OK) return s;
+    if (!p || !labels_host || !C_new_host || !ws) return fail(ctx, KM_EINVAL, "null params, output or workspace");
+    s = check_params(ctx, p, d, k);
+    if (s != KM_OK) return s;
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    HostWs h = carve_host(cv, n, d, k);
+    AssignWs w = carve_assign(cv, n, d, k, p->low, false);
+    UpdateWs u = carve_update(cv, n, d, k);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    // rows in up to kHostChunks chunks of whole 128-row blocks; each chunk is
+    // assigned as soon as it has arrived, while the next one is being copied
+    constexpr int kHostChunks = 4;
+    const int64_t R = ((n + kHostChunks - 1) / kHostChunks + 127) / 128 * 128;
+    const int nch = (int)((n + R - 1) / R);
+    for (int i = 0; i < 2; i++)
+        if (!ctx->copy_st[i]) CK(cudaStreamCreateWithFlags(&ctx->copy_st[i], cudaStreamNonBlocking));
+    while ((int)ctx->host_ev.size() < 3 * kHostChunks + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->host_ev.push_back(e);
+    }
+    cudaEvent_t ev_start = ctx->host_ev[0];
+    cudaEvent_t* ev_in = ctx->host_ev.data() + 1;
+    cudaEvent_t* ev_out = ev_in + kHostChunks;
+    cudaEvent_t* ev_back = ev_out + kHostChunks;
+    // the copies into the workspace wait for earlier work on the stream
+    CK(cudaEventRecord(ev_start, st));
+    CK(cudaMemcpyAsync(h.C, C_host, sizeof(float) * (size_t)k * d, cudaMemcpyHostToDevice, st));
+    for (int c = 0; c < nch; c++) {
+        const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
+        cudaStream_t cs = ctx->copy_st[c & 1];
+        CK(cudaStreamWaitEvent(cs, ev_start, 0));
+        CK(cudaMemcpyAsync(h.X + r0 * d, X_host + r0 * d, sizeof(float) * (size_t)rows * d, cudaMemcpyHostToDevice, cs));
+        CK(cudaEventRecord(ev_in[c], cs));
+    }
+    CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
+    CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
+    for (int c = 0; c < nch; c++) {
+        const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
+        cudaStream_t cs = ctx->copy_st[c & 1];
+        CK(cudaStreamWaitEvent(st, ev_in[c], 0));
+        CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
+        s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
+        if (s != KM_OK) return s;
+        // this chunk's labels and distances go back while the next chunk is assigned
+        CK(cudaEventRecord(ev_out[c], st));
+        CK(cudaStreamWaitEvent(cs, ev_out[c], 0));
+        CK(cudaMemcpyAsync(labels_host + r0, h.labels + r0, sizeof(int32_t) * (size_t)rows, cudaMemcpyDeviceToHost, cs));
+        if (min_dist_host)
+            CK(cudaMemcpyAsync(min_dist_host + r0, h.min_dist + r0, sizeof(double) * (size_t)rows, cudaMemcpyDeviceToHost, cs));
+        CK(cudaEventRecord(ev_back[c], cs));
+    }
+    KL(2, launch_sum_f64(h.min_dist, n, w.partials, kSumParts, w.sse, st));
+    {
+        PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
+        KL(4, launch_accumulate(h.X, n, d, h.labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
+        KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, h.C, p->empty, h.X, h.min_dist, h.C_new, h.counts,
+                              u.shift, u.taken, st));
+    }
+    CK(cudaMemcpyAsync(C_new_host, h.C_new, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToHost, st));
+    if (counts_host) CK(cudaMemcpyAsync(counts_host, h.counts, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, st));
+    for (int c = 0; c < nch; c++) CK(cudaStreamWaitEvent(st, ev_back[c], 0));
+    ctx->last_cnt = w.cnt;
+    ctx->last_sse = w.sse;
+    ctx->last_stream = st;
+    ctx->last_pairs = (uint64_t)n * (uint64_t)k;
+    if ((s = sync_status(ctx, w.cnt, st)) != KM_OK) return s;
+    if (shift_host) CK(cudaMemcpy(shift_host, u.shift, sizeof(double), cudaMemcpyDeviceToHost));
     return KM_OK;
 }
 

@@ -334,6 +334,34 @@ def test_lloyd_step_equals_assign_then_update(ctx, low, empty, shape):
     assert ref[3][-1] == 0 or empty == "farthest"
 
 
+@pytest.mark.parametrize("low,empty,shape", [("bf16", "farthest", (20000, 128, 300)), ("fp16", "keep", (7001, 64, 96)),
+                                             ("e4m3", "farthest", (5000, 64, 40)), ("fp32", "farthest", (3000, 16, 24)),
+                                             ("fp64", "keep", (2000, 8, 9)), ("bf16", "farthest", (300, 32, 7))])
+def test_lloyd_step_host_equals_device(ctx, low, empty, shape):
+    """km_lloyd_step_host (host buffers, rows in chunks overlapping copies and
+    kernels) gives km_lloyd_step's results bit for bit, pinned or pageable."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = shape
+    X, C = workloads.gaussian_mixture(n, d, k, seed=62)
+    p = pkg.params(low, empty=empty)
+    lab1, md1, Cn1, cnt1, sh1 = ctx.lloyd_step(_dev(X), _dev(C), p)
+    torch.cuda.synchronize()
+    ref = [t.cpu().numpy() for t in (lab1, md1, Cn1, cnt1)]
+    Xh, Ch = torch.from_numpy(X).pin_memory(), torch.from_numpy(C).pin_memory()
+    md = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+    cnt = torch.full((k,), -1, dtype=torch.int64).pin_memory()
+    lab2, md2, Cn2, cnt2, sh2 = ctx.lloyd_step_host(Xh, Ch, p, min_dist=md, counts=cnt)
+    assert np.array_equal(lab2.numpy(), ref[0])
+    assert np.array_equal(md2.numpy().view(np.uint64), ref[1].view(np.uint64))
+    assert np.array_equal(Cn2.numpy().view(np.uint32), ref[2].view(np.uint32))
+    assert np.array_equal(cnt2.numpy(), ref[3])
+    assert sh2 == sh1
+    assert ctx.stats()["pairs"] == n * k
+    lab3, _, Cn3, _, _ = ctx.lloyd_step_host(torch.from_numpy(X), torch.from_numpy(C), p)  # pageable
+    assert np.array_equal(lab3.numpy(), ref[0])
+    assert np.array_equal(Cn3.numpy().view(np.uint32), ref[2].view(np.uint32))
+
+
 def test_tc_large_k_full_row_path(ctx):
     """k = 57344: the full-row kernel's per-centre values no longer fit in
     shared memory and are recomputed in its binary64 pass.  In the
