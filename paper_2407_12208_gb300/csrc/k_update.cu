@@ -133,7 +133,7 @@ __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, cons
 // Integer (fixed-point) addition is order-independent, so the row order
 // inside a bucket (set by atomic cursors) does not change any bit of the
 // result.
-constexpr int SEG_CHUNK = 64;    // rows per warp work item
+constexpr int SEG_MAX = 512;     // most rows per warp work item (the 32-bit part sums stay exact)
 constexpr int SCAT_ROWS = 4096;  // rows per block of the histogram / scatter kernels
 
 // per-label counts (block histogram in shared memory, one global add per label)
@@ -150,8 +150,8 @@ __global__ void k_label_hist(const int32_t* __restrict__ labels, int64_t n, int 
 
 // Exclusive scans (one block of 1024 threads): bucket offsets, cursors, and
 // the offsets of each bucket's first work item; counts as int64.
-__global__ void k_bucket_scan(const int* __restrict__ cnt32, int k, int* __restrict__ off, int* __restrict__ cursor,
-                              int* __restrict__ item_off, long long* __restrict__ counts) {
+__global__ void k_bucket_scan(const int* __restrict__ cnt32, int k, int seg, int* __restrict__ off,
+                              int* __restrict__ cursor, int* __restrict__ item_off, long long* __restrict__ counts) {
     __shared__ int sa[1024], sb[1024];
     const int t = threadIdx.x, T = blockDim.x;
     const int per = (k + T - 1) / T;
@@ -159,7 +159,7 @@ __global__ void k_bucket_scan(const int* __restrict__ cnt32, int k, int* __restr
     int a = 0, b = 0;
     for (int j = j0; j < j1; j++) {
         a += cnt32[j];
-        b += (cnt32[j] + SEG_CHUNK - 1) / SEG_CHUNK;
+        b += (cnt32[j] + seg - 1) / seg;
     }
     sa[t] = a;
     sb[t] = b;
@@ -178,7 +178,7 @@ __global__ void k_bucket_scan(const int* __restrict__ cnt32, int k, int* __restr
         item_off[j] = ob;
         counts[j] = cnt32[j];
         oa += cnt32[j];
-        ob += (cnt32[j] + SEG_CHUNK - 1) / SEG_CHUNK;
+        ob += (cnt32[j] + seg - 1) / seg;
     }
     if (t == T - 1) {
         off[k] = sa[T - 1];
@@ -217,7 +217,7 @@ KM_DEV int bucket_of(const int* __restrict__ item_off, int k, int64_t it) {
 // 32 / LPR rows per load; exact sums in registers, folded across the row
 // groups of the warp at the end, one atomic add per coordinate per item.
 template <int NV4, int LPR>
-__global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, const int* __restrict__ off,
+__global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, int seg, const int* __restrict__ off,
                              const int* __restrict__ item_off, const int32_t* __restrict__ perm,
                              const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
     static_assert(LPR == 32 || NV4 == 1, "rows narrower than a warp take one float4 per lane");
@@ -233,8 +233,8 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
     for (int64_t it = w0; it < nitems; it += nw) {
         const int j = bucket_of(item_off, k, it);
         const int c = (int)(it - item_off[j]);
-        const int r0 = off[j] + c * SEG_CHUNK, r1 = min(off[j + 1], r0 + SEG_CHUNK);
-        // biased parts of the fixed-point values, summed modulo 2^32 (SEG_CHUNK rows at most)
+        const int r0 = off[j] + c * seg, r1 = min(off[j + 1], r0 + seg);
+        // biased parts of the fixed-point values, summed modulo 2^32 (SEG_MAX rows at most)
         unsigned a2[NV4][4], a1[NV4][4], a0[NV4][4];
 #pragma unroll
         for (int u = 0; u < NV4; u++)
@@ -305,7 +305,7 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
 // Small d (d <= 16): lanes over rows, each lane sums its rows' d coordinates,
 // then a warp reduction.
 template <int D>
-__global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k, const int* __restrict__ off,
+__global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k, int seg, const int* __restrict__ off,
                                    const int* __restrict__ item_off, const int32_t* __restrict__ perm,
                                    const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
     const FixedScale fx(fixed_shift(*amax_bits, n));
@@ -316,7 +316,7 @@ __global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k
     for (int64_t it = w0; it < nitems; it += nw) {
         const int j = bucket_of(item_off, k, it);
         const int c = (int)(it - item_off[j]);
-        const int r0 = off[j] + c * SEG_CHUNK, r1 = min(off[j + 1], r0 + SEG_CHUNK);
+        const int r0 = off[j] + c * seg, r1 = min(off[j + 1], r0 + seg);
         long long acc[D];
 #pragma unroll
         for (int l = 0; l < D; l++) acc[l] = 0;
@@ -576,13 +576,10 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         e = allow_max_smem(k_label_hist);
         if (e != cudaSuccess) return e;
         k_label_hist<<<(unsigned)nblk, 512, hsm, st>>>(labels, n, k, cnt32);
-        k_bucket_scan<<<1, 1024, 0, st>>>(cnt32, k, off, cursor, item_off, counts);
-        e = allow_max_smem(k_bucket_scatter);
-        if (e != cudaSuccess) return e;
-        k_bucket_scatter<<<(unsigned)nblk, 512, 2 * hsm, st>>>(labels, n, k, cursor, perm);
         // persistent grid: every block resident at once (a partial second wave
-        // would leave SMs idle), the items strided over the warps
-        const int64_t items = n / SEG_CHUNK + k + 1;
+        // would leave SMs idle), the items strided over the warps; work items of
+        // `seg` rows, about four per resident warp (fewer, longer items mean
+        // fewer atomic adds per centre coordinate)
         int per_sm = 1;
         if (d > 5) {
             const void* fn = d <= 32    ? (const void*)k_bucket_sum<1, 8>
@@ -595,17 +592,24 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         } else {
             per_sm = 8;
         }
+        const int64_t resident_warps = (int64_t)num_sms * std::max(per_sm, 1) * 8;
+        const int seg = (int)std::min<int64_t>(SEG_MAX, std::max<int64_t>(64, n / (resident_warps * 4) / 32 * 32));
+        k_bucket_scan<<<1, 1024, 0, st>>>(cnt32, k, seg, off, cursor, item_off, counts);
+        e = allow_max_smem(k_bucket_scatter);
+        if (e != cudaSuccess) return e;
+        k_bucket_scatter<<<(unsigned)nblk, 512, 2 * hsm, st>>>(labels, n, k, cursor, perm);
+        const int64_t items = n / seg + k + 1;
         const unsigned blocks =
             (unsigned)std::max<int64_t>(1, std::min<int64_t>((items * 32 + 255) / 256, (int64_t)num_sms * std::max(per_sm, 1)));
-        if (d == 1) k_bucket_sum_small<1><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
-        else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
-        else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
-        else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 32) k_bucket_sum<1, 8><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 64) k_bucket_sum<1, 16><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 128) k_bucket_sum<1, 32><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 256) k_bucket_sum<2, 32><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
-        else k_bucket_sum<4, 32><<<blocks, 256, 0, st>>>(X, n, d, k, off, item_off, perm, absmax_bits, sums);
+        if (d == 1) k_bucket_sum_small<1><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 32) k_bucket_sum<1, 8><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 64) k_bucket_sum<1, 16><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 128) k_bucket_sum<1, 32><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
+        else if (d <= 256) k_bucket_sum<2, 32><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
+        else k_bucket_sum<4, 32><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
         return cudaGetLastError();
     }
     e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);
