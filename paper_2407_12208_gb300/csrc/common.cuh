@@ -104,6 +104,11 @@ KM_DEV bool mbar_wait_drain(uint64_t* bar, uint32_t parity, unsigned* status) {
 }
 
 // --------------------------------------------------------------------- TMA
+// Asks L2 to fetch `bytes` (a multiple of 16) at the 16-byte aligned
+// global address p; no register receives anything.
+KM_DEV void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 KM_DEV void tma_prefetch_desc(const void* tmap) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
 }

@@ -57,6 +57,10 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
                 xv[u] = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
                 cv[u] = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            // the next pair's point row on its way to L2 while this one is
+            // evaluated (rows of 512 bytes or more: measured to pay off there)
+            if (d >= 128 && sl == 0 && pi + ngroups < np && nxt.x != pr.x)
+                prefetch_l2_bulk(X + (int64_t)nxt.x * d, (uint32_t)d * 4u);
 #pragma unroll
             for (int u = 0; u < NVV; u++) {
                 const float t0 = xv[u].x - cv[u].x, t1 = xv[u].y - cv[u].y;

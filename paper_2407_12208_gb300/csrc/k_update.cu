@@ -241,9 +241,14 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
 #pragma unroll
             for (int t = 0; t < 4; t++) a2[u][t] = a1[u][t] = a0[u][t] = 0u;
         unsigned rounds = 0;
+        int64_t next_i = (r0 + lane < r1) ? (int64_t)perm[r0 + lane] : -1;
         for (int base = r0; base < r1; base += 32) {
-            // the row indices of 32 rows in one coalesced load, then broadcast
-            const int64_t my_i = (base + lane < r1) ? (int64_t)perm[base + lane] : -1;
+            // the row indices of 32 rows in one coalesced load, then broadcast;
+            // the following 32 rows' indices are loaded now and their data sent
+            // to L2 once this round's loads are out
+            const int64_t my_i = next_i;
+            next_i = (base + 32 + lane < r1) ? (int64_t)perm[base + 32 + lane] : -1;
+            bool pf = true;
 #pragma unroll 1
             for (int b0 = 0; b0 < 32 && base + b0 < r1; b0 += STEP) {
                 rounds++;
@@ -257,6 +262,10 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
                         v[b][u] = (i >= 0 && cidx < d4) ? reinterpret_cast<const float4*>(X + i * d)[cidx]
                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
+                }
+                if (LPR < 32 && pf) {  // narrow rows (measured: a loss at 512-byte rows)
+                    if (next_i >= 0) prefetch_l2_bulk(X + next_i * d, (uint32_t)d * 4u);
+                    pf = false;
                 }
 #pragma unroll
                 for (int b = 0; b < RB; b++)
