@@ -131,6 +131,23 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
 // Group path (d % 4 == 0, padded width <= 256): 8 lanes per row, 4 rows per
 // warp, so the row reductions take 3 shuffle levels and serve 4 rows at once.
 // Lane l of a row's 8 holds float4 l, l + 8, ... (NV of them).
+// Two coordinates (scale 1, 16-bit formats) into the row's running sums, two
+// per packed instruction: ||x||^2 as a pair of double-floats (exact product,
+// two-sum), ||x~||^2 and ||x~ - x||^2 in fp32.
+KM_DEV float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+KM_DEV void row_sums2(float2 x, float2 q, float2& hi, float2& lo, float2& qq, float2& rr) {
+    const float2 p = __fmul2_rn(x, x);
+    const float2 pe = __ffma2_rn(x, x, neg2(p));
+    const float2 s = __fadd2_rn(hi, p);
+    const float2 bb = __fadd2_rn(s, neg2(hi));
+    const float2 e = __fadd2_rn(__fadd2_rn(hi, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
+    hi = s;
+    lo = __fadd2_rn(lo, __fadd2_rn(e, pe));
+    qq = __ffma2_rn(q, q, qq);
+    const float2 r = __fadd2_rn(q, neg2(x));  // exact (Sterbenz)
+    rr = __ffma2_rn(r, r, rr);
+}
+
 template <int NV>
 __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
                               float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
@@ -182,6 +199,39 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
         }
         const float inv = 1.0f / s;
         float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
+        if (fmt != 2) {
+            // 16-bit formats (scale 1): packed arithmetic, two coordinates at a time
+            float2 h2 = make_float2(0.f, 0.f), l2 = h2, qq2 = h2, rr2 = h2;
+#pragma unroll
+            for (int u = 0; u < NV; u++) {
+                const int c = sl + 8 * u;
+                if (c >= ldq4) continue;
+                const float2 a = make_float2(x[u].x, x[u].y), b = make_float2(x[u].z, x[u].w);
+                float2 qa, qb;
+                uint2 w;
+                if (fmt == 0) {
+                    const __half2 ha = __float22half2_rn(a), hb = __float22half2_rn(b);
+                    qa = __half22float2(ha);
+                    qb = __half22float2(hb);
+                    w.x = *reinterpret_cast<const uint32_t*>(&ha);
+                    w.y = *reinterpret_cast<const uint32_t*>(&hb);
+                } else {
+                    const __nv_bfloat162 ha = __float22bfloat162_rn(a), hb = __float22bfloat162_rn(b);
+                    qa = __bfloat1622float2(ha);
+                    qb = __bfloat1622float2(hb);
+                    w.x = *reinterpret_cast<const uint32_t*>(&ha);
+                    w.y = *reinterpret_cast<const uint32_t*>(&hb);
+                }
+                reinterpret_cast<uint2*>(Aq)[i * ldq4 + c] = w;
+                row_sums2(a, qa, h2, l2, qq2, rr2);
+                row_sums2(b, qb, h2, l2, qq2, rr2);
+            }
+            ph = h2.x;
+            pl = l2.x;
+            df_add(ph, pl, h2.y, l2.y);
+            q2 = qq2.x + qq2.y;
+            r2 = rr2.x + rr2.y;
+        } else
 #pragma unroll
         for (int u = 0; u < NV; u++) {
             const int c = sl + 8 * u;
