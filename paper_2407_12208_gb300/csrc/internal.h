@@ -9,7 +9,7 @@ namespace km {
 // Epilogue groups of the screening kernel (four warps each; tile t goes to
 // group t mod TC_GROUPS) and candidate-list entries per row and group (48 per
 // row in all).
-constexpr int TC_GROUPS = 2;
+constexpr int TC_GROUPS = 3;
 constexpr int TC_LIST = 48 / TC_GROUPS;
 // Candidate pairs reserved per row in the workspace; rows past the capacity
 // are recomputed by the full-row kernel.

@@ -44,9 +44,9 @@ struct TcLayout {
     size_t a_bytes, b_bytes, list_off, stage_off, bar_off, total;
 };
 
-// stg: each epilogue warp's staging area for its lanes' e values (16 float4
-// per lane, 8 KB per warp)
-constexpr size_t TC_STAGE_BYTES = (size_t)TC_NG * 4 * 16 * 32 * 16;
+// stg: each epilogue warp's staging area for its lanes' e values (8 TC_CW
+// float4 per lane, 4 TC_CW KB per warp)
+constexpr size_t TC_STAGE_BYTES = (size_t)TC_NG * 4 * (8 * TC_CW) * 32 * 16;
 __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k, bool stg) {
     TcLayout L;
     L.BN = BN;
