@@ -271,10 +271,16 @@ __global__ void __launch_bounds__(256) k_amb_fp64(const int32_t* __restrict__ am
                 if (v32[rp.x + r] * (1.0f - g) <= up) js[nb++] = pairs[rp.x + r].y;
             if (nb == 0) break;
             __syncwarp();
-            for (int e = lane; e < nb * d; e += 32) {
-                const int b = e / d, l = e - b * d;
-                const double u = __dsub_rn((double)x[l], (double)C[(int64_t)js[b] * d + l]);
-                prod[e] = __dmul_rn(u, u);
+            // lanes over the coordinates (coalesced loads, no index division)
+#pragma unroll
+            for (int b = 0; b < AMB_B; b++) {
+                if (b < nb) {
+                    const float* c = C + (int64_t)js[b] * d;
+                    for (int l = lane; l < d; l += 32) {
+                        const double u = __dsub_rn((double)x[l], (double)c[l]);
+                        prod[b * d + l] = __dmul_rn(u, u);
+                    }
+                }
             }
             __syncwarp();
             if (lane < nb) {
