@@ -27,6 +27,10 @@
  *    KM_ETIMEOUT.
  *  - There is no CPU fallback: an unsupported combination returns
  *    KM_EUNSUPPORTED.
+ *  - A context serves one calling thread at a time (its last-call record,
+ *    profiling events and host-step copy streams are unsynchronised state);
+ *    concurrent callers use one context each, or the serving calls, which
+ *    are thread-safe.
  */
 #ifndef MPKM_H
 #define MPKM_H
