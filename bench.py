@@ -21,6 +21,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -102,9 +103,13 @@ def _profile_traffic(n: int):
 class ClockSampler:
     """nvidia-smi samples of SM clock / throttle reasons during the timed region."""
 
-    def __init__(self, device_uuid: str | None):
+    def __init__(self, device_uuid: str | None, out_path: str | None = None):
         self.proc = None
-        self.out = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+        if out_path:
+            self.out = out_path
+        else:
+            fd, self.out = tempfile.mkstemp(prefix="mpkm_clocks_", suffix=".csv")
+            os.close(fd)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -112,7 +117,7 @@ class ClockSampler:
         if device_uuid:
             cmd[1:1] = ["-i", device_uuid]
         try:
-            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.out)), exist_ok=True)
             self.f = open(self.out, "w")
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
@@ -204,7 +209,7 @@ def run_ours(args):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         uuid = None
-    clk = ClockSampler(uuid)
+    clk = ClockSampler(uuid, args.clocks_csv)
     time.sleep(0.3)
     ctx.phase_times()
     ctx.set_profiling(True)
@@ -469,6 +474,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="rows (profiling a smaller case of the same kernels)")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only: no end-to-end, FP64 or CPU legs (for profiler runs)")
