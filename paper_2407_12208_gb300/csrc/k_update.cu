@@ -64,6 +64,24 @@ struct FixedScale {
         b1 = __float_as_uint(__fmaf_rn(p1, 0x1p-20f, c0));
         b2 = __float_as_uint(__fmaf_rn(p2, 0x1p-40f, c0));
     }
+    // split() on two values at once: the same operations, two per packed
+    // instruction (each half rounded exactly as its scalar counterpart)
+    KM_DEV void split2(float2 v, uint2& b2, uint2& b1, uint2& b0) const {
+        const float2 c40 = make_float2(0x1.8p63f, 0x1.8p63f), n40 = make_float2(-0x1.8p63f, -0x1.8p63f);
+        const float2 c20 = make_float2(0x1.8p43f, 0x1.8p43f), n20 = make_float2(-0x1.8p43f, -0x1.8p43f);
+        const float2 c0 = make_float2(0x1.8p23f, 0x1.8p23f);
+        const float2 y = __fmul2_rn(__fmul2_rn(v, make_float2(f1, f1)), make_float2(f2, f2));
+        const float2 p2 = __fadd2_rn(__fadd2_rn(y, c40), n40);
+        const float2 r = __fadd2_rn(y, make_float2(-p2.x, -p2.y));
+        const float2 p1 = __fadd2_rn(__fadd2_rn(r, c20), n20);
+        const float2 r0 = __fadd2_rn(r, make_float2(-p1.x, -p1.y));
+        const float2 t0 = __fadd2_rn(r0, c0);
+        const float2 t1 = __ffma2_rn(p1, make_float2(0x1p-20f, 0x1p-20f), c0);
+        const float2 t2 = __ffma2_rn(p2, make_float2(0x1p-40f, 0x1p-40f), c0);
+        b0 = make_uint2(__float_as_uint(t0.x), __float_as_uint(t0.y));
+        b1 = make_uint2(__float_as_uint(t1.x), __float_as_uint(t1.y));
+        b2 = make_uint2(__float_as_uint(t2.x), __float_as_uint(t2.y));
+    }
     // sum of m split values -> int64 (the biased parts were added modulo 2^32;
     // each true part sum is below 2^31 in magnitude for m <= 2^10)
     KM_DEV static long long combine(unsigned s2, unsigned s1, unsigned s0, unsigned m) {
@@ -271,15 +289,15 @@ __global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int 
                 for (int b = 0; b < RB; b++)
 #pragma unroll
                     for (int u = 0; u < NV4; u++) {
-                        const float xs[4] = {v[b][u].x, v[b][u].y, v[b][u].z, v[b][u].w};
-#pragma unroll
-                        for (int t = 0; t < 4; t++) {
-                            unsigned q2, q1, q0;
-                            fx.split(xs[t], q2, q1, q0);
-                            a2[u][t] += q2;
-                            a1[u][t] += q1;
-                            a0[u][t] += q0;
-                        }
+                        uint2 q2, q1, q0;
+                        fx.split2(make_float2(v[b][u].x, v[b][u].y), q2, q1, q0);
+                        a2[u][0] += q2.x; a2[u][1] += q2.y;
+                        a1[u][0] += q1.x; a1[u][1] += q1.y;
+                        a0[u][0] += q0.x; a0[u][1] += q0.y;
+                        fx.split2(make_float2(v[b][u].z, v[b][u].w), q2, q1, q0);
+                        a2[u][2] += q2.x; a2[u][3] += q2.y;
+                        a1[u][2] += q1.x; a1[u][3] += q1.y;
+                        a0[u][2] += q0.x; a0[u][3] += q0.y;
                     }
             }
         }
