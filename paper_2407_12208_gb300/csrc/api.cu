@@ -658,7 +658,11 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
         CK(cudaStreamWaitEvent(st, ev_in[c], 0));
         CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
         s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
-        if (s != KM_OK) return s;
+        if (s != KM_OK) {
+            // no copy may still be reading the caller's buffers after the return
+            for (cudaStream_t c2 : ctx->copy_st) cudaStreamSynchronize(c2);
+            return s;
+        }
         // this chunk's labels and distances go back while the next chunk is assigned
         CK(cudaEventRecord(ev_out[c], st));
         CK(cudaStreamWaitEvent(cs, ev_out[c], 0));

@@ -362,6 +362,22 @@ def test_lloyd_step_host_equals_device(ctx, low, empty, shape):
     assert np.array_equal(Cn3.numpy().view(np.uint32), ref[2].view(np.uint32))
 
 
+def test_lloyd_step_host_rejects_bad_arguments(ctx):
+    import paper_2407_12208_gb300 as pkg
+    p = pkg.params("bf16")
+    X, C = torch.zeros((100, 16)), torch.zeros((4, 16))
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pkg.KmError) as ei:
+        ctx.lloyd_step_host(X, C, p, ws=small)
+    assert ei.value.status == pkg._binding.KM_ENOMEM
+    with pytest.raises(pkg.KmError) as ei:
+        ctx.lloyd_step_host(torch.zeros((3, 16)), C, p)  # k > n
+    assert ei.value.status == pkg._binding.KM_EINVAL
+    with pytest.raises(pkg.KmError) as ei:
+        ctx.lloyd_step_host(torch.zeros((100, 8)), torch.zeros((4, 8)), pkg.params("e4m3"))  # E4M3 needs d >= 16
+    assert ei.value.status == pkg._binding.KM_EUNSUPPORTED
+
+
 def test_tc_large_k_full_row_path(ctx):
     """k = 57344: the full-row kernel's per-centre values no longer fit in
     shared memory and are recomputed in its binary64 pass.  In the
