@@ -235,12 +235,15 @@ KM_DEV int bucket_of(const int* __restrict__ item_off, int k, int64_t it) {
 // 32 / LPR rows per load; exact sums in registers, folded across the row
 // groups of the warp at the end, one atomic add per coordinate per item.
 template <int NV4, int LPR>
-__global__ void k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, int seg, const int* __restrict__ off,
+__global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ? 1 : 2)) k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, int seg,
+                                                       const int* __restrict__ off,
                              const int* __restrict__ item_off, const int32_t* __restrict__ perm,
                              const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
     static_assert(LPR == 32 || NV4 == 1, "rows narrower than a warp take one float4 per lane");
     constexpr int G = 32 / LPR;                            // rows per warp load
-    constexpr int RB = (16 / NV4) < (32 / G) ? 16 / NV4 : 32 / G;  // loads in flight per lane
+    // loads in flight per lane: 8 at full-warp rows of one float4 (three blocks
+    // per SM), else up to 16
+    constexpr int RB = (NV4 == 1 && LPR == 32) ? 8 : ((16 / NV4) < (32 / G) ? 16 / NV4 : 32 / G);
     constexpr int STEP = RB * G;                           // rows per round (divides 32)
     const FixedScale fx(fixed_shift(*amax_bits, n));
     const int lane = threadIdx.x & 31, sub = lane / LPR, cl = lane % LPR;
