@@ -279,6 +279,7 @@ def test_full_size_bf16_sampled():
 
 
 @pytest.mark.parametrize("wl,n,d,k,low", [
+    ("uniform_pairs", 1_000_000, 128, 1024, "bf16"),     # the benchmark's default workload
     ("cancellation", 1_000_000, 128, 1024, "bf16"),      # every pair flagged, every list overflows
     ("gaussian_mixture", 4_000_000, 64, 256, "bf16"),     # the mixed Lloyd iteration shape
     ("voronoi", 4096 * 4096, 5, 16, "fp32"),              # the image shape, fp32 direct
