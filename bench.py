@@ -7,9 +7,15 @@ test, direct-formula refinement and certified argmin (labels, min_dist),
 then the centre update (Eq. (center)).  Default workload: X uniform[0,1)
 1e6 x 128 fp32, C = 1024 distinct rows of X, BF16 cross term, rho = 5.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
-instead (on a bounded sample of the same workload).  Multi-GPU (torchrun):
-independent replicas, one per GPU, no collective on the data path.
+Prints one JSON line (rank 0): the device-resident step rate (`value`), the
+screening kernel against the measured BF16 roofline (`roofline`), the same
+step end to end from pinned host buffers through km_lloyd_step_host (`e2e`),
+the oracle on the host cores (`cpu_baseline`), the plain FP64 path on a row
+sample (`fp64_path`), the served stream's latencies (`serving`), SM clocks
+sampled during the timed region (`clocks`) and the library's own launch count
+(`gpu_launches`).  `--impl reference` times the CPU oracle instead (on a
+bounded sample of the same workload).  Multi-GPU (torchrun): independent
+replicas, one per GPU, no collective on the data path.
 """
 from __future__ import annotations
 
