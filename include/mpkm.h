@@ -162,6 +162,14 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
                         int64_t* counts, double* shift_host, void* ws, size_t ws_bytes,
                         void* stream);
 
+/* Failure-path check (no paper counterpart): launches one warp that waits on
+ * an mbarrier no thread arrives at.  The wait is the same bounded wait every
+ * kernel of the library uses: after its budget (about a second) it sets the
+ * timeout bit of the device status word and returns, so the call returns
+ * KM_ETIMEOUT and the context (and device) stay usable.  ws: at least 256
+ * bytes of device memory, 256-byte aligned. */
+km_status km_selftest_timeout(km_ctx* ctx, void* ws, size_t ws_bytes, void* stream);
+
 /* km_lloyd_step on HOST buffers (no paper counterpart: the transfer around
  * one iteration of Alg. 3's loop body, for callers whose data lives in host
  * memory).  X_host (n x d fp32), C_host (k x d) are read, and labels_host

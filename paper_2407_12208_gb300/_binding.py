@@ -28,7 +28,7 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
-           "km_lloyd_step_host"]
+           "km_lloyd_step_host", "km_selftest_timeout"]
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         lib.km_host_workspace_size.argtypes = [vp, i64, i32, i32, P, c.POINTER(sz)]
         lib.km_lloyd_step_host.argtypes = [vp, vp, i64, i32, i32, vp, P, vp, vp, vp, vp, c.POINTER(c.c_double), vp,
                                            sz, vp]
+        lib.km_selftest_timeout.argtypes = [vp, vp, sz, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -313,6 +314,13 @@ class Context:
                                           ws.numel(), _stream(stream)))
         t = it.value
         return C_out, labels, sse[: t + 1], eta[: t + 1], t
+
+    def selftest_timeout(self, stream=None) -> int:
+        """km_selftest_timeout: the status of a bounded wait that runs out
+        (KM_ETIMEOUT expected); raises nothing."""
+        import torch
+        ws = torch.empty(4096, dtype=torch.uint8, device="cuda:%d" % self.device)
+        return int(self.lib.km_selftest_timeout(self.h, _ptr(ws), ws.numel(), _stream(stream)))
 
     def stats(self) -> dict:
         s = Stats()

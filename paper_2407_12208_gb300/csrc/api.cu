@@ -929,6 +929,38 @@ void* g_static_addr[kStaticMaxDevices];  // resolved scratch address per device,
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticCntBytes + (size_t)KM_STATIC_MAX_ROWS * sizeof(int32_t)];
 
+namespace {
+// Failure-path check: one warp waits on an mbarrier that no thread arrives at.
+// The wait is the library's bounded one: it runs out after KM_WAIT_CYCLES,
+// sets the status word's timeout bit and returns; nothing faults or hangs.
+__global__ void k_wait_unsignalled(DevCounters* cnt) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    (void)mbar_wait(&bar, 0, (volatile int*)&abort_flag, &cnt->status);
+}
+}  // namespace
+
+extern "C" km_status km_selftest_timeout(km_ctx* ctx, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!ws) return fail(ctx, KM_EINVAL, "null workspace");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < sizeof(DevCounters)) return fail(ctx, KM_ENOMEM, "workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    DevCounters* cnt = reinterpret_cast<DevCounters*>(ws);
+    CK(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), st));
+    k_wait_unsignalled<<<1, 32, 0, st>>>(cnt);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    return sync_status(ctx, cnt, st);
+}
+
 extern "C" km_status km_assign_static(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
                                       int32_t* labels, double* min_dist, void* stream) {
     km_status s = check_common(ctx, X, n, C, k, d);
