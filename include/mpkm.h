@@ -110,9 +110,30 @@ km_status km_init(km_ctx** out, int device, void* arena, size_t arena_bytes);
 km_status km_destroy(km_ctx* ctx);
 const char* km_last_error(const km_ctx* ctx);
 
-/* Bytes of workspace the synchronous calls need for these sizes. */
+/* Bytes of workspace the synchronous calls (km_distances, km_assign,
+ * km_update_centroids, km_lloyd_step, km_lloyd_run with p->max_iter) need for
+ * these sizes: the largest of their layouts, all O(n (d + k_slots)) -- about
+ * 0.66 GB at n = 1e6, d = 128, k = 1024 with a 16-bit low format. */
 km_status km_workspace_size(const km_ctx* ctx, int64_t n, int d, int k, const km_params* p,
                             size_t* bytes);
+
+/* The quantisation of Alg. 2's first line (Section 4.3: x~ = fl_l(x)) as the
+ * tensor-core paths perform it, with the row statistics they use.
+ *  - Xq: n rows of ldq elements of the low format, ldq = d rounded up to a
+ *    multiple of 8 (fp16, bf16: 2 bytes each) or 16 (E4M3: 1 byte each),
+ *    padding zero.  E4M3 holds fl(x / s) (saturating), fp16/bf16 fl(x).
+ *  - stats: n x 4 floats (16-byte aligned): ||x||^2 (formed to about 2^-44
+ *    and rounded to fp32), then ||x||, ||x~|| and ||x~ - x|| with
+ *    x~ = s fl(x / s), each inflated by (1 + 2^-12) so that it bounds the
+ *    exact norm from above; an element that overflowed the low format makes
+ *    the last two +inf.
+ *  - scale: n floats, the row's scale s.  E4M3: the smallest power of two
+ *    with max_l |x_l| / s <= 448 (so the row maximum lands in (224, 448]),
+ *    at least 2^-126, and 1 for an all-zero row; fp16/bf16: 1.
+ * low must be KM_FP16, KM_BF16 or KM_E4M3 (else KM_EUNSUPPORTED).  Device
+ * pointers, asynchronous on `stream`. */
+km_status km_quantize(km_ctx* ctx, const float* X, int64_t n, int d, int32_t low, void* Xq, float* stats,
+                      float* scale, void* stream);
 
 /* Alg. 2 for all pairs (Section 4.3; the distance-matrix experiments of
  * Section 6.1).  D (n x k fp32, row-major) receives, per pair, the expanded
@@ -129,10 +150,11 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
  * ties).  The argmin is certified: it equals the binary64 direct-formula
  * argmin wherever that row's best/second-best gap exceeds the proved error
  * bounds (in practice: relative gaps above ~1e-7).  min_dist (nullable,
- * n doubles) receives ||x_i - c_label||^2 by the direct formula: binary64
- * where it was recomputed in binary64, else fp32 with relative error
- * <= gamma_{d+2}(2^-24) (Theorem 4.1).  n_flagged_host (nullable, host):
- * number of pairs that failed the reliability test. */
+ * n doubles) receives ||x_i - c_label||^2 by the direct formula (Eq.
+ * (dist-direct)) from the fp32 data to binary64 accuracy: relative error
+ * below 2^-40 (exactly the binary64 sum in coordinate order on the FP64
+ * path).  n_flagged_host (nullable, host): number of pairs that failed the
+ * reliability test. */
 km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
                     const km_params* p, int32_t* labels, double* min_dist,
                     uint64_t* n_flagged_host, void* ws, size_t ws_bytes, void* stream);
@@ -228,11 +250,10 @@ km_status km_get_launch_count(const km_ctx* ctx, uint64_t* launches);
 /* ---- assignment without allocation -------------------------------------- */
 
 /* The paper has no counterpart to this call.  It is km_assign with
- * low = KM_FP32_DIRECT (the same kernels and the same results: fp32 direct
- * distances certified by Theorem 4.1, binary64 for the rows whose argmin
- * they leave open) for callers that cannot allocate device memory when they
- * assign: a process whose device memory is all held by a caching pool or by
- * another framework, where a cudaMalloc would fail, and latency-bound loops
+ * low = KM_FP32_DIRECT (the same kernels and the same results) for callers
+ * that cannot allocate device memory when they assign: a process whose
+ * device memory is all held by a caching pool or by another framework,
+ * where a cudaMalloc would fail, and latency-bound loops
  * that must not call cudaMalloc/cudaFree (cudaFree can synchronise the whole
  * device).  It takes no workspace.  Its scratch (the device counters and the
  * list of rows left open, one int32 per row) is a file-scope device array of

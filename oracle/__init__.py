@@ -56,6 +56,8 @@ def _load():
         lib.orc_quantize.argtypes = [_f32p, c.c_int64, c.c_int, _f32p]
         lib.orc_gamma.restype = c.c_double
         lib.orc_gamma.argtypes = [c.c_int, c.c_double]
+        lib.orc_dist_labelled.restype = None
+        lib.orc_dist_labelled.argtypes = [_f32p, c.c_int64, _f32p, c.c_int, c.c_int, _i32p, _f64p]
         lib.orc_dist_direct.restype = None
         lib.orc_dist_direct.argtypes = [_f32p, c.c_int64, _f32p, c.c_int, c.c_int, _f64p]
         lib.orc_assign.restype = None
@@ -122,6 +124,17 @@ def dist_direct(X, C) -> np.ndarray:
     D = np.empty((n, k), dtype=np.float64)
     _load().orc_dist_direct(X, n, C, k, d, D)
     return D
+
+
+def dist_labelled(X, C, labels) -> np.ndarray:
+    """Eq. (dist-direct) in binary64 between each x_i and c_{labels[i]}."""
+    X, C = _f32(X), _f32(C)
+    n, d = X.shape
+    k = C.shape[0]
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    out = np.empty(n, dtype=np.float64)
+    _load().orc_dist_labelled(X, n, C, k, d, lab, out)
+    return out
 
 
 def assign(X, C):

@@ -100,6 +100,16 @@ double orc_dist_direct_pair(const float* x, const float* y, int d) {
     return s;
 }
 
+/* Eq. (dist-direct) for one given centre per point: out[i] = d(x_i, c_{labels[i]})^2,
+ * the distance the assignment reports for the centre it chose.            */
+void orc_dist_labelled(const float* X, int64_t n, const float* C, int k, int d, const int32_t* labels,
+                       double* out) {
+    for (int64_t i = 0; i < n; i++) {
+        int j = labels[i];
+        out[i] = (j >= 0 && j < k) ? orc_dist_direct_pair(X + i * d, C + (int64_t)j * d, d) : NAN;
+    }
+}
+
 void orc_dist_direct(const float* X, int64_t n, const float* C, int k, int d, double* D) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++)
@@ -312,8 +322,16 @@ void orc_row_quant_stats(const float* X, int64_t n, int d, int fmt, int per_row_
         if (per_row_scale) {
             double amax = 0.0;
             for (int l = 0; l < d; l++) if (fabs((double)x[l]) > amax) amax = fabs((double)x[l]);
-            /* s = 2^ceil(log2(amax / 448)): the row maximum lands in the top binade */
-            if (amax > 0.0) { int e; frexp(amax / 448.0, &e); s = ldexp(1.0, e); if (amax / 448.0 == ldexp(1.0, e - 1)) s = ldexp(1.0, e - 1); }
+            /* s = 2^ceil(log2(amax / 448)): the row maximum lands in the top
+             * binade; s is kept a normal binary32 number (s >= 2^-126), the
+             * scale being applied in binary32; an all-zero row keeps s = 1 */
+            if (amax > 0.0) {
+                int e;
+                frexp(amax / 448.0, &e);
+                s = ldexp(1.0, e);
+                if (amax / 448.0 == ldexp(1.0, e - 1)) s = ldexp(1.0, e - 1);
+                if (s < ldexp(1.0, -126)) s = ldexp(1.0, -126);
+            }
         }
         double a = 0.0, b = 0.0, c = 0.0;
         for (int l = 0; l < d; l++) {

@@ -28,7 +28,7 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
-           "km_lloyd_step_host", "km_selftest_timeout"]
+           "km_lloyd_step_host", "km_selftest_timeout", "km_quantize"]
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         lib.km_lloyd_step_host.argtypes = [vp, vp, i64, i32, i32, vp, P, vp, vp, vp, vp, c.POINTER(c.c_double), vp,
                                            sz, vp]
         lib.km_selftest_timeout.argtypes = [vp, vp, sz, vp]
+        lib.km_quantize.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -200,6 +201,21 @@ class Context:
                                        _ptr(min_dist), ctypes.byref(nf) if want_flagged else None, _ptr(ws),
                                        ws.numel(), _stream(stream)))
         return labels, min_dist, (nf.value if want_flagged else None)
+
+    def quantize(self, X, low="bf16", stream=None):
+        """km_quantize: (Xq as raw bytes n x (ldq * element size) uint8,
+        stats n x 4 float32, scale n float32)."""
+        import torch
+        n, d = X.shape
+        lowv = LOW_NAMES[low] if isinstance(low, str) else int(low)
+        esz = 1 if lowv == E4M3 else 2
+        ldq = (d + 15) // 16 * 16 if lowv == E4M3 else (d + 7) // 8 * 8
+        Xq = torch.empty((n, ldq * esz), dtype=torch.uint8, device=X.device)
+        stats = torch.empty((n, 4), dtype=torch.float32, device=X.device)
+        scale = torch.empty(n, dtype=torch.float32, device=X.device)
+        self._check(self.lib.km_quantize(self.h, _ptr(X), n, d, lowv, _ptr(Xq), _ptr(stats), _ptr(scale),
+                                         _stream(stream)))
+        return Xq, stats, scale
 
     def assign_static(self, X, C, labels, min_dist, stream=None):
         """km_assign_static: the fp32 direct assignment with the library's

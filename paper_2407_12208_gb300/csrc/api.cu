@@ -122,7 +122,6 @@ struct Carve {
 struct AssignWs {
     DevCounters* cnt;
     ColMax* colmax;
-    float* cscale_u;
     void* Xq;
     void* Cq;
     float4* xstat;
@@ -130,6 +129,7 @@ struct AssignWs {
     float4* cstat;
     float* cscale;
     float* qpad;
+    float* spad;
     uint32_t* cand;
     int2* pairs;
     float* v32;
@@ -141,14 +141,21 @@ struct AssignWs {
     double* partials;
     double* sse;
     int2* queue;
+    int64_t qcap;
     unsigned long long* qlen;
 };
+
+// Flagged pairs the distance-matrix call queues for the binary64 patch: four
+// per row (at least 2^20, at most all n k); more flagged pairs than that are
+// found by a scan of D for their marks instead.
+int64_t flag_queue_cap(int64_t n, int k) {
+    return std::min<int64_t>(n * (int64_t)k, std::max<int64_t>(4 * n, (int64_t)1 << 20));
+}
 
 AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distances) {
     AssignWs w{};
     w.cnt = cv.take<DevCounters>(1);
     w.colmax = cv.take<ColMax>(1);
-    w.cscale_u = cv.take<float>(1);
     w.partials = cv.take<double>(kSumParts);
     w.sse = cv.take<double>(1);
     w.amb_list = cv.take<int32_t>((size_t)n);
@@ -163,6 +170,7 @@ AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distance
         w.cstat = cv.take<float4>((size_t)k);
         w.cscale = cv.take<float>((size_t)k);
         w.qpad = cv.take<float>((size_t)kpad_of(k));
+        w.spad = cv.take<float>((size_t)kpad_of(k));
         w.rowinfo = cv.take<int4>((size_t)n * TC_GROUPS);
         w.ovf_list = cv.take<int32_t>((size_t)n);
         if (!distances) {
@@ -172,7 +180,8 @@ AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distance
             w.pairs = cv.take<int2>((size_t)w.pair_cap);
             w.v32 = cv.take<float>((size_t)w.pair_cap);
         } else {
-            w.queue = cv.take<int2>((size_t)n * k);
+            w.qcap = flag_queue_cap(n, k);
+            w.queue = cv.take<int2>((size_t)w.qcap);
             w.qlen = cv.take<unsigned long long>(1);
         }
     }
@@ -282,6 +291,15 @@ TestParams make_tp(const km_params* p, int d) {
 
 bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
+// The centres in the low format with their statistics (per-row power-of-two
+// scales for E4M3), the column maxima of the bound, q_j and the scales padded
+// to the tile width.
+km_status prepare_centres(km_ctx* ctx, const float* C, int k, int d, int fmt, const AssignWs& w, cudaStream_t st) {
+    KL(1, launch_quantize(C, k, d, fmt, ldq_of(fmt, d), w.Cq, w.cstat, w.cscale, st));
+    KL(1, launch_colmax(w.cstat, k, fmt == 2 ? w.cscale : nullptr, w.colmax, w.qpad, w.spad, kpad_of(k), st));
+    return KM_OK;
+}
+
 // One assignment of X against C into labels/min_dist (all device).
 // x_absmax (nullable, zeroed by the caller): max |x| over X, folded out of the
 // quantisation pass (tensor-core paths) or of the direct distances.
@@ -289,6 +307,7 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
                      int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st,
                      unsigned* x_absmax = nullptr) {
     const TestParams tp = make_tp(p, d);
+    km_status s = KM_OK;
     if (p->low == KM_FP64_DIRECT || p->low == KM_FP32_DIRECT) {
         const bool acc64 = p->low == KM_FP64_DIRECT;
         {
@@ -308,20 +327,13 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     const int esz = fmt == 2 ? 1 : 2;
     {
         PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
-        if (!x_prepared) KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st, x_absmax));
-        if (fmt == 2) {
-            KL(1, launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
-            KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
-            KL(1, launch_colmax(w.cstat, k, w.cscale_u, w.colmax, w.qpad, kpad_of(k), st));
-        } else {
-            KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
-            KL(1, launch_colmax(w.cstat, k, nullptr, w.colmax, w.qpad, kpad_of(k), st));
-        }
+        if (!x_prepared) KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, st, x_absmax));
+        if ((s = prepare_centres(ctx, C, k, d, fmt, w, st)) != KM_OK) return s;
     }
     TcArgs a{};
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
     a.kchunks = (ldq * esz + 127) / 128;
-    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
+    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.spad = w.spad; a.colmax = w.colmax;
     a.tp = tp; a.mode = 0; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
     a.cbits = 1;
     while ((1 << a.cbits) < k) a.cbits++;  // column bits of a candidate entry (k <= 65535: at most 16)
@@ -355,6 +367,27 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
         }
     }
     (void)esz;
+    return KM_OK;
+}
+
+// min_dist of the winners to binary64 accuracy (the FP64 path has it already).
+km_status refine_winners(km_ctx* ctx, const float* X, int64_t n, int d, const float* C, const km_params* p,
+                         const int32_t* labels, double* md, cudaStream_t st) {
+    if (p->low == KM_FP64_DIRECT) return KM_OK;
+    PhaseScope ps(ctx, KM_PHASE_REFINE, st);
+    KL(1, launch_winner_dist(X, n, d, C, labels, md, ctx->num_sms, st));
+    return KM_OK;
+}
+
+// The centre update's accumulation; md_wd (nullable) also receives the rows'
+// distances to their centres C_wd (the winner refinement, from the same pass
+// over X where the kernel allows).
+km_status accumulate(km_ctx* ctx, const float* X, int64_t n, int d, const int32_t* labels, int k, const UpdateWs& u,
+                     const float* C_wd, double* md_wd, cudaStream_t st) {
+    int nl = 0;
+    CK(launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st, C_wd,
+                         md_wd, &nl));
+    ctx->launches += (uint64_t)nl;
     return KM_OK;
 }
 
@@ -433,6 +466,21 @@ km_status km_workspace_size(const km_ctx* cctx, int64_t n, int d, int k, const k
     return KM_OK;
 }
 
+km_status km_quantize(km_ctx* ctx, const float* X, int64_t n, int d, int32_t low, void* Xq, float* stats,
+                      float* scale, void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!X || !Xq || !stats || !scale) return fail(ctx, KM_EINVAL, "null argument");
+    if (n < 1 || d < 1) return fail(ctx, KM_EINVAL, "need n, d >= 1 (n=%lld d=%d)", (long long)n, d);
+    if (n > (int64_t)INT32_MAX) return fail(ctx, KM_EINVAL, "n too large");
+    if (!is_tc(low)) return fail(ctx, KM_EUNSUPPORTED, "km_quantize needs a low format (FP16/BF16/E4M3)");
+    if (((uintptr_t)stats & 15) != 0) return fail(ctx, KM_EINVAL, "stats must be 16-byte aligned");
+    const int fmt = fmt_of(low);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    KL(1, launch_quantize(X, n, d, fmt, ldq_of(fmt, d), Xq, reinterpret_cast<float4*>(stats), scale, st));
+    return KM_OK;
+}
+
 km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
                     int32_t* labels, double* min_dist, uint64_t* n_flagged_host, void* ws, size_t ws_bytes,
                     void* stream) {
@@ -459,6 +507,7 @@ km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int 
     CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
     s = run_assign(ctx, X, n, C, k, d, p, labels, md, w, false, st);
     if (s != KM_OK) return s;
+    if ((s = refine_winners(ctx, X, n, d, C, p, labels, md, st)) != KM_OK) return s;
     KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
     ctx->last_cnt = w.cnt;
     ctx->last_sse = w.sse;
@@ -493,24 +542,17 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
     const int fmt = fmt_of(p->low);
     const int ldq = ldq_of(fmt, d);
     const int esz = fmt == 2 ? 1 : 2;
-    KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, 0, nullptr, st));
-    if (fmt == 2) {
-        KL(1, launch_uniform_scale(C, (int64_t)k * d, w.cscale_u, st));
-        KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 1, w.cscale_u, st));
-        KL(1, launch_colmax(w.cstat, k, w.cscale_u, w.colmax, w.qpad, kpad_of(k), st));
-    } else {
-        KL(1, launch_quantize(C, k, d, fmt, ldq, w.Cq, w.cstat, w.cscale, 0, nullptr, st));
-        KL(1, launch_colmax(w.cstat, k, nullptr, w.colmax, w.qpad, kpad_of(k), st));
-    }
+    KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, st));
+    if ((s = prepare_centres(ctx, C, k, d, fmt, w, st)) != KM_OK) return s;
     TcArgs a{};
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
     a.kchunks = (ldq * esz + 127) / 128;
-    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.colmax = w.colmax;
+    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.spad = w.spad; a.colmax = w.colmax;
     a.tp = make_tp(p, d); a.mode = 1; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
-    a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = n * (int64_t)k;
+    a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = w.qcap;
     a.flag_queue_len = w.qlen;
     KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
-    KL(1, launch_patch_flagged(X, C, k, d, w.queue, w.qlen, n * (int64_t)k, D, w.cnt, ctx->num_sms, st));
+    KL(1, launch_patch_flagged(X, C, n, k, d, w.queue, w.qlen, w.qcap, D, w.cnt, ctx->num_sms, st));
     ctx->last_cnt = w.cnt;
     ctx->last_sse = nullptr;
     ctx->last_stream = st;
@@ -545,7 +587,7 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     {
         PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
         KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
-        KL(4, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
+        if ((s = accumulate(ctx, X, n, d, labels, k, u, nullptr, nullptr, st)) != KM_OK) return s;
         KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts,
                               u.shift, u.taken, st));
     }
@@ -577,11 +619,13 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
     CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
     s = run_assign(ctx, X, n, C_old, k, d, p, labels, md, w, false, st, u.absmax);
     if (s != KM_OK) return s;
-    KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
-    // centre update (Eq. (center)) on the labels just computed
+    // centre update (Eq. (center)) on the labels just computed; its pass over
+    // X also refines the winners' distances (min_dist, binary64 accuracy)
     {
         PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-        KL(4, launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
+        s = accumulate(ctx, X, n, d, labels, k, u, C_old, p->low == KM_FP64_DIRECT ? nullptr : md, st);
+        if (s != KM_OK) return s;
+        KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
         KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts, u.shift,
                               u.taken, st));
     }
@@ -636,51 +680,61 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ctx->host_ev.push_back(e);
     }
-    cudaEvent_t ev_start = ctx->host_ev[0];
-    cudaEvent_t* ev_in = ctx->host_ev.data() + 1;
-    cudaEvent_t* ev_out = ev_in + kHostChunks;
-    cudaEvent_t* ev_back = ev_out + kHostChunks;
-    // the copies into the workspace wait for earlier work on the stream
-    CK(cudaEventRecord(ev_start, st));
-    CK(cudaMemcpyAsync(h.C, C_host, sizeof(float) * (size_t)k * d, cudaMemcpyHostToDevice, st));
-    for (int c = 0; c < nch; c++) {
-        const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
-        cudaStream_t cs = ctx->copy_st[c & 1];
-        CK(cudaStreamWaitEvent(cs, ev_start, 0));
-        CK(cudaMemcpyAsync(h.X + r0 * d, X_host + r0 * d, sizeof(float) * (size_t)rows * d, cudaMemcpyHostToDevice, cs));
-        CK(cudaEventRecord(ev_in[c], cs));
-    }
-    CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
-    CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
-    for (int c = 0; c < nch; c++) {
-        const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
-        cudaStream_t cs = ctx->copy_st[c & 1];
-        CK(cudaStreamWaitEvent(st, ev_in[c], 0));
-        CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
-        s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
-        if (s != KM_OK) {
-            // no copy may still be reading the caller's buffers after the return
-            for (cudaStream_t c2 : ctx->copy_st) cudaStreamSynchronize(c2);
-            return s;
+    // everything from the first copy on: any error exit drains the copy
+    // streams first, so no copy still reads the caller's buffers after the return
+    auto enqueue = [&]() -> km_status {
+        km_status s = KM_OK;
+        cudaEvent_t ev_start = ctx->host_ev[0];
+        cudaEvent_t* ev_in = ctx->host_ev.data() + 1;
+        cudaEvent_t* ev_out = ev_in + kHostChunks;
+        cudaEvent_t* ev_back = ev_out + kHostChunks;
+        // the copies into the workspace wait for earlier work on the stream
+        CK(cudaEventRecord(ev_start, st));
+        CK(cudaMemcpyAsync(h.C, C_host, sizeof(float) * (size_t)k * d, cudaMemcpyHostToDevice, st));
+        for (int c = 0; c < nch; c++) {
+            const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
+            cudaStream_t cs = ctx->copy_st[c & 1];
+            CK(cudaStreamWaitEvent(cs, ev_start, 0));
+            CK(cudaMemcpyAsync(h.X + r0 * d, X_host + r0 * d, sizeof(float) * (size_t)rows * d, cudaMemcpyHostToDevice, cs));
+            CK(cudaEventRecord(ev_in[c], cs));
         }
-        // this chunk's labels and distances go back while the next chunk is assigned
-        CK(cudaEventRecord(ev_out[c], st));
-        CK(cudaStreamWaitEvent(cs, ev_out[c], 0));
-        CK(cudaMemcpyAsync(labels_host + r0, h.labels + r0, sizeof(int32_t) * (size_t)rows, cudaMemcpyDeviceToHost, cs));
+        CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
+        CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
+        for (int c = 0; c < nch; c++) {
+            const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
+            cudaStream_t cs = ctx->copy_st[c & 1];
+            CK(cudaStreamWaitEvent(st, ev_in[c], 0));
+            CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
+            s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
+            if (s != KM_OK) return s;
+            // this chunk's labels go back while the next chunk is assigned
+            CK(cudaEventRecord(ev_out[c], st));
+            CK(cudaStreamWaitEvent(cs, ev_out[c], 0));
+            CK(cudaMemcpyAsync(labels_host + r0, h.labels + r0, sizeof(int32_t) * (size_t)rows, cudaMemcpyDeviceToHost, cs));
+            CK(cudaEventRecord(ev_back[c], cs));
+        }
+        {
+            // the update's pass over X also refines the winners' distances
+            PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
+            s = accumulate(ctx, h.X, n, d, h.labels, k, u, h.C, p->low == KM_FP64_DIRECT ? nullptr : h.min_dist, st);
+            if (s != KM_OK) return s;
+            KL(2, launch_sum_f64(h.min_dist, n, w.partials, kSumParts, w.sse, st));
+            KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, h.C, p->empty, h.X, h.min_dist, h.C_new, h.counts,
+                                  u.shift, u.taken, st));
+        }
         if (min_dist_host)
-            CK(cudaMemcpyAsync(min_dist_host + r0, h.min_dist + r0, sizeof(double) * (size_t)rows, cudaMemcpyDeviceToHost, cs));
-        CK(cudaEventRecord(ev_back[c], cs));
+            CK(cudaMemcpyAsync(min_dist_host, h.min_dist, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(C_new_host, h.C_new, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToHost, st));
+        if (counts_host) CK(cudaMemcpyAsync(counts_host, h.counts, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, st));
+        for (int c = 0; c < nch; c++) CK(cudaStreamWaitEvent(st, ev_back[c], 0));
+        return KM_OK;
+    };
+    s = enqueue();
+    if (s != KM_OK) {
+        for (cudaStream_t c2 : ctx->copy_st) cudaStreamSynchronize(c2);
+        cudaStreamSynchronize(st);  // and no copy back into them either
+        return s;
     }
-    KL(2, launch_sum_f64(h.min_dist, n, w.partials, kSumParts, w.sse, st));
-    {
-        PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-        KL(4, launch_accumulate(h.X, n, d, h.labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st));
-        KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, h.C, p->empty, h.X, h.min_dist, h.C_new, h.counts,
-                              u.shift, u.taken, st));
-    }
-    CK(cudaMemcpyAsync(C_new_host, h.C_new, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToHost, st));
-    if (counts_host) CK(cudaMemcpyAsync(counts_host, h.counts, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, st));
-    for (int c = 0; c < nch; c++) CK(cudaStreamWaitEvent(st, ev_back[c], 0));
     ctx->last_cnt = w.cnt;
     ctx->last_sse = w.sse;
     ctx->last_stream = st;
@@ -727,7 +781,7 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
         const int fmt = fmt_of(p->low);
         PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
         CK(cudaMemsetAsync(L.u.absmax, 0, sizeof(unsigned), st));
-        KL(1, launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, 0, nullptr, st, L.u.absmax));
+        KL(1, launch_quantize(X, n, d, fmt, ldq_of(fmt, d), L.a.Xq, L.a.xstat, L.a.xscale, st, L.u.absmax));
     } else {
         KL(1, launch_absmax(X, n * (int64_t)d, L.u.absmax, st));
     }
@@ -738,12 +792,12 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
         CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
         s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
         if (s != KM_OK) return s;
-        KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
         CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
         {
             PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-            KL(4, launch_accumulate(X, n, d, labels, k, L.u.absmax, L.u.sums, L.u.counts, L.u.iscratch, L.u.perm,
-                                     ctx->num_sms, st));
+            s = accumulate(ctx, X, n, d, labels, k, L.u, cur, p->low == KM_FP64_DIRECT ? nullptr : L.min_dist, st);
+            if (s != KM_OK) return s;
+            KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
             KL(3, launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt,
                                   L.counts, L.u.shift, L.u.taken, st));
         }
@@ -762,6 +816,7 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
     s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
     if (s != KM_OK) return s;
+    if ((s = refine_winners(ctx, X, n, d, cur, p, labels, L.min_dist, st)) != KM_OK) return s;
     KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
     CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
     KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.a.sse, st));
@@ -1000,5 +1055,7 @@ extern "C" km_status km_assign_static(km_ctx* ctx, const float* X, int64_t n, co
                                ctx->num_sms, st));
     KL(1, launch_rows_full(false, X, C, k, d, amb_list, &cnt->amb_count, labels, min_dist, cnt, tp.gamma32,
                            ctx->num_sms, st));
+    // the winners' distances to binary64 accuracy, as km_assign (no scratch)
+    KL(1, launch_winner_dist(X, n, d, C, labels, min_dist, ctx->num_sms, st));
     return KM_OK;
 }

@@ -37,8 +37,7 @@ struct ColMax {
     float ncq;   // max ||c~_j||
     float q;     // max ||c_j||^2
     float ncq2;  // max ||c~_j||^2
-    float cscale;  // uniform power-of-two scale of the quantised centres (E4M3), 1 otherwise
-    float pad[2];
+    float pad[3];
     // minima of the same statistics: a lower bound of every pair's threshold
     float nc_min, nrc_min, ncq_min, q_min, ncq2_min;
     float pad2[3];
@@ -73,19 +72,15 @@ inline cudaError_t allow_max_smem(F* func) {
 // ---- kernels (launch wrappers; all asynchronous on `st`) -----------------
 // quantise rows of A (m x d fp32) to fmt (0 fp16, 1 bf16, 2 e4m3) with row
 // stride ldq elements; stat[i] = (||a||^2 fp32, ||a||, ||a~||, ||a~ - a||);
-// rscale[i] = per-row scale (e4m3, scale_mode 0) or the uniform scale read
-// from *uscale (scale_mode 1); fp16/bf16 write 1.
+// rscale[i] = the row's power-of-two scale (e4m3; fp16/bf16 write 1).
 // absmax_out (nullable): max |a| over A folded in with atomicMax on its bits
 // (the caller zeroes it first).
 cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
-                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st,
-                            unsigned* absmax_out = nullptr);
-// amax over all of C (for the uniform E4M3 centre scale): writes the scale.
-cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out, cudaStream_t st);
-// column maxima of the centre statistics
-// and q_j padded with +inf to kpad entries
-cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, int kpad,
-                          cudaStream_t st);
+                            float* rscale, cudaStream_t st, unsigned* absmax_out = nullptr);
+// column maxima of the centre statistics, q_j padded with +inf to kpad
+// entries and the centres' scales (cscale, nullable: all 1) padded with 1
+cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, float* spad,
+                          int kpad, cudaStream_t st);
 
 // direct-formula assignment (thread per row).  acc64: binary64 accumulation
 // (the plain FP64 path) else fp32 with certification; rows = all n, or the
@@ -111,6 +106,7 @@ struct TcArgs {
     const float* xscale;
     const float4* cstat;
     const float* qpad;        // q_j = ||c_j||^2 for j < k, +inf up to the padded tile width
+    const float* spad;        // the centres' E4M3 scales s_j for j < k, 1 up to the padded tile width
     const ColMax* colmax;
     TestParams tp;
     int mode;
@@ -123,7 +119,7 @@ struct TcArgs {
     int2* rowpair;            // n: (offset, count) of the row's pairs, count -1: whole-row recompute
     float* D;                 // mode 1: n x k
     uint32_t* flag_bits;      // mode 1 (nullable)
-    int2* flag_queue;         // mode 1: flagged pairs for the fp64 patch
+    int2* flag_queue;         // mode 1: flagged pairs for the fp64 patch (bounded; D holds -1 marks)
     int64_t flag_queue_cap;
     unsigned long long* flag_queue_len;
     DevCounters* cnt;
@@ -138,17 +134,26 @@ size_t tc_smem_bytes(int fmt, int d, int k);
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels,
                           double* min_dist, int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st,
                           int* nlaunch);
-// fp64 direct values for flagged pairs of the distance matrix
-cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, const int2* queue,
+// fp64 direct values for the flagged pairs of the distance matrix (marked -1
+// in D): from the queue, or by a scan of D when the queue overflowed
+cudaError_t launch_patch_flagged(const float* X, const float* C, int64_t n, int k, int d, const int2* queue,
                                  const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt,
                                  int num_sms, cudaStream_t st);
 
 // centre update
 cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cudaStream_t st);
-// per-cluster exact sums: iscratch holds 4k + 2 ints, perm n ints
+// per-cluster exact sums: iscratch holds 4k + 2 ints, perm n ints.
+// md_out (nullable): each row's ||x_i - C_wd[labels[i]]||^2 to binary64
+// accuracy (the winner distances of launch_winner_dist, bit for bit), fused
+// into the pass over X where the kernel allows.  *nlaunch: kernels launched.
 cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
                               const unsigned* absmax_bits, long long* sums, long long* counts, int* iscratch,
-                              int32_t* perm, int num_sms, cudaStream_t st);
+                              int32_t* perm, int num_sms, cudaStream_t st, const float* C_wd, double* md_out,
+                              int* nlaunch);
+// md[i] = ||x_i - C[labels[i]]||^2, Eq. (dist-direct), to binary64 accuracy
+// on the fp32 pipe (double-float arithmetic of df.cuh)
+cudaError_t launch_winner_dist(const float* X, int64_t n, int d, const float* C, const int32_t* labels, double* md,
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
                             int64_t n, int k, int d, const float* C_old, int empty_policy,
                             const float* X, const double* min_dist, float* C_new, int64_t* counts_out,

@@ -30,17 +30,19 @@ KM_DEV float quant_val(float v, int fmt) {
     return __half2float(__half(hr));
 }
 
-// Smallest power of two s with amax / s <= 448 (E4M3's largest finite value).
+// Row scale of E4M3 (the per-row power-of-two scaling read into Section 4.3's
+// quantisation): the smallest power of two s with amax / s <= 448 (E4M3's
+// largest finite value), so the row maximum lands in (224, 448]; s is kept a
+// normal fp32 number (s >= 2^-126, so 1/s is finite and x / s exact), and an
+// all-zero row takes s = 1.  Exact for every fp32 amax, subnormals included:
+// amax = f 2^e with f in [0.5, 1) (frexpf is exact), and 448 = 0.875 2^9, so
+// s = 2^(e - 9) when f <= 0.875, else 2^(e - 8).
 KM_DEV float e4m3_row_scale(float amax) {
     if (!(amax > 0.0f)) return 1.0f;
-    float t = amax / 448.0f;  // exact up to rounding; the power-of-two choice below is conservative
     int e;
-    float f = frexpf(t, &e);  // t = f 2^e, f in [0.5, 1)
-    float s = ldexpf(1.0f, e);
-    if (f == 0.5f) s = ldexpf(1.0f, e - 1);
-    // guarantee amax / s <= 448 despite the rounding of t
-    while (amax / s > 448.0f) s *= 2.0f;
-    return s;
+    const float f = frexpf(amax, &e);
+    const int k = max(f <= 0.875f ? e - 9 : e - 8, -126);
+    return __int_as_float((k + 127) << 23);
 }
 
 // Largest |a| seen by the block's threads, folded into *out with one atomic
@@ -60,8 +62,7 @@ KM_DEV void block_absmax(float v, unsigned* out) {
 }
 
 __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
-                           float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
-                           const float* __restrict__ uscale, unsigned* __restrict__ absmax_out) {
+                           float4* __restrict__ stat, float* __restrict__ rscale, unsigned* __restrict__ absmax_out) {
     float amx = 0.0f;  // largest |a| of this thread's elements (absmax_out)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -70,15 +71,11 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
         const float* a = A + i * d;
         float s = 1.0f;
         if (fmt == 2) {
-            if (scale_mode == 1) {
-                s = *uscale;
-            } else {
-                float amax = 0.0f;
-                for (int l = lane; l < d; l += 32) amax = fmaxf(amax, fabsf(a[l]));
+            float amax = 0.0f;
+            for (int l = lane; l < d; l += 32) amax = fmaxf(amax, fabsf(a[l]));
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-                s = e4m3_row_scale(amax);
-            }
+            for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+            s = e4m3_row_scale(amax);
         }
         const float inv = 1.0f / s;  // exact: s is a power of two
         float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
@@ -150,8 +147,7 @@ KM_DEV void row_sums2(float2 x, float2 q, float2& hi, float2& lo, float2& qq, fl
 
 template <int NV>
 __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
-                              float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
-                              const float* __restrict__ uscale, unsigned* __restrict__ absmax_out) {
+                              float4* __restrict__ stat, float* __restrict__ rscale, unsigned* __restrict__ absmax_out) {
     float amx = 0.0f;  // largest |a| of this thread's elements (absmax_out)
     const int lane = threadIdx.x & 31, sl = lane & 7;
     const unsigned gmask = 0xFFu << (lane & ~7);
@@ -185,17 +181,13 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
         }
         float s = 1.0f;
         if (fmt == 2) {
-            if (scale_mode == 1) {
-                s = *uscale;
-            } else {
-                float amax = 0.0f;
+            float amax = 0.0f;
 #pragma unroll
-                for (int u = 0; u < NV; u++)
-                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
+            for (int u = 0; u < NV; u++)
+                amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
 #pragma unroll
-                for (int off = 4; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(gmask, amax, off));
-                s = e4m3_row_scale(amax);
-            }
+            for (int off = 4; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(gmask, amax, off));
+            s = e4m3_row_scale(amax);
         }
         const float inv = 1.0f / s;
         float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
@@ -297,8 +289,7 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
 // four float4 of the row in registers (coalesced 16-byte loads).
 template <int NV>
 __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, int fmt, int ldq, void* Aq,
-                               float4* __restrict__ stat, float* __restrict__ rscale, int scale_mode,
-                               const float* __restrict__ uscale, unsigned* __restrict__ absmax_out) {
+                               float4* __restrict__ stat, float* __restrict__ rscale, unsigned* __restrict__ absmax_out) {
     float amx = 0.0f;  // largest |a| of this thread's elements (absmax_out)
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -315,17 +306,13 @@ __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, in
         }
         float s = 1.0f;
         if (fmt == 2) {
-            if (scale_mode == 1) {
-                s = *uscale;
-            } else {
-                float amax = 0.0f;
+            float amax = 0.0f;
 #pragma unroll
-                for (int u = 0; u < NV; u++)
-                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
+            for (int u = 0; u < NV; u++)
+                amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-                s = e4m3_row_scale(amax);
-            }
+            for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+            s = e4m3_row_scale(amax);
         }
         const float inv = 1.0f / s;
         float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
@@ -387,26 +374,14 @@ __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, in
     if (absmax_out) block_absmax(amx, absmax_out);
 }
 
-__global__ void k_amax_scale(const float* __restrict__ C, int64_t count, float* out) {
-    __shared__ float red[32];
-    float amax = 0.0f;
-    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) amax = fmaxf(amax, fabsf(C[e]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        amax = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-        if (threadIdx.x == 0) *out = e4m3_row_scale(amax);
-    }
-}
-
 __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* __restrict__ cscale, ColMax* out,
-                         float* __restrict__ qpad, int kpad) {
-    // q_j for the screening kernel, +inf on the padding so padded columns never win
-    for (int j = threadIdx.x; j < kpad; j += blockDim.x) qpad[j] = (j < k) ? cstat[j].x : INFINITY;
+                         float* __restrict__ qpad, float* __restrict__ spad, int kpad) {
+    // q_j for the screening kernel, +inf on the padding so padded columns never
+    // win; the centres' E4M3 scales (cscale, nullable: 1), 1 on the padding
+    for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
+        qpad[j] = (j < k) ? cstat[j].x : INFINITY;
+        spad[j] = (j < k && cscale) ? cscale[j] : 1.0f;
+    }
     __shared__ float red[10][32];
     float a = 0, b = 0, c = 0, q = 0, c2 = 0;
     float an = INFINITY, bn = INFINITY, cn = INFINITY, qn = INFINITY, c2n = INFINITY;
@@ -451,8 +426,7 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
         }
         ColMax o;
         o.nc = a; o.nrc = b; o.ncq = c; o.q = q; o.ncq2 = c2;
-        o.cscale = cscale ? *cscale : 1.0f;
-        o.pad[0] = o.pad[1] = 0.0f;
+        o.pad[0] = o.pad[1] = o.pad[2] = 0.0f;
         o.nc_min = an; o.nrc_min = bn; o.ncq_min = cn; o.q_min = qn; o.ncq2_min = c2n;
         o.pad2[0] = o.pad2[1] = o.pad2[2] = 0.0f;
         *out = o;
@@ -460,8 +434,7 @@ __global__ void k_colmax(const float4* __restrict__ cstat, int k, const float* _
 }
 
 cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, void* Aq, float4* stat,
-                            float* rscale, int scale_mode, const float* uscale, cudaStream_t st,
-                            unsigned* absmax_out) {
+                            float* rscale, cudaStream_t st, unsigned* absmax_out) {
     // one warp per row, enough warps in flight to cover the memory latency
     int64_t blocks = (m * 32 + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
@@ -472,34 +445,29 @@ cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, 
     if (vec && nv8 <= 8) {
         blocks = std::min<int64_t>(std::max<int64_t>(1, (m * 8 + 255) / 256), (int64_t)152 * 16);
         if (nv8 <= 1)
-            k_quantize_g8<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_g8<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
         else if (nv8 <= 2)
-            k_quantize_g8<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_g8<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
         else if (nv8 <= 4)
-            k_quantize_g8<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_g8<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
         else
-            k_quantize_g8<8><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_g8<8><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
     } else if (vec && nv <= 4) {
         if (nv == 1)
-            k_quantize_vec<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_vec<1><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
         else if (nv == 2)
-            k_quantize_vec<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_vec<2><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
         else
-            k_quantize_vec<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+            k_quantize_vec<4><<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
     } else {
-        k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, scale_mode, uscale, absmax_out);
+        k_quantize<<<(unsigned)blocks, 256, 0, st>>>(A, m, d, fmt, ldq, Aq, stat, rscale, absmax_out);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_uniform_scale(const float* C, int64_t count, float* scale_out, cudaStream_t st) {
-    k_amax_scale<<<1, 1024, 0, st>>>(C, count, scale_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, int kpad,
-                          cudaStream_t st) {
-    k_colmax<<<1, 1024, 0, st>>>(cstat, k, cscale, out, qpad, kpad);
+cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, float* spad,
+                          int kpad, cudaStream_t st) {
+    k_colmax<<<1, 1024, 0, st>>>(cstat, k, cscale, out, qpad, spad, kpad);
     return cudaGetLastError();
 }
 

@@ -312,21 +312,36 @@ __global__ void __launch_bounds__(256) k_amb_fp64(const int32_t* __restrict__ am
     if (lane == 0 && ev64) atomicAdd(&cnt->fp64_evals, ev64);
 }
 
+// Flagged pairs of the distance matrix (marked -1 by the screening kernel):
+// their binary64 direct values, from the bounded queue the screening kernel
+// filled, or, when more pairs were flagged than it holds, by a scan of D for
+// the marks.
 __global__ void k_patch_flagged(const float* __restrict__ X, const float* __restrict__ C, int k, int d,
                                 const int2* __restrict__ queue, const unsigned long long* __restrict__ qlen,
-                                int64_t cap, float* __restrict__ D, DevCounters* cnt) {
-    const int64_t len = min((int64_t)*qlen, cap);
+                                int64_t cap, float* __restrict__ D, int64_t n, DevCounters* cnt) {
+    const int64_t len = (int64_t)*qlen;
+    const bool scan = len > cap;
+    const int64_t total = scan ? n * (int64_t)k : len;
     unsigned long long ev = 0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x) {
-        const int2 pr = queue[t];
-        const float* x = X + (int64_t)pr.x * d;
-        const float* c = C + (int64_t)pr.y * d;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row, j;
+        if (scan) {
+            if (!(D[t] < 0.0f)) continue;
+            row = t / k;
+            j = t - row * k;
+        } else {
+            const int2 pr = queue[t];
+            row = pr.x;
+            j = pr.y;
+        }
+        const float* x = X + row * d;
+        const float* c = C + j * d;
         double s = 0.0;
         for (int l = 0; l < d; l++) {
             const double u = __dsub_rn((double)x[l], (double)c[l]);
             s = __dadd_rn(s, __dmul_rn(u, u));
         }
-        D[(int64_t)pr.x * k + pr.y] = (float)s;
+        D[row * k + j] = (float)s;
         ev++;
     }
 #pragma unroll
@@ -377,10 +392,10 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_patch_flagged(const float* X, const float* C, int k, int d, const int2* queue,
+cudaError_t launch_patch_flagged(const float* X, const float* C, int64_t n, int k, int d, const int2* queue,
                                  const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt, int num_sms,
                                  cudaStream_t st) {
-    k_patch_flagged<<<num_sms * 8, 256, 0, st>>>(X, C, k, d, queue, qlen, cap, D, cnt);
+    k_patch_flagged<<<num_sms * 8, 256, 0, st>>>(X, C, k, d, queue, qlen, cap, D, n, cnt);
     return cudaGetLastError();
 }
 

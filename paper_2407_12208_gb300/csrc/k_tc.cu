@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (FMT == 2) rs = a.xscale[row];
             }
             const float p = xs.x;
-            const float neg2s = -2.0f * rs * cm.cscale;
+            // e = q_j - 2 s_i s_j g (E4M3: row and column scales, powers of two)
+            const float neg2s = -2.0f * rs;
             // bound B_ij = (a1 ||c_j|| + a2 ||c~_j - c_j|| + a3 ||c~_j|| + kn (p + q_j)) * bsafe
             const float a1 = 2.0f * xs.w, a2 = 2.0f * xs.z, a3 = tp.kacc * xs.z;
             const float bmax = (a1 * cm.nc + a2 * cm.nrc + a3 * cm.ncq + tp.kn * (p + cm.q)) * tp.bsafe;
@@ -357,6 +358,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         float4 qv[NQ];
 #pragma unroll
                         for (int t4 = 0; t4 < NQ; t4++) qv[t4] = __ldg(q4 + t4);
+                        float4 sv[FMT == 2 ? NQ : 1];
+                        if constexpr (FMT == 2) {
+                            const float4* s4 = reinterpret_cast<const float4*>(a.spad + col0);
+#pragma unroll
+                            for (int t4 = 0; t4 < NQ; t4++) sv[t4] = __ldg(s4 + t4);
+                        }
                         // the other groups' running minima of this row block (read before the wait)
                         float mo = INFINITY;
 #pragma unroll
@@ -374,10 +381,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const uint32_t* vv = v[t4 / 8];
                             const int o = (t4 & 7) * 4;
                             const float4 qq = qv[t4];
-                            const float2 lo = __ffma2_rn(make_float2(__uint_as_float(vv[o + 0]), __uint_as_float(vv[o + 1])), n2,
-                                                         make_float2(qq.x, qq.y));
-                            const float2 hi = __ffma2_rn(make_float2(__uint_as_float(vv[o + 2]), __uint_as_float(vv[o + 3])), n2,
-                                                         make_float2(qq.z, qq.w));
+                            float2 g01 = make_float2(__uint_as_float(vv[o + 0]), __uint_as_float(vv[o + 1]));
+                            float2 g23 = make_float2(__uint_as_float(vv[o + 2]), __uint_as_float(vv[o + 3]));
+                            if constexpr (FMT == 2) {  // s_j g: exact (power-of-two scale)
+                                g01 = __fmul2_rn(g01, make_float2(sv[t4].x, sv[t4].y));
+                                g23 = __fmul2_rn(g23, make_float2(sv[t4].z, sv[t4].w));
+                            }
+                            const float2 lo = __ffma2_rn(g01, n2, make_float2(qq.x, qq.y));
+                            const float2 hi = __ffma2_rn(g23, n2, make_float2(qq.z, qq.w));
                             e[4 * t4 + 0] = lo.x;
                             e[4 * t4 + 1] = lo.y;
                             e[4 * t4 + 2] = hi.x;
@@ -552,14 +563,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tmem_wait_ld(v);
                         if (!valid) continue;
                         const float4* q4 = reinterpret_cast<const float4*>(qg + col0);
+                        const float4* s4 = reinterpret_cast<const float4*>(a.spad + col0);
                         float e[32];
 #pragma unroll
                         for (int t4 = 0; t4 < 8; t4++) {
                             const float4 qq = __ldg(q4 + t4);
-                            e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]), neg2s, qq.x);
-                            e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]), neg2s, qq.y);
-                            e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]), neg2s, qq.z);
-                            e[4 * t4 + 3] = fmaf(__uint_as_float(v[4 * t4 + 3]), neg2s, qq.w);
+                            const float4 sc = FMT == 2 ? __ldg(s4 + t4) : make_float4(1.f, 1.f, 1.f, 1.f);
+                            e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]) * sc.x, neg2s, qq.x);
+                            e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]) * sc.y, neg2s, qq.y);
+                            e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]) * sc.z, neg2s, qq.z);
+                            e[4 * t4 + 3] = fmaf(__uint_as_float(v[4 * t4 + 3]) * sc.w, neg2s, qq.w);
                         }
                         // distance-matrix mode: Alg. 2's d = max(d^, 0) and its flag, every pair
                         float* drow = a.D + (size_t)row * a.k;
@@ -569,7 +582,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             if (j < a.k) {
                                 const float dh = fmaxf(p + e[t], 0.0f);
                                 const bool fl = (dh <= F) && KM_PAIR_FLAGGED(j, dh);
-                                drow[j] = dh;
+                                // a flagged pair is marked -1 until its direct value replaces it
+                                drow[j] = fl ? -1.0f : dh;
                                 if (fl) {
                                     nflag++;
                                     const unsigned long long pos = atomicAdd(a.flag_queue_len, 1ull);

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "internal.h"
 
 namespace km {
@@ -234,11 +235,17 @@ KM_DEV int bucket_of(const int* __restrict__ item_off, int k, int64_t it) {
 // row is spread over LPR lanes (NV4 float4 each, d % 4 == 0), so a warp reads
 // 32 / LPR rows per load; exact sums in registers, folded across the row
 // groups of the warp at the end, one atomic add per coordinate per item.
-template <int NV4, int LPR>
+//
+// WD: the same pass also gives each row's distance to its own centre c_j (the
+// winner's ||x - c||^2, Eq. (dist-direct)) to binary64 accuracy (df.cuh: the
+// rows' chunk partials reduced over the row's lanes, eight rows at a time), so
+// the assignment's min_dist costs no second read of X.
+template <int NV4, int LPR, bool WD>
 __global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ? 1 : 2)) k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, int seg,
                                                        const int* __restrict__ off,
                              const int* __restrict__ item_off, const int32_t* __restrict__ perm,
-                             const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
+                             const unsigned* __restrict__ amax_bits, long long* __restrict__ sums,
+                             const float* __restrict__ C, double* __restrict__ md) {
     static_assert(LPR == 32 || NV4 == 1, "rows narrower than a warp take one float4 per lane");
     constexpr int G = 32 / LPR;                            // rows per warp load
     // loads in flight per lane: 8 at full-warp rows of one float4 (three blocks
@@ -255,6 +262,16 @@ __global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ?
         const int j = bucket_of(item_off, k, it);
         const int c = (int)(it - item_off[j]);
         const int r0 = off[j] + c * seg, r1 = min(off[j + 1], r0 + seg);
+        // the bucket's centre: this lane's chunks of c_j (WD)
+        float4 cj[NV4];
+        if (WD) {
+#pragma unroll
+            for (int u = 0; u < NV4; u++) {
+                const int cidx = cl + LPR * u;
+                cj[u] = (cidx < d4) ? reinterpret_cast<const float4*>(C + (int64_t)j * d)[cidx]
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
         // biased parts of the fixed-point values, summed modulo 2^32 (SEG_MAX rows at most)
         unsigned a2[NV4][4], a1[NV4][4], a0[NV4][4];
 #pragma unroll
@@ -302,6 +319,20 @@ __global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ?
                         a1[u][2] += q1.x; a1[u][3] += q1.y;
                         a0[u][2] += q0.x; a0[u][3] += q0.y;
                     }
+                if (WD) {
+                    // the rows' distances to c_j, RW rows per multi-row butterfly
+                    constexpr int RW = RB < 8 ? RB : 8;
+#pragma unroll
+                    for (int bb = 0; bb < RB; bb += RW) {
+                        DF part[RW];
+#pragma unroll
+                        for (int b = 0; b < RW; b++) part[b] = df_lane<NV4>(v[bb + b], cj);
+                        int rs;
+                        const DF r = df_rows<RW, LPR>(part, cl, rs);
+                        const int64_t i = __shfl_sync(0xffffffffu, my_i, b0 + (bb + rs) * G + sub);
+                        if ((cl & (LPR / RW - 1)) == 0 && i >= 0) md[i] = df_value(r);
+                    }
+                }
             }
         }
         // the row groups' sums of the same coordinates (modulo 2^32 like the sums)
@@ -373,19 +404,27 @@ __global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k
 // lane, which adds it with a shared atomic.  Every AS_CHUNK rows the
 // accumulators are folded into the global int64 sums.  Integer additions
 // throughout: the order does not matter.
+// WD: each row's distance to its own centre (binary64 accuracy, df.cuh) from
+// the same read of the row, with C staged in shared memory.
 constexpr int AS_CHUNK = 1024;   // rows per warp between folds (keeps each 32-bit part sum below 2^31)
 constexpr int AS_MAX_KD = 512;   // k * d bound of this path
-template <int D>
+template <int D, bool WD>
 __global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X, int64_t n, int k,
                                                      const int32_t* __restrict__ labels,
                                                      const unsigned* __restrict__ amax_bits,
-                                                     long long* __restrict__ sums, long long* __restrict__ counts) {
-    extern __shared__ unsigned acc_sm[];  // per warp: 3 * k * D parts, then k counts
+                                                     long long* __restrict__ sums, long long* __restrict__ counts,
+                                                     const float* __restrict__ C, double* __restrict__ md) {
+    extern __shared__ unsigned acc_sm[];  // per warp: 3 * k * D parts, then k counts; then C (WD)
     const FixedScale fx(fixed_shift(*amax_bits, n));
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int kd = k * D;
     unsigned* a = acc_sm + (size_t)wib * (3 * kd + k);
     unsigned* cntw = a + 3 * kd;
+    float* Cs = reinterpret_cast<float*>(acc_sm + (size_t)(blockDim.x >> 5) * (3 * kd + k));
+    if (WD) {
+        for (int e = threadIdx.x; e < kd; e += blockDim.x) Cs[e] = C[e];
+        __syncthreads();
+    }
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c0 = w0 * AS_CHUNK; c0 < n; c0 += nw * AS_CHUNK) {
@@ -396,11 +435,15 @@ __global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X
             const int64_t i = base + lane;
             const bool valid = i < c1;
             const int j = valid ? labels[i] : -1;
+            float xr[D];
+#pragma unroll
+            for (int l = 0; l < D; l++) xr[l] = valid ? X[i * D + l] : 0.0f;
+            if (WD && valid) md[i] = df_value(df_small<D>(xr, Cs + j * D));
             unsigned v[3 * D + 1];  // true (unbiased) parts modulo 2^32, then the row count
 #pragma unroll
             for (int l = 0; l < D; l++) {
                 unsigned b2 = FixedScale::kBias, b1 = FixedScale::kBias, b0 = FixedScale::kBias;
-                if (valid) fx.split(X[i * D + l], b2, b1, b0);
+                if (valid) fx.split(xr[l], b2, b1, b0);
                 v[3 * l + 0] = b2 - FixedScale::kBias;
                 v[3 * l + 1] = b1 - FixedScale::kBias;
                 v[3 * l + 2] = b0 - FixedScale::kBias;
@@ -438,6 +481,112 @@ __global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X
             if (cntw[jj]) atomicAdd(reinterpret_cast<unsigned long long*>(&counts[jj]), (unsigned long long)cntw[jj]);
         __syncwarp();
     }
+}
+
+// ---- the winner's distance on its own (rows in natural order) ------------
+// min_dist[i] = ||x_i - c_label(i)||^2 to binary64 accuracy, by the same
+// arithmetic as the fused centre-sum passes above (df.cuh), so an assignment
+// alone and an assignment followed by the centre update give the same bits.
+// R rows per lane and pass (R <= LPR), G = 32 / LPR rows per load.
+template <int NV4, int LPR, bool VEC>
+__global__ void __launch_bounds__(256) k_winner_dist(const float* __restrict__ X, int64_t n, int d,
+                                                     const float* __restrict__ C, const int32_t* __restrict__ labels,
+                                                     double* __restrict__ md) {
+    constexpr int G = 32 / LPR;
+    constexpr int R = NV4 == 1 ? 8 : (NV4 == 2 ? 4 : 2);
+    constexpr int STEP = R * G;
+    static_assert(R <= LPR, "rows per lane exceed the lanes of a row");
+    const int lane = threadIdx.x & 31, sub = lane / LPR, cl = lane % LPR;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int d4 = (d + 3) >> 2;
+    for (int64_t base = w0 * STEP; base < n; base += nw * STEP) {
+        const int jl = (lane < STEP && base + lane < n) ? labels[base + lane] : 0;
+        float4 xv[R][NV4], cv[R][NV4];
+#pragma unroll
+        for (int b = 0; b < R; b++) {
+            const int64_t row = base + b * G + sub;
+            const int j = __shfl_sync(0xffffffffu, jl, b * G + sub);
+#pragma unroll
+            for (int u = 0; u < NV4; u++) {
+                const int cidx = cl + LPR * u;
+                const bool ok = row < n && cidx < d4;
+                if (VEC) {
+                    xv[b][u] = ok ? reinterpret_cast<const float4*>(X + row * d)[cidx] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    cv[b][u] = ok ? reinterpret_cast<const float4*>(C + (int64_t)j * d)[cidx]
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    float xe[4], ce[4];
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const int l = 4 * cidx + t;
+                        xe[t] = (ok && l < d) ? X[row * d + l] : 0.0f;
+                        ce[t] = (ok && l < d) ? C[(int64_t)j * d + l] : 0.0f;
+                    }
+                    xv[b][u] = make_float4(xe[0], xe[1], xe[2], xe[3]);
+                    cv[b][u] = make_float4(ce[0], ce[1], ce[2], ce[3]);
+                }
+            }
+        }
+        DF part[R];
+#pragma unroll
+        for (int b = 0; b < R; b++) part[b] = df_lane<NV4>(xv[b], cv[b]);
+        int rs;
+        const DF r = df_rows<R, LPR>(part, cl, rs);
+        const int64_t row = base + rs * G + sub;
+        if ((cl & (LPR / R - 1)) == 0 && row < n) md[row] = df_value(r);
+    }
+}
+
+// Rows of D <= 8 coordinates: one thread per row.
+template <int D>
+__global__ void __launch_bounds__(256) k_winner_small(const float* __restrict__ X, int64_t n,
+                                                      const float* __restrict__ C, const int32_t* __restrict__ labels,
+                                                      double* __restrict__ md) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = labels[i];
+        float xr[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) xr[l] = X[i * D + l];
+        md[i] = df_value(df_small<D>(xr, C + (int64_t)j * D));
+    }
+}
+
+cudaError_t launch_winner_dist(const float* X, int64_t n, int d, const float* C, const int32_t* labels, double* md,
+                               int num_sms, cudaStream_t st) {
+    if (n < 1) return cudaSuccess;
+    if (d <= 8) {
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8));
+        switch (d) {
+#define KM_WS(DD) \
+    case DD: k_winner_small<DD><<<blocks, 256, 0, st>>>(X, n, C, labels, md); break;
+            KM_WS(1) KM_WS(2) KM_WS(3) KM_WS(4) KM_WS(5) KM_WS(6) KM_WS(7) KM_WS(8)
+#undef KM_WS
+        }
+        return cudaGetLastError();
+    }
+    const bool vec = d % 4 == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)C % 16) == 0;
+    const int lpr = df_lpr(d), nv4 = df_nv4(d);
+    const void* fn = nullptr;
+    void (*kern)(const float*, int64_t, int, const float*, const int32_t*, double*) = nullptr;
+#define KM_WD(NV, L)                                                          \
+    if (nv4 == NV && lpr == L) {                                              \
+        if (vec) kern = k_winner_dist<NV, L, true>;                           \
+        else kern = k_winner_dist<NV, L, false>;                              \
+    }
+    KM_WD(1, 8) KM_WD(1, 16) KM_WD(1, 32) KM_WD(2, 32) KM_WD(4, 32)
+#undef KM_WD
+    if (!kern) return cudaErrorInvalidValue;
+    fn = (const void*)kern;
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (e != cudaSuccess) return e;
+    const int rows_per_warp_pass = (nv4 == 1 ? 8 : (nv4 == 2 ? 4 : 2)) * (32 / lpr);
+    const int64_t warps_needed = (n + rows_per_warp_pass - 1) / rows_per_warp_pass;
+    const unsigned blocks = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((warps_needed + 7) / 8, (int64_t)num_sms * std::max(per_sm, 1)));
+    kern<<<blocks, 256, 0, st>>>(X, n, d, C, labels, md);
+    return cudaGetLastError();
 }
 
 // mean = sum 2^-S / m in binary64, stored in fp32 (the working precision).
@@ -571,30 +720,54 @@ cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cud
 
 cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
                               const unsigned* absmax_bits, long long* sums, long long* counts, int* iscratch,
-                              int32_t* perm, int num_sms, cudaStream_t st) {
+                              int32_t* perm, int num_sms, cudaStream_t st, const float* C_wd, double* md_out,
+                              int* nlaunch) {
+    // md_out: the rows' distances to their centres (C_wd) come out of the same
+    // pass over X where the kernel has the row and its centre in hand, else
+    // from the standalone kernel first (the same arithmetic either way)
+    const bool want_wd = md_out != nullptr && C_wd != nullptr;
+    int nl = 0;
     cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(long long) * (size_t)k * d, st);
     if (e != cudaSuccess) return e;
     if (d <= 8 && (int64_t)k * d <= AS_MAX_KD) {
-        // small d: rows in order, per-warp shared accumulators
+        // small d: rows in order, per-warp shared accumulators (+ C for the distances)
         e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);
         if (e != cudaSuccess) return e;
-        const size_t sm = (size_t)8 * (3 * (size_t)k * d + k) * sizeof(unsigned);
+        const size_t sm = (size_t)8 * (3 * (size_t)k * d + k) * sizeof(unsigned) +
+                          (want_wd ? (size_t)k * d * sizeof(float) : 0);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 8, (n + 8 * AS_CHUNK - 1) / (8 * AS_CHUNK)));
         switch (d) {
 #define KM_ACC(DD)                                                                                                  \
     case DD:                                                                                                        \
-        e = allow_max_smem(k_accum_small<DD>);                                                                      \
-        if (e != cudaSuccess) return e;                                                                             \
-        k_accum_small<DD><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, sums, counts);          \
+        if (want_wd) {                                                                                              \
+            e = allow_max_smem(k_accum_small<DD, true>);                                                            \
+            if (e != cudaSuccess) return e;                                                                         \
+            k_accum_small<DD, true><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, sums, counts,  \
+                                                                       C_wd, md_out);                               \
+        } else {                                                                                                    \
+            e = allow_max_smem(k_accum_small<DD, false>);                                                           \
+            if (e != cudaSuccess) return e;                                                                         \
+            k_accum_small<DD, false><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, sums, counts, \
+                                                                        nullptr, nullptr);                          \
+        }                                                                                                           \
         break;
             KM_ACC(1) KM_ACC(2) KM_ACC(3) KM_ACC(4) KM_ACC(5) KM_ACC(6) KM_ACC(7) KM_ACC(8)
 #undef KM_ACC
         }
+        if (nlaunch) *nlaunch = 1;
         return cudaGetLastError();
     }
     const size_t hsm = sizeof(int) * (size_t)k;
     const bool vec = d % 4 == 0 && ((uintptr_t)X % 16) == 0;
     const bool bucket = 2 * hsm <= 200 * 1024 && (d == 1 || d == 2 || d == 3 || d == 5 || (vec && d <= 512));
+    // the bucket kernels of rows wider than 5 coordinates read the rows as
+    // float4: they can take the distances along when C is aligned as well
+    const bool fused = want_wd && bucket && d > 5 && ((uintptr_t)C_wd % 16) == 0;
+    if (want_wd && !fused) {
+        e = launch_winner_dist(X, n, d, C_wd, labels, md_out, num_sms, st);
+        if (e != cudaSuccess) return e;
+        nl++;
+    }
     if (bucket) {
         int* cnt32 = iscratch;            // k
         int* off = iscratch + k;          // k + 1
@@ -610,17 +783,19 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         // would leave SMs idle), the items strided over the warps; work items of
         // `seg` rows, about four per resident warp (fewer, longer items mean
         // fewer atomic adds per centre coordinate)
-        int per_sm = 1;
+        typedef void (*BucketFn)(const float*, int64_t, int, int, int, const int*, const int*, const int32_t*,
+                                 const unsigned*, long long*, const float*, double*);
+        BucketFn bfn = nullptr;
         if (d > 5) {
-            const void* fn = d <= 32    ? (const void*)k_bucket_sum<1, 8>
-                             : d <= 64  ? (const void*)k_bucket_sum<1, 16>
-                             : d <= 128 ? (const void*)k_bucket_sum<1, 32>
-                             : d <= 256 ? (const void*)k_bucket_sum<2, 32>
-                                        : (const void*)k_bucket_sum<4, 32>;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+#define KM_BS(NV, L) (fused ? (BucketFn)k_bucket_sum<NV, L, true> : (BucketFn)k_bucket_sum<NV, L, false>)
+            bfn = d <= 32 ? KM_BS(1, 8) : d <= 64 ? KM_BS(1, 16) : d <= 128 ? KM_BS(1, 32) : d <= 256 ? KM_BS(2, 32)
+                                                                                                 : KM_BS(4, 32);
+#undef KM_BS
+        }
+        int per_sm = 8;
+        if (bfn) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)bfn, 256, 0);
             if (e != cudaSuccess) return e;
-        } else {
-            per_sm = 8;
         }
         const int64_t resident_warps = (int64_t)num_sms * std::max(per_sm, 1) * 8;
         const int seg = (int)std::min<int64_t>(SEG_MAX, std::max<int64_t>(64, n / (resident_warps * 4) / 32 * 32));
@@ -635,11 +810,8 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
         else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
         else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 32) k_bucket_sum<1, 8><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 64) k_bucket_sum<1, 16><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 128) k_bucket_sum<1, 32><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d <= 256) k_bucket_sum<2, 32><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
-        else k_bucket_sum<4, 32><<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums);
+        else bfn<<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums, C_wd, md_out);
+        if (nlaunch) *nlaunch = nl + 4;
         return cudaGetLastError();
     }
     e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);
@@ -657,6 +829,7 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         k_accumulate<false><<<(unsigned)std::max<int64_t>(blk, 1), 512, 0, st>>>(X, n, d, labels, k, absmax_bits,
                                                                                   sums, counts);
     }
+    if (nlaunch) *nlaunch = nl + 1;
     return cudaGetLastError();
 }
 

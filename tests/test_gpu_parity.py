@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2407_12208_gb300 import workloads
-from gpu_util import MARGIN, RTOL_FP64, RTOL_MIXED, check_assign
+from gpu_util import MARGIN, RTOL_FP64, RTOL_MD, RTOL_MIXED, check_assign
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,7 @@ def test_fp64_direct_blobs(ctx):
     assert np.array_equal(lab, olab)
     np.testing.assert_allclose(md, od1, rtol=RTOL_FP64)
     assert nf == 0
+    check_assign(lab, md, X, C, oracle, RTOL_FP64)
 
 
 @pytest.mark.parametrize("n,d,k", [(5000, 5, 16), (1000, 16, 8), (777, 33, 40), (300, 2, 300),
@@ -52,7 +53,7 @@ def test_fp32_direct_certified(ctx, n, d, k):
     else:
         X, C = workloads.blobs(n, d, k, seed=3)
     lab, md, nf, st = _run_assign(ctx, X, C, "fp32")
-    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    check_assign(lab, md, X, C, oracle, RTOL_MD)
 
 
 # ------------------------------------------------------- tensor-core paths
@@ -79,7 +80,7 @@ def _data(kind, n, d, k, seed):
 def test_tc_assign_parity(ctx, low, kind, n, d, k):
     X, C = _data(kind, n, d, k, seed=n + d + k)
     lab, md, nf, st = _run_assign(ctx, X, C, low)
-    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    check_assign(lab, md, X, C, oracle, RTOL_MD)
     fmt = {"fp16": 0, "bf16": 1, "e4m3": 2}[low]
     sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0, per_row_scale=(fmt == 2))
     lo, hi = int(sure.sum()), int((sure | maybe).sum())
@@ -91,7 +92,7 @@ def test_tc_assign_parity(ctx, low, kind, n, d, k):
 def test_tc_paper_test_flags_everything_at_r128_bf16(ctx, low):
     X, C = workloads.uniform_pairs(600, 128, 50, seed=4)
     lab, md, nf, st = _run_assign(ctx, X, C, low, test="paper", c_A=1.0)
-    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    check_assign(lab, md, X, C, oracle, RTOL_MD)
     fmt = {"fp16": 0, "bf16": 1}[low]
     sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0, test="paper", c_A=1.0)
     assert int(sure.sum()) <= nf <= int((sure | maybe).sum())
@@ -102,7 +103,7 @@ def test_tc_paper_test_flags_everything_at_r128_bf16(ctx, low):
 def test_tc_test_off_still_certified(ctx):
     X, C = workloads.gaussian_mixture(2000, 64, 64, seed=5)
     lab, md, nf, st = _run_assign(ctx, X, C, "bf16", test="off")
-    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    check_assign(lab, md, X, C, oracle, RTOL_MD)
     assert nf == 0
 
 
@@ -112,7 +113,7 @@ def test_tc_edges(ctx, low):
     X, C = workloads.uniform_pairs(50, 96, 1, seed=6)
     lab, md, *_ = _run_assign(ctx, X, C, low)
     assert np.all(lab == 0)
-    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    check_assign(lab, md, X, C, oracle, RTOL_MD)
     X = workloads.uniform_pairs(200, 64, 200, seed=7)[0]
     lab, md, *_ = _run_assign(ctx, X, X.copy(), low)
     assert np.array_equal(lab, np.arange(200))
@@ -120,7 +121,7 @@ def test_tc_edges(ctx, low):
     X, C = workloads.uniform_pairs(400, 64, 40, seed=8)
     C[25] = C[3]
     lab, md, *_ = _run_assign(ctx, X, C, low)
-    check_assign(lab, md, X, C, oracle, RTOL_MIXED)
+    check_assign(lab, md, X, C, oracle, RTOL_MD)
     assert not np.any(lab == 25)
 
 
@@ -139,7 +140,7 @@ def test_tc_rejects_bad_arguments(ctx):
 
 
 # ------------------------------------------------------------ distance matrix
-@pytest.mark.parametrize("low", ["fp16", "bf16"])
+@pytest.mark.parametrize("low", ["fp16", "bf16", "e4m3"])
 @pytest.mark.parametrize("scenario", ["far", "near"])
 def test_distances_alg2(ctx, low, scenario):
     import paper_2407_12208_gb300 as pkg
@@ -156,16 +157,18 @@ def test_distances_alg2(ctx, low, scenario):
     flags = ((bits[(np.arange(n * k) >> 5)] >> (np.arange(n * k) & 31)) & 1).reshape(n, k).astype(bool)
     assert flags.sum() == nf
     Dex = oracle.dist_direct(X, C)
-    fmt = {"fp16": 0, "bf16": 1}[low]
-    B = oracle.tc_bound_matrix(X, C, fmt)
+    fmt = {"fp16": 0, "bf16": 1, "e4m3": 2}[low]
+    prs = fmt == 2  # E4M3: power-of-two scales per row of X and per centre
+    B = oracle.tc_bound_matrix(X, C, fmt, per_row_scale=prs)
     # unflagged: within the bound (Theorem 4.2 + conversion error); relative error <= 1/(rho-1)
     un = ~flags
     assert np.all(np.abs(D[un] - Dex[un]) <= B[un] + 1e-6 * Dex[un])
     assert np.all(np.abs(D[un] - Dex[un]) <= Dex[un] / 4.0)
     # flagged: binary64 direct value stored in fp32
     np.testing.assert_allclose(D[flags], Dex[flags], rtol=2 ** -23, atol=1e-38)
-    sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0)
+    sure, maybe = oracle.predict_tc_flags(X, C, fmt, 5.0, per_row_scale=prs)
     assert np.all(flags[sure & ~maybe]) and not np.any(flags[~sure & ~maybe])
+    assert np.all(D >= 0.0)  # no pair is left with its flag mark
 
 
 # ---------------------------------------------------------------- centre update
@@ -273,7 +276,7 @@ def test_full_size_bf16_sampled():
     lab = lab.cpu().numpy()
     md = md.cpu().numpy()
     rows = np.random.default_rng(0).choice(len(X), 2000, replace=False)
-    check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MIXED)
+    check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MD)
     st = c.stats()
     assert st["pairs"] == 1_000_000 * 1024
 
@@ -302,7 +305,7 @@ def test_full_size_lloyd_step_sampled(wl, n, d, k, low):
     lab, md, Cn, cnt = lab.cpu().numpy(), md.cpu().numpy(), Cn.cpu().numpy(), cnt.cpu().numpy()
     assert lab.min() >= 0 and lab.max() < k
     rows = np.random.default_rng(1).choice(n, 2000, replace=False)
-    check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MIXED)
+    check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MD)
     oC, ocnt, _ = oracle.update(X, lab, C, 1, md)
     assert np.array_equal(cnt, ocnt)
     np.testing.assert_allclose(Cn, oC, rtol=2 ** -22, atol=1e-30)
@@ -337,7 +340,8 @@ def test_lloyd_step_equals_assign_then_update(ctx, low, empty, shape):
 
 @pytest.mark.parametrize("low,empty,shape", [("bf16", "farthest", (20000, 128, 300)), ("fp16", "keep", (7001, 64, 96)),
                                              ("e4m3", "farthest", (5000, 64, 40)), ("fp32", "farthest", (3000, 16, 24)),
-                                             ("fp64", "keep", (2000, 8, 9)), ("bf16", "farthest", (300, 32, 7))])
+                                             ("fp64", "keep", (2000, 8, 9)), ("bf16", "farthest", (300, 32, 7)),
+                                             ("bf16", "keep", (1000, 16, 600))])
 def test_lloyd_step_host_equals_device(ctx, low, empty, shape):
     """km_lloyd_step_host (host buffers, rows in chunks overlapping copies and
     kernels) gives km_lloyd_step's results bit for bit, pinned or pageable."""
@@ -400,7 +404,7 @@ def test_tc_large_k_full_row_path(ctx):
     ties = ~sel
     if ties.any():  # exact ties: lowest index, as the oracle
         assert np.array_equal(lab[rows][ties], olab[ties])
-    np.testing.assert_allclose(md[rows], od1, rtol=RTOL_MIXED, atol=1e-30)
+    np.testing.assert_allclose(md[rows], oracle.dist_labelled(X[rows], C, lab[rows]), rtol=RTOL_MD, atol=1e-30)
 
 
 def test_update_small_d_long_label_runs(ctx):
@@ -418,3 +422,89 @@ def test_update_small_d_long_label_runs(ctx):
     oC, ocnt, _ = oracle.update(X, lab, C, 0, np.zeros(n))
     assert np.array_equal(cnt.cpu().numpy(), ocnt)
     np.testing.assert_allclose(Cn.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
+
+
+# ------------------------------------------------------ quantisation (step a1)
+def _e4m3_edge_rows(d):
+    rows = []
+    for j in range(-24, 25, 4):
+        edge = np.float32(448.0 * 2.0 ** j)
+        for m in (edge, np.nextafter(edge, np.float32(np.inf)), np.nextafter(edge, np.float32(0))):
+            r = np.linspace(-0.9, 0.9, d).astype(np.float32) * m
+            r[j % d] = -m
+            rows.append(r)
+    rows.append(np.zeros(d, np.float32))
+    rows.append(np.full(d, 1e-40, np.float32))       # binary32 subnormal maximum: the clamped scale
+    rows.append(np.full(d, 3e-37, np.float32))
+    return np.stack(rows)
+
+
+@pytest.mark.parametrize("low", ["fp16", "bf16", "e4m3"])
+@pytest.mark.parametrize("d", [37, 128])
+def test_quantize_bitexact(ctx, low, d):
+    """km_quantize (Alg. 2's first line) against the oracle's quantisation:
+    the low-format values and the E4M3 row scales bit for bit, ||x||^2 to
+    the binary32 rounding, the norms as upper bounds within (1 + 2^-11)."""
+    fmt = {"fp16": 0, "bf16": 1, "e4m3": 2}[low]
+    r = np.random.default_rng(d)
+    X = (r.normal(size=(700, d)) * 10.0 ** r.uniform(-3, 3, size=(700, 1))).astype(np.float32)
+    if fmt == 2:
+        X = np.concatenate([X, _e4m3_edge_rows(d)])
+    Xq, stats, scale = ctx.quantize(_dev(X), low)
+    torch.cuda.synchronize()
+    n = X.shape[0]
+    tdt = {0: torch.float16, 1: torch.bfloat16, 2: torch.float8_e4m3fn}[fmt]
+    vals = Xq.view(tdt).float().cpu().numpy().astype(np.float64)
+    sc = scale.cpu().numpy().astype(np.float64)
+    st = stats.cpu().numpy().astype(np.float64)
+    oq, op, onx, onq, onr, osc = oracle.row_quant_stats(X, fmt, per_row_scale=(fmt == 2))
+    np.testing.assert_array_equal(sc, osc)
+    np.testing.assert_array_equal(vals[:, :d] * sc[:, None], oq.astype(np.float64))
+    assert np.all(vals[:, d:] == 0.0)
+    # ||x||^2: the binary64 value rounded to binary32 (ties below 2^-44 aside)
+    np.testing.assert_allclose(st[:, 0], op, rtol=2.0 ** -23, atol=0)
+    for col, ref in ((1, onx), (2, onq), (3, onr)):
+        assert np.all(st[:, col] >= ref * (1 - 2.0 ** -40)), col
+        assert np.all(st[:, col] <= ref * (1 + 2.0 ** -11) + 1e-37), col
+
+
+# ------------------------------------------- empty clusters on the mixed path
+@pytest.mark.parametrize("low", ["bf16", "fp16", "e4m3"])
+def test_lloyd_mixed_empty_cluster_farthest(low):
+    """A centre far from every point empties its cluster in the first
+    iteration: KM_EMPTY_FARTHEST re-seeds it with the point of largest
+    min_dist (binary64-accurate on the mixed path, as the oracle's).  Labels,
+    centres and the SSE trajectory follow oracle.lloyd."""
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    X, C0 = workloads.gaussian_mixture(20000, 64, 32, seed=63)
+    C0[5] = C0[5] + 1e3
+    C0[17] = C0[17] - 1e3
+    p = pkg.params(low, max_iter=6, empty="farthest")
+    C, lab, sse, eta, it = c.lloyd_run(_dev(X), _dev(C0), p)
+    oC, olab, osse, oit = oracle.lloyd(X, C0, 6, empty_policy=1)
+    assert np.array_equal(lab.cpu().numpy(), olab)
+    np.testing.assert_allclose(C.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
+    np.testing.assert_allclose(sse, osse, rtol=RTOL_MIXED)
+    # the first SSE (before any update) is the sum of binary64-accurate distances
+    np.testing.assert_allclose(sse[0], osse[0], rtol=1e-12)
+
+
+def test_workspace_is_linear_in_n(ctx):
+    """The workspace of every synchronous call is O(n): below 1 GB at the
+    1e6 x 128, k = 1024 benchmark shape, in every low format."""
+    import paper_2407_12208_gb300 as pkg
+    for low in ("bf16", "fp16", "e4m3", "fp32", "fp64"):
+        b = ctx.workspace_size(1_000_000, 128, 1024, pkg.params(low))
+        assert b < 1_000_000_000, (low, b)
+
+
+def test_distances_queue_overflow_scans(ctx):
+    """More flagged pairs than the bounded queue holds (every pair of the
+    cancellation data): the binary64 patch finds them by their marks."""
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.cancellation(300, 32, 300, seed=64)
+    D, bits, nf = ctx.distances(_dev(X), _dev(C), pkg.params("bf16", "tc"))
+    D = D.cpu().numpy().astype(np.float64)
+    assert nf == 300 * 300
+    np.testing.assert_allclose(D, oracle.dist_direct(X, C), rtol=2 ** -23, atol=1e-38)

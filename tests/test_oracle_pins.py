@@ -67,6 +67,54 @@ def test_quantize_matches_torch_conversion(fmt, tdtype):
     np.testing.assert_array_equal(got, ref)
 
 
+def _e4m3_scales(rows):
+    d = max(len(r) for r in rows)
+    X = np.zeros((len(rows), d), np.float32)
+    for i, r in enumerate(rows):
+        X[i, :len(r)] = r
+    Xq, _, _, _, _, sc = oracle.row_quant_stats(X, 2, per_row_scale=True)
+    return X, Xq, sc
+
+
+def test_e4m3_row_scale_rule():
+    # The per-row E4M3 scale (reading R12): the smallest power of two s with
+    # max|x| / s <= 448 -- the row maximum lands in (224, 448] and never
+    # saturates -- kept a normal binary32 number (s >= 2^-126); s = 1 for an
+    # all-zero row.  Checked from its definition on edge rows: maxima exactly
+    # 448 2^j and one binary32 ulp either side, negative maxima, rows whose
+    # maximum is a binary32 subnormal, and the all-zero row.
+    rows, expect = [], []
+    for j in range(-30, 31, 3):
+        edge = np.float32(448.0 * 2.0 ** j)
+        up = np.nextafter(edge, np.float32(np.inf))
+        dn = np.nextafter(edge, np.float32(0))
+        rows += [[edge, edge * np.float32(0.25)], [-up, edge * np.float32(0.5)], [dn, -dn]]
+        expect += [2.0 ** j, 2.0 ** (j + 1), 2.0 ** j]
+    X, Xq, sc = _e4m3_scales(rows)
+    np.testing.assert_array_equal(sc, np.array(expect))
+    r = np.random.default_rng(12)
+    rand = [list((r.normal(size=16) * 10.0 ** r.uniform(-35, 35)).astype(np.float32)) for _ in range(200)]
+    tiny = [[1e-40, 2e-41], [np.float32(2.0 ** -149)], [np.float32(3e-38), -1e-39], [np.float32(448 * 2.0 ** -126)],
+            [np.float32(448 * 2.0 ** -127)]]
+    X, Xq, sc = _e4m3_scales(rand + tiny + [[0.0, 0.0]])
+    amax = np.abs(X).max(axis=1).astype(np.float64)
+    for i in range(len(X)):
+        if amax[i] == 0.0:
+            assert sc[i] == 1.0
+            continue
+        m, e = math.frexp(sc[i])
+        assert m == 0.5, sc[i]                        # a power of two
+        assert amax[i] / sc[i] <= 448.0               # never saturates
+        if sc[i] > 2.0 ** -126:
+            assert amax[i] / sc[i] > 224.0            # the smallest such power
+            # the row maximum is represented to E4M3's unit roundoff (no saturation)
+            k = int(np.argmax(np.abs(X[i])))
+            assert abs(Xq[i, k] - X[i, k]) <= 2.0 ** -4 * abs(X[i, k])
+        else:
+            assert sc[i] == 2.0 ** -126 and amax[i] <= 448.0 * 2.0 ** -126
+    assert list(sc[-6:-1]) == [2.0 ** -126] * 4 + [2.0 ** -126]
+
+
 def test_e4m3_saturates():
     assert oracle.round_to_format(1e6, 2) == 448.0
     assert oracle.round_to_format(-465.0, 2) == -448.0
@@ -87,6 +135,23 @@ def test_dist_direct_exact_on_tiny_inputs_and_theorem_4_1():
                 assert abs(Fraction(D[i, j]) - ex) <= Fraction(g) * ex
         # transposition / index check: D[i, j] belongs to (X_i, C_j)
         assert D[1, 2] == pytest.approx(float(_exact_dist(X[1], C[2])), rel=1e-14)
+
+
+def test_dist_labelled_exact_on_tiny_inputs():
+    # the distance to a given centre per point: exact rational arithmetic
+    # within Theorem 4.1's bound, and the right (point, centre) pair
+    r = np.random.default_rng(11)
+    for d in (1, 4, 9, 33):
+        X = (r.normal(size=(7, d)) * 10.0 ** r.uniform(-2, 2, size=(7, 1))).astype(np.float32)
+        C = (r.normal(size=(4, d))).astype(np.float32)
+        lab = r.integers(0, 4, size=7).astype(np.int32)
+        got = oracle.dist_labelled(X, C, lab)
+        g = oracle.gamma(d + 2, 2.0 ** -53)
+        for i in range(7):
+            ex = _exact_dist(X[i], C[lab[i]])
+            assert abs(Fraction(got[i]) - ex) <= Fraction(g) * ex
+            other = _exact_dist(X[i], C[(lab[i] + 1) % 4])
+            assert other == ex or abs(Fraction(got[i]) - other) > Fraction(g) * other
 
 
 def test_dist_direct_zero_and_symmetry():

@@ -107,3 +107,21 @@ def test_static_requires_both_outputs(ctx):
     rc = ctx.lib.km_assign_static(ctx.h, ctypes.c_void_p(X.data_ptr()), 8, ctypes.c_void_p(C.data_ptr()), 2, 4,
                                   ctypes.c_void_p(lab.data_ptr()), None, None)
     assert rc == pkg._binding.KM_EINVAL
+
+
+def test_static_allocates_no_device_memory(ctx):
+    """After the first call (which resolves the scratch address), further
+    calls leave the device's free memory and torch's allocator untouched."""
+    X, C = workloads.blobs(30000, 32, 50, seed=44)
+    X, C = _dev(X), _dev(C)
+    lab, md = _outputs(X.shape[0])
+    ctx.assign_static(X, C, lab, md)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    used0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        ctx.assign_static(X, C, lab, md)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == used0
