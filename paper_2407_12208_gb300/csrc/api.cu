@@ -193,7 +193,7 @@ struct UpdateWs {
     long long* counts;
     unsigned* absmax;
     double* shift;
-    int32_t* taken;
+    void* esel;
     int* iscratch;
     int32_t* perm;
 };
@@ -203,7 +203,7 @@ UpdateWs carve_update(Carve& cv, int64_t n, int d, int k) {
     u.counts = cv.take<long long>((size_t)k);
     u.absmax = cv.take<unsigned>(1);
     u.shift = cv.take<double>(1);
-    u.taken = cv.take<int32_t>((size_t)k);
+    u.esel = cv.take<unsigned char>(empty_select_bytes(k));
     u.iscratch = cv.take<int>((size_t)4 * k + 2);
     u.perm = cv.take<int32_t>((size_t)n);
     return u;
@@ -335,8 +335,9 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     a.kchunks = (ldq * esz + 127) / 128;
     a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.spad = w.spad; a.colmax = w.colmax;
     a.tp = tp; a.mode = 0; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
-    a.cbits = 1;
-    while ((1 << a.cbits) < k) a.cbits++;  // column bits of a candidate entry (k <= 65535: at most 16)
+    int qbits = 0;
+    while ((1 << qbits) < (k + 3) / 4) qbits++;  // quad index bits (k <= 65535: at most 14)
+    a.ebits = qbits + 4;
     a.pairs = w.pairs; a.pair_cap = w.pair_cap; a.v32 = w.v32; a.rowpair = w.rowpair;
     {
         PhaseScope ps(ctx, KM_PHASE_SCREEN, st);
@@ -387,6 +388,16 @@ km_status accumulate(km_ctx* ctx, const float* X, int64_t n, int d, const int32_
     int nl = 0;
     CK(launch_accumulate(X, n, d, labels, k, u.absmax, u.sums, u.counts, u.iscratch, u.perm, ctx->num_sms, st, C_wd,
                          md_wd, &nl));
+    ctx->launches += (uint64_t)nl;
+    return KM_OK;
+}
+
+// Means, empty clusters and shift of the centre update.
+km_status finalize(km_ctx* ctx, const UpdateWs& u, int64_t n, int k, int d, const float* C_old, const km_params* p,
+                   const float* X, const double* md, float* C_new, int64_t* counts, DevCounters* cnt, cudaStream_t st) {
+    int nl = 0;
+    CK(launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts, u.shift, u.esel,
+                       &cnt->status, ctx->num_sms, st, &nl));
     ctx->launches += (uint64_t)nl;
     return KM_OK;
 }
@@ -588,8 +599,7 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
         PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
         KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
         if ((s = accumulate(ctx, X, n, d, labels, k, u, nullptr, nullptr, st)) != KM_OK) return s;
-        KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, min_dist, C_new, counts,
-                              u.shift, u.taken, st));
+        if ((s = finalize(ctx, u, n, k, d, C_old, p, X, min_dist, C_new, counts, cnt, st)) != KM_OK) return s;
     }
     if (shift_host) {
         if ((s = sync_status(ctx, cnt, st)) != KM_OK) return s;
@@ -626,8 +636,7 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
         s = accumulate(ctx, X, n, d, labels, k, u, C_old, p->low == KM_FP64_DIRECT ? nullptr : md, st);
         if (s != KM_OK) return s;
         KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
-        KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts, u.shift,
-                              u.taken, st));
+        if ((s = finalize(ctx, u, n, k, d, C_old, p, X, md, C_new, counts, w.cnt, st)) != KM_OK) return s;
     }
     ctx->last_cnt = w.cnt;
     ctx->last_sse = w.sse;
@@ -719,8 +728,8 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
             s = accumulate(ctx, h.X, n, d, h.labels, k, u, h.C, p->low == KM_FP64_DIRECT ? nullptr : h.min_dist, st);
             if (s != KM_OK) return s;
             KL(2, launch_sum_f64(h.min_dist, n, w.partials, kSumParts, w.sse, st));
-            KL(3, launch_finalize(u.sums, u.counts, u.absmax, n, k, d, h.C, p->empty, h.X, h.min_dist, h.C_new, h.counts,
-                                  u.shift, u.taken, st));
+            if ((s = finalize(ctx, u, n, k, d, h.C, p, h.X, h.min_dist, h.C_new, h.counts, w.cnt, st)) != KM_OK)
+                return s;
         }
         if (min_dist_host)
             CK(cudaMemcpyAsync(min_dist_host, h.min_dist, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
@@ -798,8 +807,8 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
             s = accumulate(ctx, X, n, d, labels, k, L.u, cur, p->low == KM_FP64_DIRECT ? nullptr : L.min_dist, st);
             if (s != KM_OK) return s;
             KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
-            KL(3, launch_finalize(L.u.sums, L.u.counts, L.u.absmax, n, k, d, cur, p->empty, X, L.min_dist, nxt,
-                                  L.counts, L.u.shift, L.u.taken, st));
+            if ((s = finalize(ctx, L.u, n, k, d, cur, p, X, L.min_dist, nxt, L.counts, L.a.cnt, st)) != KM_OK)
+                return s;
         }
         std::swap(cur, nxt);
         if (cancel && *cancel) {

@@ -33,15 +33,20 @@ KM_DEV float4 ld_shared_v4(uint32_t a) {
 }
 KM_DEV void st_shared_u32(uint32_t a, uint32_t v) { asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory"); }
 
-// Candidate entry: the fp32 bit pattern of d^ with its low cbits mantissa bits
-// replaced by the column index j < 2^cbits (cbits <= 16).  The stored value t
-// is d^ truncated toward zero to 24 - cbits significant bits, so the true d^
-// is at least t - |t| 2^(cbits - 23).
-KM_DEV uint32_t cand_entry(int j, float dh, uint32_t cmask) { return (__float_as_uint(dh) & ~cmask) | (uint32_t)j; }
-KM_DEV int cand_col(uint32_t e, uint32_t cmask) { return (int)(e & cmask); }
-// lscale = 2^(cbits - 23)
-KM_DEV float cand_lower(uint32_t e, uint32_t cmask, float lscale) {
-    const float t = __uint_as_float(e & ~cmask);
+// Candidate entry, one per quad of columns (4q .. 4q + 3): the fp32 bit
+// pattern of the quad's smallest d^ with its low ebits bits replaced by
+// (q << 4) | mask, mask bit c set when column 4q + c is a candidate
+// (ebits = qbits + 4 <= 18, q < 2^qbits).  The stored value t is d^
+// truncated toward zero to 24 - ebits significant bits, so every candidate
+// of the quad has d^ >= t - |t| 2^(ebits - 23).
+KM_DEV uint32_t quad_entry(int q, unsigned mask, float dh, uint32_t emask) {
+    return (__float_as_uint(dh) & ~emask) | ((uint32_t)q << 4) | mask;
+}
+KM_DEV int entry_quad(uint32_t e, uint32_t emask) { return (int)((e & emask) >> 4); }
+KM_DEV unsigned entry_mask(uint32_t e) { return e & 15u; }
+// lscale = 2^(ebits - 23)
+KM_DEV float cand_lower(uint32_t e, uint32_t emask, float lscale) {
+    const float t = __uint_as_float(e & ~emask);
     return t - fabsf(t) * lscale;
 }
 

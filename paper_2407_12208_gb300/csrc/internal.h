@@ -110,8 +110,8 @@ struct TcArgs {
     const ColMax* colmax;
     TestParams tp;
     int mode;
-    uint32_t* cand;           // mode 0: TC_GROUPS x TC_LIST x n entries (group, slot, row): d^'s bits with the low cbits replaced by j
-    int cbits;                // bits of the column index in a candidate entry: ceil(log2 k), at least 1
+    uint32_t* cand;           // mode 0: TC_GROUPS x TC_LIST x n quad entries (group, slot, row), common.cuh
+    int ebits;                // low bits of an entry holding the quad index and mask: ceil(log2 ceil(k / 4)) + 4
     int4* rowinfo;            // n x TC_GROUPS: (count, overflow, window W bits, d^min bits) per epilogue group
     int2* pairs;              // refinement: candidate pairs (row, j), each row's pairs contiguous
     int64_t pair_cap;         // capacity of pairs / v32
@@ -154,10 +154,16 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
 // on the fp32 pipe (double-float arithmetic of df.cuh)
 cudaError_t launch_winner_dist(const float* X, int64_t n, int d, const float* C, const int32_t* labels, double* md,
                                int num_sms, cudaStream_t st);
+// bytes of scratch the empty-cluster selection needs (launch_finalize's esel)
+size_t empty_select_bytes(int k);
+// means (binary64 division, fp32 store), empty clusters (KM_EMPTY_FARTHEST:
+// the rows of largest min_dist, one cooperative launch), shift.
+// esel: empty_select_bytes(k) bytes, 256-byte aligned; status: the device
+// status word (a bounded wait that runs out sets its timeout bit).
 cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
-                            int64_t n, int k, int d, const float* C_old, int empty_policy,
-                            const float* X, const double* min_dist, float* C_new, int64_t* counts_out,
-                            double* shift, int32_t* taken_rows, cudaStream_t st);
+                            int64_t n, int k, int d, const float* C_old, int empty_policy, const float* X,
+                            const double* min_dist, float* C_new, int64_t* counts_out, double* shift,
+                            void* esel, unsigned* status, int num_sms, cudaStream_t st, int* nlaunch);
 // deterministic sum of n doubles (fixed two-level order)
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* partials, int nparts, double* out,
                            cudaStream_t st);

@@ -8,7 +8,11 @@
 //   rounded to fp32 -- the same value as binary64 rounded to fp32 except in
 //   ties below 2^-44;  ||x~|| and ||x~ - x|| are fp32 sums inflated by
 //   (1 + 2^-12), which covers their own rounding (gamma_d(2^-24) < 2^-12 for
-//   d <= 4096), so the bound B built from them stays rigorous.
+//   d <= 4096), so the bound B built from them stays rigorous.  A non-zero
+//   row with ||x||^2 < 2^-100 (squares near binary32's underflow) gets
+//   infinite ||x~|| and ||x~ - x||: the bound is then infinite and every pair
+//   of the row goes to the direct formula, as for a row that overflowed the
+//   low format.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -21,6 +25,7 @@
 namespace km {
 
 constexpr float kNormInflate = 1.0f + 1.0f / 4096.0f;
+constexpr float kTinyNorm2 = 0x1p-100f;  // below this ||x||^2 the fp32 statistics are not trusted
 
 KM_DEV float quant_val(float v, int fmt) {
     if (fmt == 0) return __half2float(__float2half_rn(v));
@@ -79,9 +84,11 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
         }
         const float inv = 1.0f / s;  // exact: s is a power of two
         float ph = 0.0f, pl = 0.0f, q2 = 0.0f, r2 = 0.0f;
+        bool nz = false;
         for (int l = lane; l < ldq; l += 32) {
             float v = (l < d) ? a[l] : 0.0f;
             amx = fmaxf(amx, fabsf(v));
+            nz |= v != 0.0f;
             float qv = quant_val(v * inv, fmt);  // quantised value of x / s
             if (l < d) {
                 df_add_sq(v, ph, pl);
@@ -107,6 +114,7 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
             q2 += __shfl_xor_sync(0xffffffffu, q2, off);
             r2 += __shfl_xor_sync(0xffffffffu, r2, off);
         }
+        const bool nzr = __any_sync(0xffffffffu, nz);
         if (lane == 0) {
             float p = ph + pl;
             float4 o;
@@ -114,9 +122,10 @@ __global__ void k_quantize(const float* __restrict__ A, int64_t m, int d, int fm
             o.y = sqrtf(p) * kNormInflate;
             o.z = sqrtf(q2) * kNormInflate;
             o.w = sqrtf(r2) * kNormInflate;
-            // an element that overflowed the low format makes the row unusable
-            // for the expanded formula: an infinite bound flags all its pairs
-            if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
+            // an element that overflowed the low format, or squares near the
+            // underflow, make the row unusable for the expanded formula: an
+            // infinite bound flags all its pairs
+            if (!isfinite(o.z) || (nzr && !(p >= kTinyNorm2))) { o.z = INFINITY; o.w = INFINITY; }
             stat[i] = o;
             if (rscale) rscale[i] = s;
         }
@@ -174,11 +183,14 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
         const int64_t i = i0 + (int64_t)r * ngroups;
         if (i >= m) break;  // the same row for the group's eight lanes
         float4 x[NV];
+        bool nz = false;
 #pragma unroll
         for (int u = 0; u < NV; u++) {
             x[u] = xr[r][u];
             amx = fmaxf(amx, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
+            nz |= (x[u].x != 0.0f) | (x[u].y != 0.0f) | (x[u].z != 0.0f) | (x[u].w != 0.0f);
         }
+        const bool nzr = (__ballot_sync(gmask, nz) & gmask) != 0u;
         float s = 1.0f;
         if (fmt == 2) {
             float amax = 0.0f;
@@ -274,9 +286,10 @@ __global__ void k_quantize_g8(const float* __restrict__ A, int64_t m, int d, int
             o.y = sqrtf(p) * kNormInflate;
             o.z = sqrtf(q2) * kNormInflate;
             o.w = sqrtf(r2) * kNormInflate;
-            // an element that overflowed the low format makes the row unusable
-            // for the expanded formula: an infinite bound flags all its pairs
-            if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
+            // an element that overflowed the low format, or squares near the
+            // underflow, make the row unusable for the expanded formula: an
+            // infinite bound flags all its pairs
+            if (!isfinite(o.z) || (nzr && !(p >= kTinyNorm2))) { o.z = INFINITY; o.w = INFINITY; }
             stat[i] = o;
             if (rscale) rscale[i] = s;
         }
@@ -298,12 +311,15 @@ __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, in
     for (int64_t i = warp; i < m; i += nw) {
         const float4* a4 = reinterpret_cast<const float4*>(A + i * d);
         float4 x[NV];
+        bool nz = false;
 #pragma unroll
         for (int u = 0; u < NV; u++) {
             const int c = lane + 32 * u;
             x[u] = (c < d4) ? a4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
             amx = fmaxf(amx, fmaxf(fmaxf(fabsf(x[u].x), fabsf(x[u].y)), fmaxf(fabsf(x[u].z), fabsf(x[u].w))));
+            nz |= (x[u].x != 0.0f) | (x[u].y != 0.0f) | (x[u].z != 0.0f) | (x[u].w != 0.0f);
         }
+        const bool nzr = __any_sync(0xffffffffu, nz);
         float s = 1.0f;
         if (fmt == 2) {
             float amax = 0.0f;
@@ -366,7 +382,7 @@ __global__ void k_quantize_vec(const float* __restrict__ A, int64_t m, int d, in
             o.y = sqrtf(p) * kNormInflate;
             o.z = sqrtf(q2) * kNormInflate;
             o.w = sqrtf(r2) * kNormInflate;
-            if (!isfinite(o.z)) { o.z = INFINITY; o.w = INFINITY; }
+            if (!isfinite(o.z) || (nzr && !(p >= kTinyNorm2))) { o.z = INFINITY; o.w = INFINITY; }
             stat[i] = o;
             if (rscale) rscale[i] = s;
         }

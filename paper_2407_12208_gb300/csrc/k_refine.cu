@@ -84,18 +84,19 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
     }
 }
 
-// Candidate selection, one thread per row: the entries of both epilogue
-// groups' lists inside the window of the row's final d^ minimum (the smaller
-// of the two groups' minima), written out as (row, j) pairs, contiguous per
-// row, one atomic reservation per warp.  Rows whose list overflowed, or that
-// no longer fit in the pair buffer, get count -1 (whole-row recompute).
+// Candidate selection, one thread per row: the quad entries of every epilogue
+// group's list inside the window of the row's final d^ minimum (the smallest
+// of the groups' minima), each masked column written out as a (row, j) pair,
+// contiguous per row, one atomic reservation per block.  Rows whose list
+// overflowed, or that no longer fit in the pair buffer, get count -1
+// (whole-row recompute).
 __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ rowinfo,
-                                                     const uint32_t* __restrict__ cand, int64_t n, int cbits,
+                                                     const uint32_t* __restrict__ cand, int64_t n, int ebits,
                                                      int2* __restrict__ pairs, int64_t cap,
                                                      int2* __restrict__ rowpair, DevCounters* cnt) {
     const int lane = threadIdx.x & 31;
-    const uint32_t cmask = (1u << cbits) - 1u;
-    const float lscale = __uint_as_float((uint32_t)(127 + cbits - 23) << 23);  // 2^(cbits - 23)
+    const uint32_t emask = (1u << ebits) - 1u;
+    const float lscale = __uint_as_float((uint32_t)(127 + ebits - 23) << 23);  // 2^(ebits - 23)
     // rounds of blockDim rows per block, the same count in every warp (the
     // reservation synchronises the block)
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += (int64_t)gridDim.x * blockDim.x) {
@@ -131,10 +132,18 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
             for (int s = 0; s < SPEC; s++) eg[s] = (s < ng) ? cg[(size_t)s * n] : 0u;
             unsigned m = 0;
 #pragma unroll
-            for (int s = 0; s < SPEC; s++) m |= (s < ng && cand_lower(eg[s], cmask, lscale) <= lim) ? (1u << s) : 0u;
-            for (int s = SPEC; s < ng; s++) m |= (cand_lower(cg[(size_t)s * n], cmask, lscale) <= lim) ? (1u << s) : 0u;
+            for (int s = 0; s < SPEC; s++) {
+                const bool in = s < ng && cand_lower(eg[s], emask, lscale) <= lim;
+                m |= in ? (1u << s) : 0u;
+                c += in ? __popc(entry_mask(eg[s])) : 0;
+            }
+            for (int s = SPEC; s < ng; s++) {
+                const uint32_t e = cg[(size_t)s * n];
+                const bool in = cand_lower(e, emask, lscale) <= lim;
+                m |= in ? (1u << s) : 0u;
+                c += in ? __popc(entry_mask(e)) : 0;
+            }
             msk[g] = m;
-            c += __popc(m);
         }
         // one reservation per block: lane prefix sums, then warp totals through
         // shared memory (every warp of the block takes part in each round)
@@ -164,8 +173,11 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
 #pragma unroll
                 for (int g = 0; g < TC_GROUPS; g++) {
                     const uint32_t* cg = c0 + (size_t)g * TC_LIST * n;
-                    for (unsigned m = msk[g]; m; m &= m - 1)
-                        pairs[off0 + w++] = make_int2((int)row, cand_col(cg[(size_t)(__ffs(m) - 1) * n], cmask));
+                    for (unsigned m = msk[g]; m; m &= m - 1) {
+                        const uint32_t e = cg[(size_t)(__ffs(m) - 1) * n];
+                        const int j0 = 4 * entry_quad(e, emask);
+                        for (unsigned b = entry_mask(e); b; b &= b - 1) pairs[off0 + w++] = make_int2((int)row, j0 + __ffs(b) - 1);
+                    }
                 }
             }
             rowpair[row] = make_int2(fits ? (int)off0 : 0, (full || !fits) ? -1 : c);
@@ -360,7 +372,7 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     const int64_t rows_blocks = std::max<int64_t>(1, (a.n + 255) / 256);
     const int64_t rb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(sel_per_sm, 1));
     const int64_t cb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(cert_per_sm, 1));
-    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.cbits, a.pairs, a.pair_cap, a.rowpair, a.cnt);
+    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.ebits, a.pairs, a.pair_cap, a.rowpair, a.cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *nlaunch = 4;

@@ -16,9 +16,10 @@
 //               (one packed FMA per two columns); per quad of columns its
 //               minimum; only the quads that can hold a candidate or a flagged
 //               pair take the slow path: d^ = p + e, the exact reliability
-//               test, and a candidate append.  Candidates: every j with
-//               d^_j <= d^_min + 2 B_max, the only centres that can be the true
-//               argmin.
+//               test, and one list entry per quad with candidates (its index,
+//               the mask of its candidate columns, its smallest d^).
+//               Candidates: every j with d^_j <= d^_min + 2 B_max, the only
+//               centres that can be the true argmin.
 //
 // All waits are bounded (common.cuh); a timeout sets the status word and the
 // CTA winds down.
@@ -131,14 +132,14 @@ __device__ __noinline__ bool pair_flagged(int test, float rho, float kn, float b
 // Keep only the list entries still inside the window (slot-major layout):
 // all slots are read first (independent loads), then packed with predicated
 // stores.
-KM_DEV int compact_list(uint32_t* list, int cnt, float lim, uint32_t cmask, float lscale) {
+KM_DEV int compact_list(uint32_t* list, int cnt, float lim, uint32_t emask, float lscale) {
     uint32_t c[TC_L];
 #pragma unroll
     for (int r = 0; r < TC_L; r++) c[r] = list[r * TC_BM];
     int w = 0;
 #pragma unroll
     for (int r = 0; r < TC_L; r++) {
-        const bool keep = r < cnt && cand_lower(c[r], cmask, lscale) <= lim;
+        const bool keep = r < cnt && cand_lower(c[r], emask, lscale) <= lim;
         if (keep) list[w * TC_BM] = c[r];
         w += keep ? 1 : 0;
     }
@@ -294,8 +295,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t lbase = smem_u32(list);                            // the same as a shared address
         const ColMax cm = *a.colmax;
         const TestParams tp = a.tp;
-        const uint32_t cmask = (1u << a.cbits) - 1u;
-        const float lscale = __uint_as_float((uint32_t)(127 + a.cbits - 23) << 23);  // 2^(cbits - 23)
+        const uint32_t emask = (1u << a.ebits) - 1u;
+        const float lscale = __uint_as_float((uint32_t)(127 + a.ebits - 23) << 23);  // 2^(ebits - 23)
         unsigned long long nflag_total = 0;
         bool ok = true;
         int iter = 0;
@@ -417,34 +418,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         for (int qd = 0; qd < NQ; qd++) qmask |= (qm[qd] <= sthr) ? (1u << qd) : 0u;
                         // Slow path: each lane walks its own quads holding a candidate or a
                         // possibly flagged pair (the warp iterates as often as its busiest
-                        // lane); the quad's values are picked from registers by a select tree
-                        // on the lane's own quad index; one branch-free append per quad (a
-                        // lane with nothing to add writes the dummy slot), the rare further
-                        // candidates of a quad after a warp vote.
+                        // lane).  A quad with candidates becomes one list entry: its index,
+                        // the mask of its columns inside the window and its smallest d^ (a
+                        // lane with nothing to add writes the dummy slot).
                         if (__any_sync(0xffffffffu, qmask)) {
                             if (__any_sync(0xffffffffu, cnt > TC_L - 4 * TC_CW && !ovf)) {
                                 // every lane packs its list (dropping entries that left the window)
-                                const int cc = compact_list(list, cnt, p + cthr, cmask, lscale);
+                                const int cc = compact_list(list, cnt, p + cthr, emask, lscale);
                                 if (!ovf) cnt = cc;
                             }
                             __syncwarp();
-                            if (STG) {
-                                // Possibly flagged pairs (d^ <= F) lie in the qualifying quads:
-                                // they are counted in the walk below, value by value (every
-                                // d^ <= Fall is flagged whatever its column); a lane whose
-                                // whole step lies under Fall counts the step at once.
-                                const bool fstep = __any_sync(0xffffffffu, p + cmin <= F);
-                                bool fwhole = false;
-                                if (fstep && __any_sync(0xffffffffu, p + e[0] <= Fall)) {
-                                    float cmax = e[0];
+                            // Possibly flagged pairs (d^ <= F) lie in the qualifying quads:
+                            // they are counted in the walk below, value by value (every
+                            // d^ <= Fall is flagged whatever its column); a lane whose
+                            // whole step lies under Fall counts the step at once.
+                            const bool fstep = __any_sync(0xffffffffu, p + cmin <= F);
+                            bool fwhole = false;
+                            if (fstep && __any_sync(0xffffffffu, p + e[0] <= Fall)) {
+                                float cmax = e[0];
 #pragma unroll
-                                    for (int t = 1; t < NCOL; t++) cmax = fmaxf(cmax, e[t]);
-                                    fwhole = p + cmax <= Fall;  // padded columns hold +inf: never taken
-                                    nflag += fwhole ? NCOL : 0;
+                                for (int t = 1; t < NCOL; t++) cmax = fmaxf(cmax, e[t]);
+                                fwhole = p + cmax <= Fall;  // padded columns hold +inf: never taken
+                                nflag += fwhole ? NCOL : 0;
+                            }
+                            // one quad: its entry, and its flagged pairs while they are counted one by one
+                            auto take_quad = [&](float x0, float x1, float x2, float x3, int jq, bool act) {
+                                const unsigned mk = (x0 <= cthr ? 1u : 0u) | (x1 <= cthr ? 2u : 0u) |
+                                                    (x2 <= cthr ? 4u : 0u) | (x3 <= cthr ? 8u : 0u);
+                                const bool pc = act && mk != 0u && !ovf;
+                                const bool room = cnt < TC_L;
+                                const int slot = (pc && room) ? cnt : TC_L;
+                                const float qmn = fminf(fmin3(x0, x1, x2), x3);
+                                st_shared_u32(lbase + slot * (TC_BM * 4), quad_entry(jq >> 2, mk, p + qmn, emask));
+                                ovf |= (pc && !room);
+                                cnt += (pc && room) ? 1 : 0;
+                                if (fstep) {
+                                    const float xs4[4] = {x0, x1, x2, x3};
+#pragma unroll
+                                    for (int c = 0; c < 4; c++) {
+                                        const float dh = p + xs4[c];
+                                        if (act && !fwhole && dh <= F)
+                                            nflag += (dh <= Fall || KM_PAIR_FLAGGED(jq + c, dh)) ? 1 : 0;
+                                    }
                                 }
-                                // A row whose list overflowed takes no more candidates: it walks
-                                // its quads only while flagged pairs remain to be counted one by one.
-                                unsigned ph = (ovf && !(fstep && !fwhole)) ? 0u : qmask;
+                            };
+                            // A row whose list overflowed takes no more candidates: it walks
+                            // its quads only while flagged pairs remain to be counted one by one.
+                            const unsigned walk = (ovf && !(fstep && !fwhole)) ? 0u : qmask;
+                            if (STG) {
                                 // the lane's values staged in shared memory (quad-major: the
                                 // 32 lanes of a quad side by side, conflict-free both ways),
                                 // then one loop over all its quads: a 16-byte read per quad
@@ -452,103 +473,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                                 for (int qd = 0; qd < NQ; qd++)
                                     st_shared_v4(stg + qd * 512, e[4 * qd], e[4 * qd + 1], e[4 * qd + 2], e[4 * qd + 3]);
+                                unsigned ph = walk;
                                 while (__any_sync(0xffffffffu, ph)) {
                                     const bool act = ph != 0;
                                     const int qd = act ? __ffs(ph) - 1 : 0;
                                     ph &= ph - 1;
                                     const float4 ev = ld_shared_v4(stg + qd * 512);
-                                    const float et[4] = {ev.x, ev.y, ev.z, ev.w};
-                                    const int jq = col0 + 4 * qd;
-                                    const bool q0 = et[0] <= cthr, q1 = et[1] <= cthr, q2 = et[2] <= cthr, q3 = et[3] <= cthr;
-                                    const int c1 = q0 ? 0 : (q1 ? 1 : (q2 ? 2 : 3));
-                                    const float e1 = q0 ? et[0] : (q1 ? et[1] : (q2 ? et[2] : et[3]));
-                                    {
-                                        const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
-                                        const bool room = cnt < TC_L;
-                                        const int slot = (pc && room) ? cnt : TC_L;
-                                        st_shared_u32(lbase + slot * (TC_BM * 4), cand_entry(jq + c1, p + e1, cmask));
-                                        ovf |= (pc && !room);
-                                        cnt += (pc && room) ? 1 : 0;
-                                    }
-                                    const int nq = (int)q0 + (int)q1 + (int)q2 + (int)q3;
-                                    if (__any_sync(0xffffffffu, act && nq > 1 && !ovf)) {
-#pragma unroll
-                                        for (int c = 1; c < 4; c++) {
-                                            const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
-                                            const bool room = cnt < TC_L;
-                                            const int slot = (pc && room) ? cnt : TC_L;
-                                            st_shared_u32(lbase + slot * (TC_BM * 4), cand_entry(jq + c, p + et[c], cmask));
-                                            ovf |= (pc && !room);
-                                            cnt += (pc && room) ? 1 : 0;
-                                        }
-                                    }
-                                    if (fstep) {
-#pragma unroll
-                                        for (int c = 0; c < 4; c++) {
-                                            const float dh = p + et[c];
-                                            if (act && !fwhole && dh <= F)
-                                                nflag += (dh <= Fall || KM_PAIR_FLAGGED(jq + c, dh)) ? 1 : 0;
-                                        }
-                                    }
+                                    take_quad(ev.x, ev.y, ev.z, ev.w, col0 + 4 * qd, act);
                                 }
                             } else {
 #pragma unroll
-                            for (int half = 0; half < TC_CW; half++) {
-                                unsigned ph = (qmask >> (8 * half)) & 0xffu;
-                                const float* eh = e + 32 * half;
-                                while (__any_sync(0xffffffffu, ph)) {
-                                    const bool act = ph != 0;
-                                    const int qd = act ? __ffs(ph) - 1 : 0;
-                                    ph &= ph - 1;
-                                    const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
-                                    float et[4];
+                                for (int half = 0; half < TC_CW; half++) {
+                                    unsigned ph = (walk >> (8 * half)) & 0xffu;
+                                    const float* eh = e + 32 * half;
+                                    while (__any_sync(0xffffffffu, ph)) {
+                                        const bool act = ph != 0;
+                                        const int qd = act ? __ffs(ph) - 1 : 0;
+                                        ph &= ph - 1;
+                                        // the quad's values picked from registers by a select tree
+                                        const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
+                                        float et[4];
 #pragma unroll
-                                    for (int c = 0; c < 4; c++) {
-                                        const float s0 = b0 ? eh[4 + c] : eh[c], s1 = b0 ? eh[12 + c] : eh[8 + c];
-                                        const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
-                                        const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
-                                        et[c] = b2 ? t1 : t0;
-                                    }
-                                    const bool q0 = et[0] <= cthr, q1 = et[1] <= cthr, q2 = et[2] <= cthr, q3 = et[3] <= cthr;
-                                    const int jq = col0 + 32 * half + 4 * qd;
-                                    const int c1 = q0 ? 0 : (q1 ? 1 : (q2 ? 2 : 3));
-                                    const float e1 = q0 ? et[0] : (q1 ? et[1] : (q2 ? et[2] : et[3]));
-                                    {
-                                        const bool pc = act && (q0 || q1 || q2 || q3) && !ovf;
-                                        const bool room = cnt < TC_L;
-                                        const int slot = (pc && room) ? cnt : TC_L;
-                                        list[slot * TC_BM] = cand_entry(jq + c1, p + e1, cmask);
-                                        ovf |= (pc && !room);
-                                        cnt += (pc && room) ? 1 : 0;
-                                    }
-                                    const int nq = (int)q0 + (int)q1 + (int)q2 + (int)q3;
-                                    if (__any_sync(0xffffffffu, act && nq > 1 && !ovf)) {
-#pragma unroll
-                                        for (int c = 1; c < 4; c++) {
-                                            const bool pc = act && (c > c1) && (et[c] <= cthr) && !ovf;
-                                            const bool room = cnt < TC_L;
-                                            const int slot = (pc && room) ? cnt : TC_L;
-                                            list[slot * TC_BM] = cand_entry(jq + c, p + et[c], cmask);
-                                            ovf |= (pc && !room);
-                                            cnt += (pc && room) ? 1 : 0;
+                                        for (int c = 0; c < 4; c++) {
+                                            const float s0 = b0 ? eh[4 + c] : eh[c], s1 = b0 ? eh[12 + c] : eh[8 + c];
+                                            const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
+                                            const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
+                                            et[c] = b2 ? t1 : t0;
                                         }
-                                    }
-                                }
-                            }
-                            }
-                            if (!STG && __any_sync(0xffffffffu, p + cmin <= F)) {
-                                // a step whose largest d^ is under every column's threshold is
-                                // flagged whole (padded columns hold +inf: never taken here)
-                                float cmax = e[0];
-#pragma unroll
-                                for (int t = 1; t < NCOL; t++) cmax = fmaxf(cmax, e[t]);
-                                if (p + cmax <= Fall) {
-                                    nflag += NCOL;
-                                } else {
-#pragma unroll
-                                    for (int t = 0; t < NCOL; t++) {
-                                        const float dh = p + e[t];
-                                        if (dh <= F) nflag += KM_PAIR_FLAGGED(col0 + t, dh) ? 1 : 0;
+                                        take_quad(et[0], et[1], et[2], et[3], col0 + 32 * half + 4 * qd, act);
                                     }
                                 }
                             }

@@ -608,57 +608,193 @@ __global__ void k_means(const long long* __restrict__ sums, const long long* __r
     }
 }
 
-// Empty clusters (ascending j) take the not-yet-taken point with the largest
-// min_dist (lowest index on ties); then shift = max_j ||c_new - c_old||.
-__global__ void k_empty_and_shift(const long long* __restrict__ counts, int64_t n, int k, int d,
-                                  int empty_policy, const float* __restrict__ X, const double* __restrict__ min_dist,
-                                  const float* __restrict__ C_old, float* __restrict__ C_new, double* shift,
-                                  int32_t* __restrict__ taken) {
-    __shared__ double rv[1024];
-    __shared__ long long ri[1024];
-    __shared__ int ntaken, nempty;
+// ---- empty clusters: the rows with the largest min_dist ------------------
+// KM_EMPTY_FARTHEST (reading of "automatic empty cluster reinitialisation",
+// Section 6.2): the empty clusters, in ascending j, take the rows in
+// decreasing order of min_dist, ties to the lowest row index, each row once.
+// One cooperative launch over the resident blocks:
+//   1. block 0 lists the empty clusters (E of them, ascending) and clears the
+//      histograms; every block returns at once when E == 0;
+//   2. radix select (eight passes of 8 bits, most significant first) of T,
+//      the E-th largest min_dist bit pattern (non-negative doubles order like
+//      their bits), and A, the number of rows above it;
+//   3. among the rows equal to T, radix select (four passes) of the
+//      (E - A)-th smallest row index I;
+//   4. the E rows {md > T} + {md == T, index <= I} are collected, ranked by
+//      (md desc, index asc) and copied into the clusters in order.
+// Work is O(n) per pass whatever E is.  The blocks meet at a grid barrier
+// whose every wait is bounded: on timeout the status word's timeout bit is
+// set and the kernel winds down.
+struct EmptySel {
+    unsigned bar_count, bar_gen;  // grid barrier
+    int nempty, ncollected;
+    unsigned hist[12][256];       // 8 passes on the distance bits, 4 on the row index
+};
+size_t empty_select_bytes(int k) {
+    return ((sizeof(EmptySel) + 255) & ~(size_t)255) + (size_t)k * (sizeof(int) + 16 + sizeof(int));
+}
+
+KM_DEV bool grid_barrier(EmptySel* es, unsigned nblocks, unsigned* status) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = &es->bar_gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&es->bar_count, 1u) == nblocks - 1) {
+            es->bar_count = 0;
+            __threadfence();
+            atomicAdd(&es->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                __nanosleep(64);
+                if (clock64() - t0 > KM_WAIT_CYCLES) {
+                    atomicOr(status, KM_DEVERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+// From a pass's histogram: the digit holding the rank-th key (1-based) in the
+// given direction (descending: from 255 down), the keys before that digit and
+// the rank left within it.  Every thread computes the same answer.
+KM_DEV void radix_pick(const unsigned* hist, bool descending, unsigned rank, unsigned& digit, unsigned& before) {
+    unsigned acc = 0;
+    digit = 0;
+    before = 0;
+    for (int t = 0; t < 256; t++) {
+        const int dgt = descending ? 255 - t : t;
+        const unsigned c = __ldcg(hist + dgt);  // written by other blocks' atomics
+        if (acc + c >= rank) {
+            digit = (unsigned)dgt;
+            before = acc;
+            return;
+        }
+        acc += c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_empty_select(const long long* __restrict__ counts, int64_t n, int k, int d,
+                                                      const float* __restrict__ X, const double* __restrict__ md,
+                                                      float* __restrict__ C_new, EmptySel* es,
+                                                      int* __restrict__ empties, unsigned long long* __restrict__ keys,
+                                                      int* __restrict__ rows, int* __restrict__ order,
+                                                      unsigned* status) {
+    __shared__ unsigned sh[256];
+    __shared__ int wsum[8];
+    const unsigned nb = gridDim.x;
     const int t = threadIdx.x;
-    if (t == 0) { ntaken = 0; nempty = 0; }
-    __syncthreads();
-    // count the empty clusters in parallel; the ordered walk below runs only if any
-    int ne = 0;
-    for (int j = t; j < k; j += blockDim.x) ne += (counts[j] == 0);
-    if (ne) atomicAdd(&nempty, ne);
-    __syncthreads();
-    if (empty_policy == 1 && min_dist != nullptr && nempty > 0) {
-        for (int j = 0; j < k; j++) {
-            if (counts[j] != 0) continue;
-            double best = -1.0;
-            long long arg = -1;
-            for (int64_t i = t; i < n; i += blockDim.x) {
-                double v = min_dist[i];
-                if (v > best) {
-                    bool used = false;
-                    for (int q = 0; q < ntaken; q++) used |= (taken[q] == (int32_t)i);
-                    if (!used) { best = v; arg = i; }
-                }
+    // 1. the empty clusters in ascending j (block 0), histograms cleared
+    if (blockIdx.x == 0) {
+        for (int e = t; e < 12 * 256; e += blockDim.x) (&es->hist[0][0])[e] = 0u;
+        int base = 0;
+        for (int j0 = 0; j0 < k; j0 += blockDim.x) {
+            const int j = j0 + t;
+            const int e = (j < k && counts[j] == 0) ? 1 : 0;
+            int incl = e;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((t & 31) >= o) incl += v;
             }
-            rv[t] = best;
-            ri[t] = arg;
+            if ((t & 31) == 31) wsum[t >> 5] = incl;
             __syncthreads();
-            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-                if (t < s) {
-                    double ov = rv[t + s];
-                    long long oi = ri[t + s];
-                    if (oi >= 0 && (ov > rv[t] || (ov == rv[t] && (ri[t] < 0 || oi < ri[t])))) {
-                        rv[t] = ov;
-                        ri[t] = oi;
-                    }
-                }
-                __syncthreads();
+            int pre = 0, tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+                pre += (w < (t >> 5)) ? wsum[w] : 0;
+                tot += wsum[w];
             }
-            const long long a = ri[0];
-            if (a >= 0) {
-                for (int l = t; l < d; l += blockDim.x) C_new[(int64_t)j * d + l] = X[a * d + l];
-                if (t == 0) taken[ntaken++] = (int32_t)a;
-            }
+            if (e) empties[base + pre + incl - 1] = j;
+            base += tot;
             __syncthreads();
         }
+        if (t == 0) {
+            es->nempty = base;
+            es->ncollected = 0;
+        }
+    }
+    if (!grid_barrier(es, nb, status)) return;
+    const int E = *(volatile int*)&es->nempty;
+    if (E == 0) return;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + t, gstride = (int64_t)nb * blockDim.x;
+    const unsigned long long* mdb = reinterpret_cast<const unsigned long long*>(md);
+    // 2. T, the E-th largest distance pattern, and A, the rows above it
+    unsigned long long prefix = 0, mask = 0;
+    unsigned rank = (unsigned)E, above = 0;
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 56 - 8 * pass;
+        sh[t] = 0;
+        __syncthreads();
+        for (int64_t i = gtid; i < n; i += gstride) {
+            const unsigned long long key = mdb[i];
+            if ((key & mask) == prefix) atomicAdd(&sh[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (sh[t]) atomicAdd(&es->hist[pass][t], sh[t]);
+        if (!grid_barrier(es, nb, status)) return;
+        unsigned digit, before;
+        radix_pick(es->hist[pass], true, rank, digit, before);
+        above += before;
+        rank -= before;
+        prefix |= (unsigned long long)digit << shift;
+        mask |= 255ull << shift;
+    }
+    const unsigned long long T = prefix;
+    // 3. among the rows equal to T, the rank-th smallest index I (rank = E - A)
+    unsigned iprefix = 0, imask = 0;
+    for (int pass = 0; pass < 4; pass++) {
+        const int shift = 24 - 8 * pass;
+        sh[t] = 0;
+        __syncthreads();
+        for (int64_t i = gtid; i < n; i += gstride) {
+            if (mdb[i] == T && ((unsigned)i & imask) == iprefix) atomicAdd(&sh[((unsigned)i >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (sh[t]) atomicAdd(&es->hist[8 + pass][t], sh[t]);
+        if (!grid_barrier(es, nb, status)) return;
+        unsigned digit, before;
+        radix_pick(es->hist[8 + pass], false, rank, digit, before);
+        rank -= before;
+        iprefix |= digit << shift;
+        imask |= 255u << shift;
+    }
+    const unsigned I = iprefix;
+    // 4. collect the E rows, rank them, fill the clusters
+    for (int64_t i = gtid; i < n; i += gstride) {
+        const unsigned long long key = mdb[i];
+        if (key > T || (key == T && (unsigned)i <= I)) {
+            const int s = atomicAdd(&es->ncollected, 1);
+            if (s < E) {
+                keys[s] = key;
+                rows[s] = (int)i;
+            }
+        }
+    }
+    if (!grid_barrier(es, nb, status)) return;
+    // (the lists were written by other blocks: read through L2)
+    for (int64_t s = gtid; s < E; s += gstride) {
+        const unsigned long long ks = __ldcg(keys + s);
+        const int rs = __ldcg(rows + s);
+        int r = 0;
+        for (int q = 0; q < E; q++) {
+            const unsigned long long kq = __ldcg(keys + q);
+            r += (kq > ks || (kq == ks && __ldcg(rows + q) < rs)) ? 1 : 0;
+        }
+        order[r] = rs;
+    }
+    if (!grid_barrier(es, nb, status)) return;
+    for (int64_t e = gtid; e < (int64_t)E * d; e += gstride) {
+        const int r = (int)(e / d), l = (int)(e - (int64_t)r * d);
+        C_new[(int64_t)__ldcg(empties + r) * d + l] = X[(int64_t)__ldcg(order + r) * d + l];
     }
 }
 
@@ -836,19 +972,41 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
 cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
                             int64_t n, int k, int d, const float* C_old, int empty_policy, const float* X,
                             const double* min_dist, float* C_new, int64_t* counts_out, double* shift,
-                            int32_t* taken_rows, cudaStream_t st) {
+                            void* esel, unsigned* status, int num_sms, cudaStream_t st, int* nlaunch) {
+    int nl = 0;
     int64_t kd = (int64_t)k * d;
     int64_t blocks = min((int64_t)1024, (kd + 255) / 256);
     k_means<<<(unsigned)blocks, 256, 0, st>>>(sums, counts, absmax_bits, n, k, d, C_old, C_new, counts_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_empty_and_shift<<<1, 1024, 0, st>>>(counts, n, k, d, empty_policy, X, min_dist, C_old, C_new, shift,
-                                           taken_rows);
+    nl++;
+    if (empty_policy == 1 && min_dist != nullptr) {
+        EmptySel* es = reinterpret_cast<EmptySel*>(esel);
+        char* tail = reinterpret_cast<char*>(esel) + ((sizeof(EmptySel) + 255) & ~(size_t)255);
+        int* empties = reinterpret_cast<int*>(tail);
+        unsigned long long* keys = reinterpret_cast<unsigned long long*>(empties + k + (k & 1));
+        int* rows = reinterpret_cast<int*>(keys + k);
+        int* order = rows + k;
+        e = cudaMemsetAsync(es, 0, 2 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        // one block per SM: every block resident at once (cooperative launch)
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_empty_select, 256, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        void* args[] = {(void*)&counts, (void*)&n, (void*)&k, (void*)&d, (void*)&X, (void*)&min_dist, (void*)&C_new,
+                        (void*)&es, (void*)&empties, (void*)&keys, (void*)&rows, (void*)&order, (void*)&status};
+        e = cudaLaunchCooperativeKernel((const void*)k_empty_select, dim3((unsigned)num_sms), dim3(256), args, 0, st);
+        if (e != cudaSuccess) return e;
+        nl++;
+    }
     e = cudaMemsetAsync(shift, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    const int64_t sblocks = std::min<int64_t>(((int64_t)k * 32 + 255) / 256, 152 * 8);
+    const int64_t sblocks = std::min<int64_t>(((int64_t)k * 32 + 255) / 256, (int64_t)num_sms * 8);
     k_shift<<<(unsigned)std::max<int64_t>(sblocks, 1), 256, 0, st>>>(k, d, C_old, C_new,
                                                                    reinterpret_cast<unsigned long long*>(shift));
+    nl++;
+    if (nlaunch) *nlaunch = nl;
     return cudaGetLastError();
 }
 

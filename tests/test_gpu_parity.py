@@ -463,9 +463,14 @@ def test_quantize_bitexact(ctx, low, d):
     assert np.all(vals[:, d:] == 0.0)
     # ||x||^2: the binary64 value rounded to binary32 (ties below 2^-44 aside)
     np.testing.assert_allclose(st[:, 0], op, rtol=2.0 ** -23, atol=0)
+    # rows whose squares approach binary32's underflow: infinite bound terms
+    # (every pair of such a row goes to the direct formula)
+    tiny = (np.abs(X).max(axis=1) > 0) & (onx ** 2 < 2.0 ** -100)
+    assert np.all(np.isinf(st[tiny, 2])) and np.all(np.isinf(st[tiny, 3]))
+    ok = ~tiny
     for col, ref in ((1, onx), (2, onq), (3, onr)):
-        assert np.all(st[:, col] >= ref * (1 - 2.0 ** -40)), col
-        assert np.all(st[:, col] <= ref * (1 + 2.0 ** -11) + 1e-37), col
+        assert np.all(st[ok, col] >= ref[ok] * (1 - 2.0 ** -40)), col
+        assert np.all(st[ok, col] <= ref[ok] * (1 + 2.0 ** -11) + 1e-37), col
 
 
 # ------------------------------------------- empty clusters on the mixed path
@@ -508,3 +513,43 @@ def test_distances_queue_overflow_scans(ctx):
     D = D.cpu().numpy().astype(np.float64)
     assert nf == 300 * 300
     np.testing.assert_allclose(D, oracle.dist_direct(X, C), rtol=2 ** -23, atol=1e-38)
+
+
+def test_empty_farthest_many_clusters_at_scale(ctx):
+    """64 empty clusters at n = 4e6: the rows of largest min_dist (ties to
+    the lowest index: min_dist on a coarse grid makes many ties) in one
+    cooperative radix selection, as the oracle's ordered walk picks them, in
+    well under a millisecond more than keeping the old centres."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = 4_000_000, 8, 256
+    r = np.random.default_rng(65)
+    X = r.normal(size=(n, d)).astype(np.float32)
+    lab = r.integers(0, k, size=n).astype(np.int32)
+    lab[lab % 4 == 1] -= 1  # clusters 1, 5, 9, ...: 64 empty
+    md = np.round(r.random(n) * 1e5) / 1e5
+    C = r.normal(size=(k, d)).astype(np.float32)
+    Xd, labd, Cd, mdd = _dev(X), _dev(lab), _dev(C), _dev(md)
+    pf, pk = pkg.params("fp64", empty="farthest"), pkg.params("fp64", empty="keep")
+    for p in (pf, pk):
+        ctx.update_centroids(Xd, labd, Cd, p, min_dist=mdd, want_shift=False)
+    torch.cuda.synchronize()
+
+    def timed(p):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            ctx.update_centroids(Xd, labd, Cd, p, min_dist=mdd, want_shift=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    extra_ms = timed(pf) - timed(pk)
+    Cn, cnt, _ = ctx.update_centroids(Xd, labd, Cd, pf, min_dist=mdd)
+    oC, ocnt, _ = oracle.update(X, lab, C, 1, md)
+    assert np.array_equal(cnt.cpu().numpy(), ocnt)
+    empty = np.nonzero(ocnt == 0)[0]
+    assert empty.size == 64
+    Cn = Cn.cpu().numpy()
+    np.testing.assert_array_equal(Cn[empty], oC[empty])  # the same rows, in the same order
+    np.testing.assert_allclose(Cn, oC, rtol=2 ** -22, atol=1e-30)
+    assert extra_ms < 1.0, extra_ms
