@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
     for (int64_t pi = gid; pi < np; pi += ngroups) {
         const int2 pr = nxt;
         if (pi + ngroups < np) nxt = pairs[pi + ngroups];  // the next pair's index, ahead of its use
+        if (pr.x < 0) continue;  // a slot of a row that did not fit (the group's eight lanes alike)
         float acc = 0.0f;
         if (NV > 0) {
             const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)pr.x * d);
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
             }
             // the next pair's point row on its way to L2 while this one is
             // evaluated (rows of 512 bytes or more: measured to pay off there)
-            if (d >= 128 && sl == 0 && pi + ngroups < np && nxt.x != pr.x)
+            if (d >= 128 && sl == 0 && pi + ngroups < np && nxt.x >= 0 && nxt.x != pr.x)
                 prefetch_l2_bulk(X + (int64_t)nxt.x * d, (uint32_t)d * 4u);
 #pragma unroll
             for (int u = 0; u < NVV; u++) {
@@ -168,6 +169,11 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
         const int64_t off0 = (int64_t)bbase + wpre + incl - c;
         const bool fits = off0 + c <= cap;
         if (valid) {
+            if (!full && !fits) {
+                // reserved but past the capacity: the part of the range below the
+                // capacity is marked empty (row -1), so the evaluation skips it
+                for (int64_t t = off0; t < off0 + c && t < cap; t++) pairs[t] = make_int2(-1, 0);
+            }
             if (!full && fits) {
                 int w = 0;
 #pragma unroll
