@@ -135,6 +135,25 @@ km_status km_workspace_size(const km_ctx* ctx, int64_t n, int d, int k, const km
 km_status km_quantize(km_ctx* ctx, const float* X, int64_t n, int d, int32_t low, void* Xq, float* stats,
                       float* scale, void* stream);
 
+/* Which low format pays for this data (no counterpart in the paper, which
+ * fixes the format per experiment).  The cost of the screening path grows
+ * with the candidates it keeps per row: the centres whose d^ lies within
+ * 2 B_max of the row minimum, B the error bound behind the reliability test
+ * (Theorem 4.2 + Eq. (quantis-convert-error)), and a row whose candidates
+ * overflow its list is recomputed over all centres.  On a strided sample of
+ * 2048 rows this call counts, from fp32 direct distances, the candidates
+ * each row would keep under BF16 and under E4M3 (per-row scales) and the
+ * share of rows above one list's capacity, and returns *low_host = KM_E4M3
+ * when d >= 16, its predicted overflow share is at most max_overflow_share
+ * and it keeps at most two candidates per row more than BF16; else KM_BF16.
+ * stats_host (nullable, host, 4 doubles): BF16 mean candidates per row and
+ * overflow share, then the same for E4M3 (+inf and 1 when d < 16).  ws: as
+ * km_workspace_size.  Synchronises `stream`.  KM_EUNSUPPORTED where no
+ * tensor-core path exists (k > 65535, d too large for the BF16 tiles). */
+km_status km_choose_low(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
+                        double max_overflow_share, int32_t* low_host, double* stats_host, void* ws, size_t ws_bytes,
+                        void* stream);
+
 /* Alg. 2 for all pairs (Section 4.3; the distance-matrix experiments of
  * Section 6.1).  D (n x k fp32, row-major) receives, per pair, the expanded
  * low-precision value where the reliability test passes and the binary64

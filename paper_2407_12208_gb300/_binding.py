@@ -28,7 +28,7 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
-           "km_lloyd_step_host", "km_selftest_timeout", "km_quantize"]
+           "km_lloyd_step_host", "km_selftest_timeout", "km_quantize", "km_choose_low"]
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
                                            sz, vp]
         lib.km_selftest_timeout.argtypes = [vp, vp, sz, vp]
         lib.km_quantize.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
+        lib.km_choose_low.argtypes = [vp, vp, i64, vp, i32, i32, c.c_double, c.POINTER(c.c_int32), vp, vp, sz, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -216,6 +217,21 @@ class Context:
         self._check(self.lib.km_quantize(self.h, _ptr(X), n, d, lowv, _ptr(Xq), _ptr(stats), _ptr(scale),
                                          _stream(stream)))
         return Xq, stats, scale
+
+    def choose_low(self, X, C, max_overflow_share=0.01, ws=None, stream=None):
+        """km_choose_low: (the chosen low format's name, {bf16/e4m3: mean
+        candidates per row, predicted overflow share})."""
+        import numpy as np
+        n, d = X.shape
+        k = C.shape[0]
+        ws = ws if ws is not None else self.workspace(n, d, k, params("bf16"))
+        low = ctypes.c_int32(0)
+        st = np.zeros(4, dtype=np.float64)
+        self._check(self.lib.km_choose_low(self.h, _ptr(X), n, _ptr(C), k, d, float(max_overflow_share),
+                                           ctypes.byref(low), st.ctypes.data_as(ctypes.c_void_p), _ptr(ws), ws.numel(),
+                                           _stream(stream)))
+        name = {v: kk for kk, v in LOW_NAMES.items()}[low.value]
+        return name, {"bf16": (float(st[0]), float(st[1])), "e4m3": (float(st[2]), float(st[3]))}
 
     def assign_static(self, X, C, labels, min_dist, stream=None):
         """km_assign_static: the fp32 direct assignment with the library's

@@ -492,6 +492,57 @@ km_status km_quantize(km_ctx* ctx, const float* X, int64_t n, int d, int32_t low
     return KM_OK;
 }
 
+km_status km_choose_low(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
+                        double max_overflow_share, int32_t* low_host, double* stats_host, void* ws, size_t ws_bytes,
+                        void* stream) {
+    km_status s = check_common(ctx, X, n, C, k, d);
+    if (s != KM_OK) return s;
+    if (!low_host || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
+    if (!(max_overflow_share >= 0.0 && max_overflow_share <= 1.0))
+        return fail(ctx, KM_EINVAL, "max_overflow_share must lie in [0, 1]");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    if (k > 65535 || tc_smem_bytes(1, d, 1) == 0)
+        return fail(ctx, KM_EUNSUPPORTED, "no tensor-core path for d=%d, k=%d", d, k);
+    constexpr int kSample = 2048;
+    Carve cv{(char*)ws};
+    unsigned long long* acc = cv.take<unsigned long long>(4);
+    ColMax* colmax = cv.take<ColMax>(1);
+    void* Cq = cv.take<char>((size_t)k * ldq_of(1, d) * 2);
+    float4* cstat = cv.take<float4>((size_t)k);
+    float* cscale = cv.take<float>((size_t)k);
+    float* qpad = cv.take<float>((size_t)kpad_of(k));
+    float* spad = cv.take<float>((size_t)kpad_of(k));
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), st));
+    const int fmts[2] = {1, 2};  // bf16, E4M3
+    for (int f = 0; f < 2; f++) {
+        const int fmt = fmts[f];
+        if (fmt == 2 && d < 16) continue;
+        km_params q;
+        km_default_params(&q);
+        q.low = fmt == 2 ? KM_E4M3 : KM_BF16;
+        KL(1, launch_quantize(C, k, d, fmt, ldq_of(fmt, d), Cq, cstat, cscale, st));
+        KL(1, launch_colmax(cstat, k, fmt == 2 ? cscale : nullptr, colmax, qpad, spad, kpad_of(k), st));
+        KL(1, launch_predict_candidates(X, n, d, C, k, fmt, colmax, make_tp(&q, d), kSample, acc + 2 * f,
+                                        ctx->num_sms, st));
+    }
+    unsigned long long h[4];
+    CK(cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double ns = (double)std::min<int64_t>(kSample, n);
+    double stats[4] = {h[0] / ns, h[1] / ns, INFINITY, 1.0};
+    if (d >= 16) {
+        stats[2] = h[2] / ns;
+        stats[3] = h[3] / ns;
+    }
+    *low_host = (d >= 16 && stats[3] <= max_overflow_share && stats[2] <= stats[0] + 2.0) ? KM_E4M3 : KM_BF16;
+    if (stats_host)
+        for (int i = 0; i < 4; i++) stats_host[i] = stats[i];
+    return KM_OK;
+}
+
 km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
                     int32_t* labels, double* min_dist, uint64_t* n_flagged_host, void* ws, size_t ws_bytes,
                     void* stream) {

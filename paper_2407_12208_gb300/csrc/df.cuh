@@ -29,6 +29,16 @@ struct DF {
     float hi, lo;
 };
 
+// a - b on two coordinates at once (sub.rn.f32x2: each half rounded as a
+// scalar subtraction)
+KM_DEV float2 fsub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const float2*>(&r);
+}
+
 // x - c as t + tl, and the square as (p, q) with p + q = (x - c)^2 (1 + O(u^2)).
 KM_DEV void df_sq_diff(float x, float c, float& p, float& q) {
     const float t = __fsub_rn(x, c);
@@ -42,11 +52,11 @@ KM_DEV void df_sq_diff(float x, float c, float& p, float& q) {
 // Two coordinates at once (two per packed instruction, each half rounded as
 // its scalar counterpart above).
 KM_DEV void df_sq_diff2(float2 x, float2 c, float2& p, float2& q) {
-    const float2 nc = make_float2(-c.x, -c.y);
-    const float2 t = __fadd2_rn(x, nc);
-    const float2 bb = __fadd2_rn(t, make_float2(-x.x, -x.y));
-    const float2 u = __fadd2_rn(t, make_float2(-bb.x, -bb.y));
-    const float2 tl = __fadd2_rn(__fadd2_rn(x, make_float2(-u.x, -u.y)), __fadd2_rn(nc, make_float2(-bb.x, -bb.y)));
+    const float2 t = fsub2(x, c);
+    const float2 bb = fsub2(t, x);
+    const float2 u = fsub2(t, bb);
+    // (x - u) + (-c - bb) = (x - u) - (c + bb)
+    const float2 tl = fsub2(fsub2(x, u), __fadd2_rn(c, bb));
     p = __fmul2_rn(t, t);
     const float2 pe = __ffma2_rn(t, t, make_float2(-p.x, -p.y));
     q = __ffma2_rn(__fadd2_rn(t, t), tl, pe);
@@ -76,9 +86,9 @@ KM_DEV DF df_chunk(float4 x, float4 c) {
     df_sq_diff2(make_float2(x.z, x.w), make_float2(c.z, c.w), p23, q23);
     // A = sq0 + sq2 and B = sq1 + sq3 in one packed TwoSum
     const float2 s = __fadd2_rn(p01, p23);
-    const float2 bb = __fadd2_rn(s, make_float2(-p01.x, -p01.y));
-    const float2 v = __fadd2_rn(s, make_float2(-bb.x, -bb.y));
-    const float2 e = __fadd2_rn(__fadd2_rn(p01, make_float2(-v.x, -v.y)), __fadd2_rn(p23, make_float2(-bb.x, -bb.y)));
+    const float2 bb = fsub2(s, p01);
+    const float2 v = fsub2(s, bb);
+    const float2 e = __fadd2_rn(fsub2(p01, v), fsub2(p23, bb));
     const float2 lo = __fadd2_rn(e, __fadd2_rn(q01, q23));
     return df_combine(DF{s.x, lo.x}, DF{s.y, lo.y});
 }
@@ -135,26 +145,43 @@ KM_DEV DF df_rows(DF (&v)[R], int cl, int& row) {
     return v[0];
 }
 
-KM_DEV double df_value(DF v) { return (double)v.hi + (double)v.lo; }
+// binary32 -> binary64 by moving bits (exact for zeros and normal numbers);
+// GB300 runs the conversion instruction on its narrow FP64 pipe, so only
+// subnormals (and non-finite values) take it.
+KM_DEV double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+KM_DEV double df_value(DF v) { return f32_to_f64(v.hi) + f32_to_f64(v.lo); }
 
 // A whole row of D <= 8 coordinates in one thread: chunk 0 and (D > 4) chunk 1
 // combined -- what the butterfly over the eight lanes of such a row gives,
 // since the other six lanes' chunks are padding.
+// The centre as two float4 (c4[1] unused for D <= 4); coordinates past D
+// must be zero in both.
+template <int D>
+KM_DEV DF df_small4(const float (&x)[D], float4 c0, float4 c1) {
+    static_assert(D >= 1 && D <= 8, "rows of at most 8 coordinates");
+    float xa[8];
+#pragma unroll
+    for (int l = 0; l < 8; l++) xa[l] = l < D ? x[l] : 0.0f;
+    const DF h0 = df_chunk(make_float4(xa[0], xa[1], xa[2], xa[3]), c0);
+    if constexpr (D <= 4) {
+        return h0;
+    } else {
+        return df_combine(h0, df_chunk(make_float4(xa[4], xa[5], xa[6], xa[7]), c1));
+    }
+}
 template <int D>
 KM_DEV DF df_small(const float (&x)[D], const float* c) {
-    static_assert(D >= 1 && D <= 8, "rows of at most 8 coordinates");
-    float xa[8], ca[8];
+    float ca[8];
 #pragma unroll
-    for (int l = 0; l < 8; l++) {
-        xa[l] = l < D ? x[l] : 0.0f;
-        ca[l] = l < D ? c[l] : 0.0f;
-    }
-    const DF c0 = df_chunk(make_float4(xa[0], xa[1], xa[2], xa[3]), make_float4(ca[0], ca[1], ca[2], ca[3]));
-    if constexpr (D <= 4) {
-        return c0;
-    } else {
-        return df_combine(c0, df_chunk(make_float4(xa[4], xa[5], xa[6], xa[7]), make_float4(ca[4], ca[5], ca[6], ca[7])));
-    }
+    for (int l = 0; l < 8; l++) ca[l] = l < D ? c[l] : 0.0f;
+    return df_small4<D>(x, make_float4(ca[0], ca[1], ca[2], ca[3]), make_float4(ca[4], ca[5], ca[6], ca[7]));
 }
 
 // Chunk geometry of a row of d coordinates: d4 = ceil(d / 4) chunks over LPR

@@ -82,6 +82,13 @@ cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, 
 cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, float* spad,
                           int kpad, cudaStream_t st);
 
+// candidates per sampled row under the format's certification window (the
+// choice of the low format): acc[0] += candidates, acc[1] += rows above one
+// list's capacity; nsample rows at a stride of n / nsample
+cudaError_t launch_predict_candidates(const float* X, int64_t n, int d, const float* C, int k, int fmt,
+                                      const ColMax* cmx, const TestParams& tp, int nsample,
+                                      unsigned long long* acc, int num_sms, cudaStream_t st);
+
 // direct-formula assignment (thread per row).  acc64: binary64 accumulation
 // (the plain FP64 path) else fp32 with certification; rows = all n, or the
 // device list row_list[0 .. *row_count).  Uncertified fp32 rows are appended

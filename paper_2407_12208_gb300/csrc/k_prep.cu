@@ -481,6 +481,112 @@ cudaError_t launch_quantize(const float* A, int64_t m, int d, int fmt, int ldq, 
     return cudaGetLastError();
 }
 
+// ---- candidate-count prediction (the choice of the low format) ----------
+// For a sample of rows: the fp32 direct distances to every centre, the row's
+// certification window W = 2 B_max of the format (B_max from the row's
+// quantisation statistics and the column maxima of the centres' ones, as the
+// screening kernel forms it), and the number of centres within W of the
+// row's minimum: the candidates the screen keeps for that row.  A row whose
+// candidates exceed one epilogue group's list (TC_LIST entries) is counted
+// as an overflow.  acc[0] += candidates, acc[1] += overflowing rows.
+__global__ void __launch_bounds__(256) k_predict_candidates(const float* __restrict__ X, int64_t n, int d,
+                                                            const float* __restrict__ C, int k, int fmt,
+                                                            const ColMax* __restrict__ cmx, TestParams tp, int64_t stride,
+                                                            int nsample, unsigned long long* acc) {
+    extern __shared__ float xs[];
+    __shared__ float red[8];
+    __shared__ float sh_stat[4];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const ColMax cm = *cmx;
+    for (int sidx = blockIdx.x; sidx < nsample; sidx += gridDim.x) {
+        const int64_t i = (int64_t)sidx * stride;
+        __syncthreads();
+        for (int l = t; l < d; l += blockDim.x) xs[l] = X[i * d + l];
+        __syncthreads();
+        // the row's statistics in the format (warp 0): ||x||^2, ||x~||, ||x~ - x||
+        if (w == 0) {
+            float amax = 0.0f;
+            for (int l = lane; l < d; l += 32) amax = fmaxf(amax, fabsf(xs[l]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            const float s = fmt == 2 ? e4m3_row_scale(amax) : 1.0f;
+            float p = 0.0f, q2 = 0.0f, r2 = 0.0f;
+            for (int l = lane; l < d; l += 32) {
+                const float v = xs[l];
+                const float qs = quant_val(v / s, fmt) * s;
+                p = fmaf(v, v, p);
+                q2 = fmaf(qs, qs, q2);
+                r2 = fmaf(qs - v, qs - v, r2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                p += __shfl_xor_sync(0xffffffffu, p, o);
+                q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+                r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+            }
+            if (lane == 0) {
+                sh_stat[0] = p;
+                sh_stat[1] = sqrtf(q2) * kNormInflate;
+                sh_stat[2] = sqrtf(r2) * kNormInflate;
+            }
+        }
+        // fp32 direct distances: the row minimum first
+        float mn = INFINITY;
+        for (int j = t; j < k; j += blockDim.x) {
+            const float* c = C + (int64_t)j * d;
+            float acc2 = 0.0f;
+            for (int l = 0; l < d; l++) {
+                const float u = xs[l] - c[l];
+                acc2 = fmaf(u, u, acc2);
+            }
+            mn = fminf(mn, acc2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        if (lane == 0) red[w] = mn;
+        __syncthreads();
+        mn = red[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) mn = fminf(mn, red[q]);
+        const float p = sh_stat[0], nxq = sh_stat[1], nrx = sh_stat[2];
+        const float bmax = (2.0f * nrx * cm.nc + 2.0f * nxq * cm.nrc + tp.kacc * nxq * cm.ncq + tp.kn * (p + cm.q)) * tp.bsafe;
+        const float lim = mn + 2.0f * bmax * 1.001f;
+        unsigned cntc = 0;
+        for (int j = t; j < k; j += blockDim.x) {
+            const float* c = C + (int64_t)j * d;
+            float acc2 = 0.0f;
+            for (int l = 0; l < d; l++) {
+                const float u = xs[l] - c[l];
+                acc2 = fmaf(u, u, acc2);
+            }
+            cntc += acc2 <= lim ? 1u : 0u;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cntc += __shfl_xor_sync(0xffffffffu, cntc, o);
+        __syncthreads();
+        if (lane == 0) reinterpret_cast<unsigned*>(red)[w] = cntc;
+        __syncthreads();
+        if (t == 0) {
+            unsigned tot = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); q++) tot += reinterpret_cast<unsigned*>(red)[q];
+            atomicAdd(&acc[0], (unsigned long long)tot);
+            if (tot > (unsigned)TC_LIST) atomicAdd(&acc[1], 1ull);
+        }
+    }
+}
+
+cudaError_t launch_predict_candidates(const float* X, int64_t n, int d, const float* C, int k, int fmt,
+                                      const ColMax* cmx, const TestParams& tp, int nsample,
+                                      unsigned long long* acc, int num_sms, cudaStream_t st) {
+    const int64_t stride = std::max<int64_t>(1, n / nsample);
+    const int ns = (int)std::min<int64_t>(nsample, (n + stride - 1) / stride);
+    const size_t sm = (size_t)d * sizeof(float);
+    cudaError_t e = allow_max_smem(k_predict_candidates);
+    if (e != cudaSuccess) return e;
+    k_predict_candidates<<<(unsigned)std::max(1, std::min(ns, num_sms * 4)), 256, sm, st>>>(X, n, d, C, k, fmt, cmx, tp,
+                                                                                           stride, ns, acc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_colmax(const float4* cstat, int k, const float* cscale, ColMax* out, float* qpad, float* spad,
                           int kpad, cudaStream_t st) {
     k_colmax<<<1, 1024, 0, st>>>(cstat, k, cscale, out, qpad, spad, kpad);

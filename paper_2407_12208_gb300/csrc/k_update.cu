@@ -420,9 +420,14 @@ __global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X
     const int kd = k * D;
     unsigned* a = acc_sm + (size_t)wib * (3 * kd + k);
     unsigned* cntw = a + 3 * kd;
-    float* Cs = reinterpret_cast<float*>(acc_sm + (size_t)(blockDim.x >> 5) * (3 * kd + k));
+    // C with rows of 8 floats (zero past D), 16-byte aligned: two vector reads per row
+    const size_t coff = (((size_t)(blockDim.x >> 5) * (3 * kd + k)) + 3) & ~(size_t)3;
+    float4* Cs = reinterpret_cast<float4*>(acc_sm + coff);
     if (WD) {
-        for (int e = threadIdx.x; e < kd; e += blockDim.x) Cs[e] = C[e];
+        for (int e = threadIdx.x; e < k * 8; e += blockDim.x) {
+            const int j = e >> 3, l = e & 7;
+            reinterpret_cast<float*>(Cs)[e] = l < D ? C[j * D + l] : 0.0f;
+        }
         __syncthreads();
     }
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X
             float xr[D];
 #pragma unroll
             for (int l = 0; l < D; l++) xr[l] = valid ? X[i * D + l] : 0.0f;
-            if (WD && valid) md[i] = df_value(df_small<D>(xr, Cs + j * D));
+            if (WD && valid) md[i] = df_value(df_small4<D>(xr, Cs[2 * j], D > 4 ? Cs[2 * j + 1] : make_float4(0.f, 0.f, 0.f, 0.f)));
             unsigned v[3 * D + 1];  // true (unbiased) parts modulo 2^32, then the row count
 #pragma unroll
             for (int l = 0; l < D; l++) {
@@ -869,8 +874,8 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         // small d: rows in order, per-warp shared accumulators (+ C for the distances)
         e = cudaMemsetAsync(counts, 0, sizeof(long long) * (size_t)k, st);
         if (e != cudaSuccess) return e;
-        const size_t sm = (size_t)8 * (3 * (size_t)k * d + k) * sizeof(unsigned) +
-                          (want_wd ? (size_t)k * d * sizeof(float) : 0);
+        const size_t sm = (((size_t)8 * (3 * (size_t)k * d + k) + 3) & ~(size_t)3) * sizeof(unsigned) +
+                          (want_wd ? (size_t)k * 8 * sizeof(float) : 0);
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * 8, (n + 8 * AS_CHUNK - 1) / (8 * AS_CHUNK)));
         switch (d) {
 #define KM_ACC(DD)                                                                                                  \

@@ -553,3 +553,57 @@ def test_empty_farthest_many_clusters_at_scale(ctx):
     np.testing.assert_array_equal(Cn[empty], oC[empty])  # the same rows, in the same order
     np.testing.assert_allclose(Cn, oC, rtol=2 ** -22, atol=1e-30)
     assert extra_ms < 1.0, extra_ms
+
+
+# --------------------------------------- config-3 trajectories at full size
+@pytest.mark.parametrize("low", ["fp16", "e4m3"])
+def test_mixture_lloyd_full_size_teacher_forced(low):
+    """The mixed-precision Lloyd iteration at its full size (Gaussian mixture
+    n = 4e6, d = 64, k = 256) for 50 iterations, teacher-forced: every GPU
+    iteration starts from the oracle's centres; labels and min_dist on 2000
+    sampled rows against the oracle's assignment, counts and centres against
+    the oracle's update (Eq. (center)) of the GPU's labels, every iteration."""
+    import paper_2407_12208_gb300 as pkg
+    c = pkg.Context(0)
+    n, d, k = 4_000_000, 64, 256
+    X, C0 = workloads.gaussian_mixture(n, d, k, seed=15)
+    Xd = _dev(X)
+    p = pkg.params(low, empty="farthest")
+    rows = np.sort(np.random.default_rng(17).choice(n, 2000, replace=False))
+    C = C0.copy()
+    sse = []
+    for it in range(50):
+        lab, md, Cn, cnt, _ = c.lloyd_step(Xd, _dev(C), p)
+        torch.cuda.synchronize()
+        lab, md, Cn, cnt = lab.cpu().numpy(), md.cpu().numpy(), Cn.cpu().numpy(), cnt.cpu().numpy()
+        check_assign(lab[rows], md[rows], X[rows], C, oracle, RTOL_MD)
+        oC, ocnt, _ = oracle.update(X, lab, C, 1, md)
+        assert np.array_equal(cnt, ocnt), it
+        np.testing.assert_allclose(Cn, oC, rtol=2 ** -22, atol=1e-30)
+        sse.append(float(md.sum()))
+        C = oC
+    # SSE never increases along the (teacher-forced) iteration, Lemma 2.1
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(sse, sse[1:]))
+
+
+# ------------------------------------------------- choosing the low format
+def test_choose_low_predicts_list_overflow(ctx):
+    """km_choose_low: on uniform data E4M3's error bound exceeds the spread of
+    the distances (every row's candidates overflow its list) and BF16 is
+    chosen; on well-separated clusters E4M3 keeps one candidate per row and is
+    chosen.  The predicted overflow share is what an E4M3 assignment of the
+    same data then measures, within 0.1."""
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.uniform_pairs(20000, 128, 256, seed=66)
+    X2, C2 = workloads.gaussian_mixture(20000, 128, 64, seed=67, std_lo=0.01, std_hi=0.02)
+    for Xh, Ch, expect in ((X, C, "bf16"), (X2, C2, "e4m3")):
+        Xd, Cd = _dev(Xh), _dev(Ch)
+        low, st = ctx.choose_low(Xd, Cd, max_overflow_share=0.01)
+        assert low == expect, (low, st)
+        ctx.assign(Xd, Cd, pkg.params("e4m3"))
+        measured = ctx.stats()["overflow_rows"] / Xh.shape[0]
+        assert abs(measured - st["e4m3"][1]) <= 0.1, (measured, st)
+        assert st["bf16"][1] <= 0.01 and st["bf16"][0] >= 1.0
+    with pytest.raises(pkg.KmError) as ei:
+        ctx.choose_low(_dev(X), _dev(C), max_overflow_share=2.0)
+    assert ei.value.status == pkg._binding.KM_EINVAL
