@@ -11,7 +11,9 @@ Prints one JSON line (rank 0): the device-resident step rate (`value`), the
 screening kernel against the measured BF16 roofline (`roofline`), the same
 step end to end from pinned host buffers through km_lloyd_step_host (`e2e`),
 the oracle on the host cores (`cpu_baseline`), the plain FP64 path on a row
-sample (`fp64_path`), the served stream's latencies (`serving`), SM clocks
+sample (`fp64_path`), the served stream's latencies (`serving`), the
+distance-matrix precision modes in the structure of the paper's Tables 6.1 /
+6.2 (`table6`), SM clocks
 sampled during the timed region (`clocks`) and the library's own launch count
 (`gpu_launches`).  `--impl reference` times the CPU oracle instead (on a
 bounded sample of the same workload).  Multi-GPU (torchrun): independent
@@ -356,6 +358,9 @@ def run_ours(args):
     serving = None
     if rank == 0 and not args.only_step and not args.no_serving:
         serving = serving_leg(args, local)
+    table6 = None
+    if rank == 0 and not args.only_step and not args.no_table6:
+        table6 = table6_leg(args, local)
 
     if rank == 0:
         line = {
@@ -367,7 +372,7 @@ def run_ours(args):
                        "step": "km_lloyd_step: quantise X (+ max |x|), screen, refine, certified argmin, min_dist, exact centre update",
                        "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "fp64_path": fp64, "serving": serving,
+            "fp64_path": fp64, "serving": serving, "table6": table6,
             "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},
             "eta": stats["flagged"] / max(stats["pairs"], 1),
             "assign_stats": {kk: stats[kk] for kk in ("fp32_evals", "fp64_evals", "ambiguous_rows", "overflow_rows")},
@@ -376,6 +381,53 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+TABLE6_MODES = [
+    # (label, low, test, fallback): the rows of Table 6.1 this library provides
+    ("FP16->FP64", "fp16", "tc", "fp64"), ("FP16->FP32", "fp16", "tc", "fp32"), ("FP16->FP16", "fp16", "tc", "low"),
+    ("BF16->FP64", "bf16", "tc", "fp64"), ("BF16->FP32", "bf16", "tc", "fp32"), ("BF16->BF16", "bf16", "tc", "low"),
+    ("FP16->FP64 (Alg. 2 test)", "fp16", "paper", "fp64"), ("BF16->FP64 (Alg. 2 test)", "bf16", "paper", "fp64"),
+    ("FP32->FP64 (Alg. 2)", "fp32x", "paper", "fp64"), ("FP32->FP32 (Alg. 2)", "fp32x", "paper", "fp32"),
+    ("uniform FP16", "fp16", "off", "fp64"), ("uniform BF16", "bf16", "off", "fp64"),
+    ("FP32 direct", "fp32", "tc", "fp64"), ("FP64 direct", "fp64", "tc", "fp64"),
+]
+
+
+def table6_leg(args, device: int) -> dict:
+    """Tables 6.1 / 6.2 of the paper, in structure: the 5000 x 5000 distance
+    matrix of r = 128 points (Gaussian rows; a fraction of the centres are
+    near-duplicates of the points, C = P + 1e-4 N(0, I), the rest fresh
+    rows), every precision mode of km_distances: device time (mean of 3
+    after one warm-up, CUDA events), the flagged share eta and the largest
+    relative error against the binary64 direct values."""
+    import torch
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import workloads
+    ctx = pkg.Context(device)
+    out = {}
+    for frac in (0.0, 0.1, 0.5, 1.0):
+        X, C = workloads.near_far(5000, 128, frac, seed=81)
+        Xd, Cd = torch.from_numpy(X).cuda(device), torch.from_numpy(C).cuda(device)
+        D64, _, _ = ctx.distances(Xd, Cd, pkg.params("fp64"))
+        D64 = D64.double()
+        rows = {}
+        for label, low, test, fb in TABLE6_MODES:
+            p = pkg.params(low, test, fallback=fb)
+            ctx.distances(Xd, Cd, p)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                D, bits, nf = ctx.distances(Xd, Cd, p)
+            e1.record()
+            torch.cuda.synchronize()
+            ref = D64.clamp_min(1e-300)
+            rel = float(((D.double() - D64).abs() / ref).max())
+            rows[label] = {"ms": e0.elapsed_time(e1) / 3, "eta": nf / 25e6, "max_rel_err": rel}
+        out["near_%d%%" % round(100 * frac)] = rows
+    ctx.close()
+    return {"n": 5000, "k": 5000, "r": 128, "near_eps": 1e-4, "rho": 5.0, "c_A": 2.0, "modes": out}
 
 
 def serving_leg(args, device: int) -> dict:
@@ -388,13 +440,16 @@ def serving_leg(args, device: int) -> dict:
     import numpy as np
     import paper_2407_12208_gb300 as pkg
     from paper_2407_12208_gb300 import workloads
+    import torch
     specs = workloads.serving_jobs(args.serve_jobs, seed=2024, n_lo=1e3, n_hi=1e5)
+    ctx = pkg.Context(device, arena_bytes=80 << 30)
     data = []
     for i, sp in enumerate(specs):
         X, C = workloads.gaussian_mixture(sp["n"], sp["d"], sp["k"], seed=3000 + i)
-        low = "fp32" if sp["d"] <= 8 else ("bf16" if sp["d"] < 64 else "e4m3")
+        # small d: the direct path; else the library's rule (km_choose_low)
+        low = "fp32" if sp["d"] <= 8 else ctx.choose_low(torch.from_numpy(X).cuda(device),
+                                                          torch.from_numpy(C).cuda(device))[0]
         data.append((X, C, pkg.params(low, max_iter=25, tau=0.0)))
-    ctx = pkg.Context(device, arena_bytes=80 << 30)
 
     def run(arrivals):
         ids, t0 = [], time.perf_counter()
@@ -489,6 +544,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="rows (profiling a smaller case of the same kernels)")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--no-table6", action="store_true", help="skip the distance-matrix precision leg")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--only-step", action="store_true",

@@ -62,8 +62,21 @@ typedef enum {
     KM_FP32_DIRECT = 1,   /* Eq. (dist-direct) in fp32, certified, fp64 where ambiguous */
     KM_FP16 = 2,          /* binary16 cross term (Table 1.1), FP32 accumulation */
     KM_BF16 = 3,          /* bfloat16 cross term (Table 1.1), FP32 accumulation */
-    KM_E4M3 = 4           /* FP8 E4M3 cross term with power-of-two per-row scales */
+    KM_E4M3 = 4,          /* FP8 E4M3 cross term with power-of-two per-row scales */
+    KM_FP32 = 5           /* km_distances only: Alg. 2 with binary32 as the low precision, on CUDA
+                             cores, every operation rounded in the order Alg. 2 states it */
 } km_low;
+
+/* Precision of the fallback (Eq. (fallback-rule)): the direct formula that
+ * km_distances evaluates for the pairs failing the reliability test.  The
+ * assignment calls always certify their argmin in fp32 and binary64 and take
+ * only KM_FB_FP64. */
+typedef enum {
+    KM_FB_FP64 = 0,       /* binary64 (Alg. 2) */
+    KM_FB_FP32 = 1,       /* binary32 */
+    KM_FB_LOW = 2         /* the low format itself, every operation rounded to it (the same-precision
+                             fallback of Section 4.2; fp16 / bf16, and binary32 for KM_FP32) */
+} km_fallback;
 
 /* Reliability test of Section 4.3. */
 typedef enum {
@@ -87,6 +100,7 @@ typedef struct {
     int32_t max_iter;     /* Lloyd iterations t_max (Alg. 1) */
     int32_t empty;        /* km_empty */
     double tau;           /* stop when max_j ||c_j^(t) - c_j^(t-1)|| < tau; tau <= 0 runs max_iter iterations */
+    int32_t fallback;     /* km_fallback (km_distances; default KM_FB_FP64) */
 } km_params;
 
 /* Counters of the last assign / distances / lloyd call on a context. */
@@ -100,7 +114,7 @@ typedef struct {
     double sse;               /* sum of min_dist of the last assignment (Eq. (sse)) */
 } km_stats;
 
-/* Fills the defaults: BF16, KM_TEST_TC, rho 5, c_A 2, max_iter 20, tau 0, FARTHEST. */
+/* Fills the defaults: BF16, KM_TEST_TC, rho 5, c_A 2, max_iter 20, tau 0, FARTHEST, KM_FB_FP64. */
 void km_default_params(km_params* p);
 
 /* Creates a context on `device`.  `arena` (device memory, caller-owned, may
@@ -156,11 +170,15 @@ km_status km_choose_low(km_ctx* ctx, const float* X, int64_t n, const float* C, 
 
 /* Alg. 2 for all pairs (Section 4.3; the distance-matrix experiments of
  * Section 6.1).  D (n x k fp32, row-major) receives, per pair, the expanded
- * low-precision value where the reliability test passes and the binary64
- * direct value (rounded to fp32, the working precision) where it fails.
- * flag_bits (nullable; ceil(n*k/32) words, bit (i*k+j) of the row-major
- * pair index) marks the pairs that fell back.  n_flagged_host (nullable,
- * host) receives the number of flagged pairs.  low must be FP16/BF16/E4M3. */
+ * low-precision value where the reliability test passes and the direct
+ * value in the fallback's precision (p->fallback; rounded to fp32, the
+ * working precision) where it fails.  flag_bits (nullable; ceil(n*k/32)
+ * words, bit (i*k+j) of the row-major pair index) marks the pairs that fell
+ * back.  n_flagged_host (nullable, host) receives the number of flagged
+ * pairs.  low: FP16/BF16/E4M3 (tensor cores, the cross term accumulated in
+ * fp32), KM_FP32 (Alg. 2 in binary32), or KM_FP64_DIRECT / KM_FP32_DIRECT
+ * (the direct formula for every pair in that precision, no test).
+ * KM_FB_LOW with E4M3 is KM_EUNSUPPORTED (no E4M3 arithmetic). */
 km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d,
                        const km_params* p, float* D, uint32_t* flag_bits,
                        uint64_t* n_flagged_host, void* ws, size_t ws_bytes, void* stream);

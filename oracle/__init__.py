@@ -72,6 +72,11 @@ def _load():
         lib.orc_mp_dist_paper.argtypes = [_f32p, _f32p, c.c_int, c.c_double, c.c_double, c.c_int,
                                           c.POINTER(c.c_double), c.POINTER(c.c_double),
                                           c.POINTER(c.c_double)]
+        lib.orc_dist_direct_fmt.restype = c.c_double
+        lib.orc_dist_direct_fmt.argtypes = [_f32p, _f32p, c.c_int, c.c_int]
+        lib.orc_mp_dist_fb.restype = c.c_int
+        lib.orc_mp_dist_fb.argtypes = [_f32p, _f32p, c.c_int, c.c_double, c.c_double, c.c_int, c.c_int,
+                                       c.POINTER(c.c_double), c.POINTER(c.c_double), c.POINTER(c.c_double)]
         lib.orc_tc_bound.restype = c.c_double
         lib.orc_tc_bound.argtypes = [c.c_double] * 7 + [c.c_int, c.c_int]
         lib.orc_row_quant_stats.restype = None
@@ -196,6 +201,25 @@ def mp_dist_paper(x, y, rho: float, fmt: int, c_A: float = 1.0):
     dd, dh, E = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     f = _load().orc_mp_dist_paper(x, y, x.size, float(rho), float(c_A), int(fmt),
                                   ctypes.byref(dd), ctypes.byref(dh), ctypes.byref(E))
+    if f < 0:
+        return None, None, None, None
+    return bool(f), dd.value, dh.value, E.value
+
+
+def dist_direct_fmt(x, y, fmt: int) -> float:
+    """Eq. (dist-direct) with every operation rounded to fmt (0 fp16, 1 bf16,
+    3 fp32, 4 fp64): the fallback of Section 4.2 in that precision."""
+    x, y = _f32(x), _f32(y)
+    return _load().orc_dist_direct_fmt(x, y, x.size, int(fmt))
+
+
+def mp_dist_fb(x, y, rho: float, fmt: int, fb_fmt: int, c_A: float = 1.0):
+    """Alg. 2 (every low-precision op rounded; fmt 3 = binary32) with the
+    fallback of Eq. (fallback-rule) in precision fb_fmt: (flag, d, dhat, E)."""
+    x, y = _f32(x), _f32(y)
+    dd, dh, E = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    f = _load().orc_mp_dist_fb(x, y, x.size, float(rho), float(c_A), int(fmt), int(fb_fmt),
+                               ctypes.byref(dd), ctypes.byref(dh), ctypes.byref(E))
     if f < 0:
         return None, None, None, None
     return bool(f), dd.value, dh.value, E.value

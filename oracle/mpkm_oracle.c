@@ -38,7 +38,7 @@
 /* ------------------------------------------------------------------------ */
 /* Table 1.1: floating-point formats.  fmt 0 = binary16, 1 = bfloat16,
  * 2 = FP8 E4M3 ("fn" variant: no infinities, largest finite 448; not in the
- * paper's table, t = 4 significand bits).  Rounding is to nearest, ties to
+ * paper's table, t = 4 significand bits), 3 = binary32.  Rounding is to nearest, ties to
  * even; fp16/bf16 overflow to infinity, E4M3 saturates to +-448 (the
  * behaviour of the hardware's satfinite conversion).                       */
 /* ------------------------------------------------------------------------ */
@@ -46,6 +46,7 @@ static void fmt_params(int fmt, int* t, int* emin, double* xmax, int* sat) {
     switch (fmt) {
     case 0: *t = 11; *emin = -14;  *xmax = 65504.0; *sat = 0; break;
     case 1: *t = 8;  *emin = -126; *xmax = ldexp(255.0, 120); *sat = 0; break;
+    case 3: *t = 24; *emin = -126; *xmax = ldexp(16777215.0, 104); *sat = 0; break;  /* binary32 */
     default: *t = 4; *emin = -6;   *xmax = 448.0; *sat = 1; break;
     }
 }
@@ -245,6 +246,9 @@ int orc_lloyd(const float* X, int64_t n, int d, int k, const float* C_init,
  * gamma^l_{r+2} is undefined ((r+2) u_l >= 1).  d_out receives the value
  * Alg. 2 returns; dhat_out and E_out the low-precision quantities.         */
 /* ------------------------------------------------------------------------ */
+int orc_mp_dist_paper(const float* x, const float* y, int r, double rho, double c_A, int fmt,
+                      double* d_out, double* dhat_out, double* E_out);
+
 static double lo_dot(const float* a, const float* b, int r, int fmt) {
     double s = 0.0;
     for (int l = 0; l < r; l++) {
@@ -254,6 +258,32 @@ static double lo_dot(const float* a, const float* b, int r, int fmt) {
         s = orc_round_to_format(s + prod, fmt);
     }
     return s;
+}
+
+/* Eq. (dist-direct) with every operation rounded to the format (Section
+ * 4.2's fallback in precision u_h, here u_h = u of fmt): the inputs rounded
+ * to it, then per coordinate t = fl(x~ - y~), s = fl(s + fl(t t)), in order.
+ * fmt 4 (binary64) is orc_dist_direct_pair.                                 */
+double orc_dist_direct_fmt(const float* x, const float* y, int r, int fmt) {
+    if (fmt == 4) return orc_dist_direct_pair(x, y, r);
+    double s = 0.0;
+    for (int l = 0; l < r; l++) {
+        double t = orc_round_to_format(orc_round_to_format((double)x[l], fmt) - orc_round_to_format((double)y[l], fmt), fmt);
+        s = orc_round_to_format(s + orc_round_to_format(t * t, fmt), fmt);
+    }
+    return s;
+}
+
+/* Alg. 2 with the fallback of Eq. (fallback-rule) in the precision fb_fmt
+ * (4 = binary64 as in Alg. 2, 3 = binary32, or fmt itself: the same-precision
+ * fallback).  Otherwise as orc_mp_dist_paper.                               */
+int orc_mp_dist_fb(const float* x, const float* y, int r, double rho, double c_A, int fmt, int fb_fmt,
+                   double* d_out, double* dhat_out, double* E_out) {
+    double d = 0.0;
+    int f = orc_mp_dist_paper(x, y, r, rho, c_A, fmt, &d, dhat_out, E_out);
+    if (f == 1) d = orc_dist_direct_fmt(x, y, r, fb_fmt);
+    if (d_out) *d_out = d;
+    return f;
 }
 
 int orc_mp_dist_paper(const float* x, const float* y, int r, double rho, double c_A, int fmt,

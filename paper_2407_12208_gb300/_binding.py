@@ -17,10 +17,13 @@ LIB_PATH = os.path.join(HERE, "libmpkm.so")
 KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ENOTREADY, KM_ECANCELLED, KM_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["KM_OK", "KM_EINVAL", "KM_ENOMEM", "KM_ECUDA", "KM_ETIMEOUT", "KM_ENOTREADY",
                 "KM_ECANCELLED", "KM_EUNSUPPORTED"]
-FP64_DIRECT, FP32_DIRECT, FP16, BF16, E4M3 = range(5)
+FP64_DIRECT, FP32_DIRECT, FP16, BF16, E4M3, FP32 = range(6)
 TEST_TC, TEST_PAPER, TEST_OFF = range(3)
 EMPTY_KEEP, EMPTY_FARTHEST = range(2)
-LOW_NAMES = {"fp64": FP64_DIRECT, "fp32": FP32_DIRECT, "fp16": FP16, "bf16": BF16, "e4m3": E4M3}
+FB_FP64, FB_FP32, FB_LOW = range(3)
+LOW_NAMES = {"fp64": FP64_DIRECT, "fp32": FP32_DIRECT, "fp16": FP16, "bf16": BF16, "e4m3": E4M3,
+             "fp32x": FP32}  # fp32x: Alg. 2 with binary32 as the low precision (km_distances)
+FALLBACK_NAMES = {"fp64": FB_FP64, "fp32": FB_FP32, "low": FB_LOW}
 TEST_NAMES = {"tc": TEST_TC, "paper": TEST_PAPER, "off": TEST_OFF}
 
 # Symbols declared in include/mpkm.h
@@ -42,7 +45,7 @@ class KmError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("low", ctypes.c_int32), ("test", ctypes.c_int32), ("rho", ctypes.c_double),
                 ("paper_factor", ctypes.c_double), ("max_iter", ctypes.c_int32), ("empty", ctypes.c_int32),
-                ("tau", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("fallback", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -117,7 +120,8 @@ def load(path: str = LIB_PATH):
         return lib
 
 
-def params(low="bf16", test="tc", rho=5.0, paper_factor=2.0, max_iter=20, empty="farthest", tau=0.0) -> Params:
+def params(low="bf16", test="tc", rho=5.0, paper_factor=2.0, max_iter=20, empty="farthest", tau=0.0,
+           fallback="fp64") -> Params:
     p = Params()
     load().km_default_params(ctypes.byref(p))
     p.low = LOW_NAMES[low] if isinstance(low, str) else int(low)
@@ -127,6 +131,7 @@ def params(low="bf16", test="tc", rho=5.0, paper_factor=2.0, max_iter=20, empty=
     p.max_iter = int(max_iter)
     p.empty = {"keep": EMPTY_KEEP, "farthest": EMPTY_FARTHEST}[empty] if isinstance(empty, str) else int(empty)
     p.tau = float(tau)
+    p.fallback = FALLBACK_NAMES[fallback] if isinstance(fallback, str) else int(fallback)
     return p
 
 

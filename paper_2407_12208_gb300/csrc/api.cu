@@ -143,6 +143,8 @@ struct AssignWs {
     int2* queue;
     int64_t qcap;
     unsigned long long* qlen;
+    float* dxx;   // matrix modes on CUDA cores: Alg. 2's d_xx per row, d_yy per centre
+    float* dyy;
 };
 
 // Flagged pairs the distance-matrix call queues for the binary64 patch: four
@@ -184,6 +186,12 @@ AssignWs carve_assign(Carve& cv, int64_t n, int d, int k, int low, bool distance
             w.queue = cv.take<int2>((size_t)w.qcap);
             w.qlen = cv.take<unsigned long long>(1);
         }
+    } else if (distances) {
+        w.dxx = cv.take<float>((size_t)n);
+        w.dyy = cv.take<float>((size_t)k);
+        w.qcap = flag_queue_cap(n, k);
+        w.queue = cv.take<int2>((size_t)w.qcap);
+        w.qlen = cv.take<unsigned long long>(1);
     }
     return w;
 }
@@ -252,11 +260,31 @@ LloydWs carve_lloyd(Carve& cv, int64_t n, int d, int k, int low, int max_iter) {
     return L;
 }
 
-km_status check_params(km_ctx* ctx, const km_params* p, int d, int k = 1) {
+km_status check_params(km_ctx* ctx, const km_params* p, int d, int k = 1, bool matrix = false) {
     if (!p) return fail(ctx, KM_EINVAL, "params is NULL");
-    if (p->low < KM_FP64_DIRECT || p->low > KM_E4M3) return fail(ctx, KM_EINVAL, "unknown low precision %d", p->low);
+    if (p->low < KM_FP64_DIRECT || p->low > KM_FP32) return fail(ctx, KM_EINVAL, "unknown low precision %d", p->low);
     if (p->test < KM_TEST_TC || p->test > KM_TEST_OFF) return fail(ctx, KM_EINVAL, "unknown test %d", p->test);
     if (p->empty != KM_EMPTY_KEEP && p->empty != KM_EMPTY_FARTHEST) return fail(ctx, KM_EINVAL, "unknown empty policy");
+    if (p->fallback < KM_FB_FP64 || p->fallback > KM_FB_LOW) return fail(ctx, KM_EINVAL, "unknown fallback %d", p->fallback);
+    if (!matrix) {
+        if (p->low == KM_FP32) return fail(ctx, KM_EUNSUPPORTED, "KM_FP32 is a distance-matrix mode (km_distances)");
+        if (p->fallback != KM_FB_FP64)
+            return fail(ctx, KM_EUNSUPPORTED, "the assignment certifies in fp32 and binary64: fallback must be KM_FB_FP64");
+    }
+    if (p->low == KM_FP32) {
+        if (p->test == KM_TEST_TC && !(p->rho > 1.0)) return fail(ctx, KM_EINVAL, "rho must exceed 1 for the tc test");
+        if (p->test == KM_TEST_PAPER && !(p->rho > 2.0))
+            return fail(ctx, KM_EINVAL, "rho must exceed 2 for the paper test (Eq. (quantis-reliability-test))");
+        if (p->test == KM_TEST_PAPER && !(p->paper_factor > 0.0)) return fail(ctx, KM_EINVAL, "paper_factor must be positive");
+        if (d > 1024) return fail(ctx, KM_EUNSUPPORTED, "KM_FP32 supports d <= 1024");
+        return KM_OK;
+    }
+    if (matrix && !is_tc(p->low)) {
+        if (d > 1024) return fail(ctx, KM_EUNSUPPORTED, "the direct distance matrix supports d <= 1024");
+        return KM_OK;
+    }
+    if (p->fallback == KM_FB_LOW && p->low == KM_E4M3)
+        return fail(ctx, KM_EUNSUPPORTED, "no same-precision fallback for E4M3 (no E4M3 arithmetic)");
     if (is_tc(p->low)) {
         if (p->test == KM_TEST_TC && !(p->rho > 1.0)) return fail(ctx, KM_EINVAL, "rho must exceed 1 for the tc test");
         if (p->test == KM_TEST_PAPER) {
@@ -433,6 +461,7 @@ void km_default_params(km_params* p) {
     p->max_iter = 20;
     p->empty = KM_EMPTY_FARTHEST;
     p->tau = 0.0;
+    p->fallback = KM_FB_FP64;
 }
 
 km_status km_init(km_ctx** out, int device, void* arena, size_t arena_bytes) {
@@ -589,8 +618,7 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
                        void* stream) {
     km_status s = check_common(ctx, X, n, C, k, d);
     if (s != KM_OK) return s;
-    if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
-    if (!is_tc(p->low)) return fail(ctx, KM_EUNSUPPORTED, "km_distances needs a low format (FP16/BF16/E4M3)");
+    if ((s = check_params(ctx, p, d, k, true)) != KM_OK) return s;
     if (!D || !ws) return fail(ctx, KM_EINVAL, "null output or workspace");
     if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
     Carve cv{(char*)ws};
@@ -601,20 +629,41 @@ km_status km_distances(km_ctx* ctx, const float* X, int64_t n, const float* C, i
     CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
     CK(cudaMemsetAsync(w.qlen, 0, sizeof(unsigned long long), st));
     if (flag_bits) CK(cudaMemsetAsync(flag_bits, 0, ((size_t)n * k + 31) / 32 * 4, st));
-    const int fmt = fmt_of(p->low);
-    const int ldq = ldq_of(fmt, d);
-    const int esz = fmt == 2 ? 1 : 2;
-    KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, st));
-    if ((s = prepare_centres(ctx, C, k, d, fmt, w, st)) != KM_OK) return s;
-    TcArgs a{};
-    a.n = n; a.k = k; a.d = d; a.fmt = fmt;
-    a.kchunks = (ldq * esz + 127) / 128;
-    a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.spad = w.spad; a.colmax = w.colmax;
-    a.tp = make_tp(p, d); a.mode = 1; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
-    a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = w.qcap;
-    a.flag_queue_len = w.qlen;
-    KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
-    KL(1, launch_patch_flagged(X, C, n, k, d, w.queue, w.qlen, w.qcap, D, w.cnt, ctx->num_sms, st));
+    if (!is_tc(p->low)) {
+        if (p->low == KM_FP32) {
+            // Alg. 2 with u_l = 2^-24: E = fl(rho c_A gamma_{d+2}(u_l)) fl(d_xx + d_yy)
+            const double u32 = std::ldexp(1.0, -24);
+            const float coef = (float)(p->rho * p->paper_factor * gamma_m(d + 2, u32));
+            const float kacc = (float)((2.0 * gamma_m(d, u32) + 4.0 * u32) * (1.0 + 1e-6));
+            const float kn = (float)(4.0 * u32);
+            KL(1, launch_rowdot_fp32(X, n, d, w.dxx, ctx->num_sms, st));
+            KL(1, launch_rowdot_fp32(C, k, d, w.dyy, ctx->num_sms, st));
+            KL(1, launch_matrix(0, X, n, C, k, d, w.dxx, w.dyy, p->test, (float)p->rho, coef, kacc, kn, D, flag_bits,
+                                w.queue, w.qcap, w.qlen, w.cnt, ctx->num_sms, st));
+            // the same-precision fallback of binary32 is the binary32 direct formula
+            const int fb = p->fallback == KM_FB_FP64 ? 0 : 1;
+            KL(1, launch_patch_flagged(fb, 0, X, C, n, k, d, w.queue, w.qlen, w.qcap, D, w.cnt, ctx->num_sms, st));
+        } else {
+            KL(1, launch_matrix(p->low == KM_FP64_DIRECT ? 1 : 2, X, n, C, k, d, nullptr, nullptr, KM_TEST_OFF, 0.f,
+                                0.f, 0.f, 0.f, D, nullptr, w.queue, w.qcap, w.qlen, w.cnt, ctx->num_sms, st));
+        }
+    } else {
+        const int fmt = fmt_of(p->low);
+        const int ldq = ldq_of(fmt, d);
+        const int esz = fmt == 2 ? 1 : 2;
+        KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, st));
+        if ((s = prepare_centres(ctx, C, k, d, fmt, w, st)) != KM_OK) return s;
+        TcArgs a{};
+        a.n = n; a.k = k; a.d = d; a.fmt = fmt;
+        a.kchunks = (ldq * esz + 127) / 128;
+        a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.spad = w.spad; a.colmax = w.colmax;
+        a.tp = make_tp(p, d); a.mode = 1; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+        a.D = D; a.flag_bits = flag_bits; a.flag_queue = w.queue; a.flag_queue_cap = w.qcap;
+        a.flag_queue_len = w.qlen;
+        KL(1, launch_tc(w.Xq, w.Cq, ldq, a, ctx->num_sms, st));
+        const int fb = p->fallback == KM_FB_FP64 ? 0 : (p->fallback == KM_FB_FP32 ? 1 : 2);
+        KL(1, launch_patch_flagged(fb, fmt, X, C, n, k, d, w.queue, w.qlen, w.qcap, D, w.cnt, ctx->num_sms, st));
+    }
     ctx->last_cnt = w.cnt;
     ctx->last_sse = nullptr;
     ctx->last_stream = st;

@@ -161,19 +161,40 @@ KM_DEV double df_value(DF v) { return f32_to_f64(v.hi) + f32_to_f64(v.lo); }
 // A whole row of D <= 8 coordinates in one thread: chunk 0 and (D > 4) chunk 1
 // combined -- what the butterfly over the eight lanes of such a row gives,
 // since the other six lanes' chunks are padding.
-// The centre as two float4 (c4[1] unused for D <= 4); coordinates past D
-// must be zero in both.
+// A chunk whose coordinates past the first L are padding (zero in x and c):
+// the same value as df_chunk, with the padding's exact zeros left out
+// (a square of (0 - 0) is (+0, +0), and adding it changes nothing).
+template <int L>
+KM_DEV DF df_chunk_live(float4 x, float4 c) {
+    if constexpr (L >= 4) {
+        return df_chunk(x, c);
+    } else {
+        float p0, q0, p1 = 0.0f, q1 = 0.0f;
+        df_sq_diff(x.x, c.x, p0, q0);
+        if constexpr (L >= 2) df_sq_diff(x.y, c.y, p1, q1);
+        DF A{p0, q0};
+        if constexpr (L == 3) {
+            float p2, q2;
+            df_sq_diff(x.z, c.z, p2, q2);
+            A = df_add_raw(p0, q0, p2, q2);
+        }
+        return df_combine(A, DF{p1, q1});
+    }
+}
+
+// The centre as two float4 (the second unused for D <= 4); coordinates past
+// D must be zero in both.
 template <int D>
 KM_DEV DF df_small4(const float (&x)[D], float4 c0, float4 c1) {
     static_assert(D >= 1 && D <= 8, "rows of at most 8 coordinates");
     float xa[8];
 #pragma unroll
     for (int l = 0; l < 8; l++) xa[l] = l < D ? x[l] : 0.0f;
-    const DF h0 = df_chunk(make_float4(xa[0], xa[1], xa[2], xa[3]), c0);
+    const DF h0 = df_chunk_live<(D < 4 ? D : 4)>(make_float4(xa[0], xa[1], xa[2], xa[3]), c0);
     if constexpr (D <= 4) {
         return h0;
     } else {
-        return df_combine(h0, df_chunk(make_float4(xa[4], xa[5], xa[6], xa[7]), c1));
+        return df_combine(h0, df_chunk_live<D - 4>(make_float4(xa[4], xa[5], xa[6], xa[7]), c1));
     }
 }
 template <int D>

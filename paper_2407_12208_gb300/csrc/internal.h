@@ -141,11 +141,23 @@ size_t tc_smem_bytes(int fmt, int d, int k);
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels,
                           double* min_dist, int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st,
                           int* nlaunch);
-// fp64 direct values for the flagged pairs of the distance matrix (marked -1
-// in D): from the queue, or by a scan of D when the queue overflowed
-cudaError_t launch_patch_flagged(const float* X, const float* C, int64_t n, int k, int d, const int2* queue,
-                                 const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt,
-                                 int num_sms, cudaStream_t st);
+// the fallback's direct values for the flagged pairs of the distance matrix
+// (marked -1 in D): fb 0 binary64, 1 binary32, 2 the low format fmt (0
+// fp16, 1 bf16) itself; from the queue, or by a scan of D when it overflowed
+cudaError_t launch_patch_flagged(int fb, int fmt, const float* X, const float* C, int64_t n, int k, int d,
+                                 const int2* queue, const unsigned long long* qlen, int64_t cap, float* D,
+                                 DevCounters* cnt, int num_sms, cudaStream_t st);
+// out[i] = sum_l fl(a_il^2) in binary32, recursive summation (Alg. 2's d_xx)
+cudaError_t launch_rowdot_fp32(const float* A, int64_t m, int d, float* out, int num_sms, cudaStream_t st);
+// the distance matrix on CUDA cores, rounded operations in order: mode 0 Alg. 2
+// in binary32 (dxx, dyy from launch_rowdot_fp32; test 1 paper: coef = fl(rho
+// c_A gamma_{d+2}(2^-24)); test 0 tc: kacc, kn; 2 off), flagged pairs marked
+// -1, queued and set in flag_bits (nullable); mode 1 direct formula in
+// binary64, mode 2 in binary32
+cudaError_t launch_matrix(int mode, const float* X, int64_t n, const float* C, int k, int d, const float* dxx,
+                          const float* dyy, int test, float rho, float coef, float kacc, float kn, float* D,
+                          uint32_t* flag_bits, int2* queue, int64_t qcap, unsigned long long* qlen, DevCounters* cnt,
+                          int num_sms, cudaStream_t st);
 
 // centre update
 cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cudaStream_t st);

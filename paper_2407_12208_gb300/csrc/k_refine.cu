@@ -17,9 +17,7 @@
 //     binary64 (products and sums rounded separately, coordinates in order:
 //     the oracle's own arithmetic), lowest index on ties.  Overflowed rows
 //     are listed for the full-row kernel, which evaluates every centre.
-//
-// k_patch_flagged: binary64 direct values for the flagged pairs of the
-// distance matrix (Alg. 2's fallback branch).
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -330,43 +328,6 @@ __global__ void __launch_bounds__(256) k_amb_fp64(const int32_t* __restrict__ am
     if (lane == 0 && ev64) atomicAdd(&cnt->fp64_evals, ev64);
 }
 
-// Flagged pairs of the distance matrix (marked -1 by the screening kernel):
-// their binary64 direct values, from the bounded queue the screening kernel
-// filled, or, when more pairs were flagged than it holds, by a scan of D for
-// the marks.
-__global__ void k_patch_flagged(const float* __restrict__ X, const float* __restrict__ C, int k, int d,
-                                const int2* __restrict__ queue, const unsigned long long* __restrict__ qlen,
-                                int64_t cap, float* __restrict__ D, int64_t n, DevCounters* cnt) {
-    const int64_t len = (int64_t)*qlen;
-    const bool scan = len > cap;
-    const int64_t total = scan ? n * (int64_t)k : len;
-    unsigned long long ev = 0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t row, j;
-        if (scan) {
-            if (!(D[t] < 0.0f)) continue;
-            row = t / k;
-            j = t - row * k;
-        } else {
-            const int2 pr = queue[t];
-            row = pr.x;
-            j = pr.y;
-        }
-        const float* x = X + row * d;
-        const float* c = C + j * d;
-        double s = 0.0;
-        for (int l = 0; l < d; l++) {
-            const double u = __dsub_rn((double)x[l], (double)c[l]);
-            s = __dadd_rn(s, __dmul_rn(u, u));
-        }
-        D[row * k + j] = (float)s;
-        ev++;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, off);
-    if ((threadIdx.x & 31) == 0 && ev) atomicAdd(&cnt->fp64_evals, ev);
-}
-
 cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32_t* labels, double* min_dist,
                           int32_t* full_list, int32_t* amb_list, int num_sms, cudaStream_t st, int* nlaunch) {
     // persistent grids: the resident blocks only
@@ -407,13 +368,6 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     if (e != cudaSuccess) return e;
     k_amb_fp64<<<(unsigned)num_sms, 256, amb_smem, st>>>(amb_list, &a.cnt->amb_count, a.rowpair, a.pairs, a.v32, X, C,
                                                           a.d, a.tp.gamma32, labels, min_dist, a.cnt);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_patch_flagged(const float* X, const float* C, int64_t n, int k, int d, const int2* queue,
-                                 const unsigned long long* qlen, int64_t cap, float* D, DevCounters* cnt, int num_sms,
-                                 cudaStream_t st) {
-    k_patch_flagged<<<num_sms * 8, 256, 0, st>>>(X, C, k, d, queue, qlen, cap, D, n, cnt);
     return cudaGetLastError();
 }
 

@@ -590,12 +590,15 @@ def test_mixture_lloyd_full_size_teacher_forced(low):
 def test_choose_low_predicts_list_overflow(ctx):
     """km_choose_low: on uniform data E4M3's error bound exceeds the spread of
     the distances (every row's candidates overflow its list) and BF16 is
-    chosen; on well-separated clusters E4M3 keeps one candidate per row and is
-    chosen.  The predicted overflow share is what an E4M3 assignment of the
-    same data then measures, within 0.1."""
+    chosen; on points tight around well-separated centres E4M3 keeps one
+    candidate per row and is chosen.  The predicted overflow share is what an
+    E4M3 assignment of the same data then measures, within 0.1."""
     import paper_2407_12208_gb300 as pkg
     X, C = workloads.uniform_pairs(20000, 128, 256, seed=66)
-    X2, C2 = workloads.gaussian_mixture(20000, 128, 64, seed=67, std_lo=0.01, std_hi=0.02)
+    # points tightly around 64 centres N(0, 25) apart, and those centres
+    r = np.random.default_rng(67)
+    C2 = r.normal(0.0, 5.0, size=(64, 128)).astype(np.float32)
+    X2 = (C2[r.integers(0, 64, size=20000)] + r.normal(0.0, 0.01, size=(20000, 128))).astype(np.float32)
     for Xh, Ch, expect in ((X, C, "bf16"), (X2, C2, "e4m3")):
         Xd, Cd = _dev(Xh), _dev(Ch)
         low, st = ctx.choose_low(Xd, Cd, max_overflow_share=0.01)
@@ -607,3 +610,88 @@ def test_choose_low_predicts_list_overflow(ctx):
     with pytest.raises(pkg.KmError) as ei:
         ctx.choose_low(_dev(X), _dev(C), max_overflow_share=2.0)
     assert ei.value.status == pkg._binding.KM_EINVAL
+
+
+# ------------------------------- the precision matrix of Tables 6.1 / 6.2
+def _flags_of(bits, n, k):
+    bits = bits.cpu().numpy().view(np.uint32)
+    idx = np.arange(n * k)
+    return ((bits[idx >> 5] >> (idx & 31)) & 1).reshape(n, k).astype(bool)
+
+
+@pytest.mark.parametrize("fb", ["fp64", "fp32"])
+@pytest.mark.parametrize("c_A", [1.0, 2.0])
+def test_distances_fp32_alg2_bitexact(ctx, fb, c_A):
+    """Alg. 2 with binary32 as the low precision (FP32 -> FP64 and FP32 ->
+    FP32 of Table 6.1): every pair's flag and value equal the oracle's
+    emulation of Alg. 2 bit for bit (values stored in binary32)."""
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.near_far(120, 64, 0.5, seed=68)
+    C = C[:90]
+    p = pkg.params("fp32x", "paper", rho=5.0, paper_factor=c_A, fallback=fb)
+    D, bits, nf = ctx.distances(_dev(X), _dev(C), p)
+    D = D.cpu().numpy()
+    flags = _flags_of(bits, 120, 90)
+    fbf = 4 if fb == "fp64" else 3
+    ref_d = np.empty((120, 90), np.float32)
+    ref_f = np.empty((120, 90), bool)
+    for i in range(120):
+        for j in range(90):
+            f, d, _, _ = oracle.mp_dist_fb(X[i], C[j], 5.0, 3, fbf, c_A)
+            ref_d[i, j], ref_f[i, j] = np.float32(d), f
+    assert np.array_equal(flags, ref_f) and nf == int(ref_f.sum())
+    assert 0 < nf < 120 * 90
+    np.testing.assert_array_equal(D.view(np.uint32), ref_d.view(np.uint32))
+
+
+@pytest.mark.parametrize("low,fb", [("fp16", "low"), ("bf16", "low"), ("fp16", "fp32"), ("bf16", "fp32")])
+def test_distances_fallback_precisions(ctx, low, fb):
+    """Eq. (fallback-rule) in the chosen precision: the flagged pairs hold
+    the direct formula evaluated with every operation rounded to the low
+    format (the same-precision fallback) or to binary32, as the oracle
+    emulates it, bit for bit; the unflagged ones are within the bound."""
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.near_far(300, 128, 0.5, seed=69)
+    C = C[:200]
+    p = pkg.params(low, "tc", fallback=fb)
+    D, bits, nf = ctx.distances(_dev(X), _dev(C), p)
+    D = D.cpu().numpy()
+    flags = _flags_of(bits, 300, 200)
+    assert flags.sum() == nf > 0
+    fmt = {"fp16": 0, "bf16": 1}[low]
+    fbf = fmt if fb == "low" else 3
+    ii, jj = np.nonzero(flags)
+    ref = np.array([oracle.dist_direct_fmt(X[i], C[j], fbf) for i, j in zip(ii, jj)], dtype=np.float32)
+    np.testing.assert_array_equal(D[ii, jj].view(np.uint32), ref.view(np.uint32))
+    Dex = oracle.dist_direct(X, C)
+    B = oracle.tc_bound_matrix(X, C, fmt)
+    un = ~flags
+    assert np.all(np.abs(D[un] - Dex[un]) <= B[un] + 1e-6 * Dex[un])
+
+
+@pytest.mark.parametrize("low", ["fp64", "fp32"])
+def test_distances_direct_modes(ctx, low):
+    """The direct formula for every pair (the FP64 direct row of Table 6.1,
+    and binary32): the oracle's values bit for bit, nothing flagged."""
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.blobs(150, 40, 70, seed=70)
+    D, bits, nf = ctx.distances(_dev(X), _dev(C), pkg.params(low))
+    D = D.cpu().numpy()
+    if low == "fp64":
+        ref = oracle.dist_direct(X, C).astype(np.float32)
+    else:
+        ref = np.array([[oracle.dist_direct_fmt(x, c, 3) for c in C] for x in X], dtype=np.float32)
+    np.testing.assert_array_equal(D.view(np.uint32), ref.view(np.uint32))
+    assert nf == 0
+
+
+def test_precision_modes_rejected_where_undefined(ctx):
+    import paper_2407_12208_gb300 as pkg
+    X = _dev(np.random.default_rng(0).random((64, 32), dtype=np.float32))
+    for p in (pkg.params("fp32x"), pkg.params("bf16", fallback="fp32")):
+        with pytest.raises(pkg.KmError) as ei:
+            ctx.assign(X, X[:4], p)  # the assignment certifies in fp32 and binary64 itself
+        assert ei.value.status == pkg._binding.KM_EUNSUPPORTED
+    with pytest.raises(pkg.KmError) as ei:
+        ctx.distances(X, X[:4], pkg.params("e4m3", fallback="low"))
+    assert ei.value.status == pkg._binding.KM_EUNSUPPORTED

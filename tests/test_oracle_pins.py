@@ -115,6 +115,87 @@ def test_e4m3_row_scale_rule():
     assert list(sc[-6:-1]) == [2.0 ** -126] * 4 + [2.0 ** -126]
 
 
+def test_binary32_rounding_matches_numpy():
+    # fmt 3 of round_to_format is binary32: numpy's float64 -> float32 cast
+    # (IEEE round to nearest even) on normals, ties, subnormals and overflow
+    r = np.random.default_rng(13)
+    v = r.uniform(-1, 1, 20000) * 10.0 ** r.uniform(-46, 39, 20000)
+    ties = (np.arange(1, 200, dtype=np.float64) + 0.5) * 2.0 ** -23
+    v = np.concatenate([v, ties, ties * 2.0 ** -130, [3.5e38, 3.41e38, -1e39, 1e-46]])
+    with np.errstate(over="ignore"):
+        ref = v.astype(np.float32).astype(np.float64)
+    got = np.array([oracle.round_to_format(float(a), 3) for a in v])
+    np.testing.assert_array_equal(got, ref)
+    assert oracle.unit_roundoff(3) == 2.0 ** -24
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 3])
+def test_dist_direct_fmt_matches_library_arithmetic(fmt):
+    # the direct formula with every operation rounded to the format, against
+    # the same sequence of operations done in the library's own arithmetic of
+    # that format (numpy float32 / float16, torch bfloat16); the inputs keep
+    # every exact intermediate within 24 bits, so the library's float32
+    # evaluation followed by one rounding is the format's own rounding
+    r = np.random.default_rng(14 + fmt)
+    for _ in range(200):
+        x = r.uniform(-4, 4, 8)
+        y = x + r.choice([-1, 1], 8) * r.uniform(0.5, 2, 8)
+        x32, y32 = x.astype(np.float32), y.astype(np.float32)
+        got = oracle.dist_direct_fmt(x32, y32, fmt)
+        if fmt == 3:
+            s = np.float32(0)
+            for a, b in zip(x32, y32):
+                t = np.float32(a - b)
+                s = np.float32(s + np.float32(t * t))
+            ref = float(s)
+        elif fmt == 0:
+            xh, yh = x32.astype(np.float16), y32.astype(np.float16)
+            s = np.float16(0)
+            for a, b in zip(xh, yh):
+                t = np.float16(a - b)
+                s = np.float16(s + np.float16(t * t))
+            ref = float(s)
+        else:
+            torch = pytest.importorskip("torch")
+            xb = torch.from_numpy(x32).to(torch.bfloat16)
+            yb = torch.from_numpy(y32).to(torch.bfloat16)
+            s = torch.zeros((), dtype=torch.bfloat16)
+            for a, b in zip(xb, yb):
+                t = a - b
+                s = s + t * t
+            ref = float(s)
+        assert got == ref, (fmt, got, ref)
+    # the binary64 case is Eq. (dist-direct) itself
+    x = r.normal(size=16).astype(np.float32)
+    y = r.normal(size=16).astype(np.float32)
+    assert oracle.dist_direct_fmt(x, y, 4) == oracle.dist_direct(x[None], y[None])[0, 0]
+
+
+def test_alg2_fallback_precisions():
+    # Eq. (fallback-rule): a flagged pair is recomputed by the direct formula
+    # in the fallback's precision (binary64, binary32, or the low format
+    # itself); an unflagged pair keeps Alg. 2's d^ whatever the fallback
+    u = 2.0 ** -24
+    x = np.zeros(8, np.float32); x[0] = 1.0
+    y = x.copy(); y[1] = np.float32(10 * u)
+    for fmt in (0, 1):
+        for fb in (4, 3, fmt):
+            flag, d, _, _ = oracle.mp_dist_fb(x, y, 5.0, fmt, fb)
+            assert flag and d == oracle.dist_direct_fmt(x, y, fb)
+        assert oracle.mp_dist_fb(x, y, 5.0, fmt, 4)[1] == (10 * u) ** 2   # exact in binary64
+        # in the low format itself: the square (10u)^2 underflows binary16;
+        # bfloat16 has binary32's exponent range and holds it exactly
+        assert oracle.mp_dist_fb(x, y, 5.0, fmt, fmt)[1] == (0.0 if fmt == 0 else (10 * u) ** 2)
+        far = np.full(8, 3.0, np.float32)
+        fl, d, dh, _ = oracle.mp_dist_fb(x, far, 5.0, fmt, 3)
+        assert not fl and d == dh
+    # Alg. 2 in binary32 (the FP32 -> FP64 mode): the same worked example is
+    # flagged at u = 2^-24 too, and x = y always
+    flag, d, dh, E = oracle.mp_dist_fb(x, y, 5.0, 3, 4)
+    assert flag and d == (10 * u) ** 2 and E > 0
+    assert oracle.mp_dist_fb(x, x, 5.0, 3, 4)[0]
+
+
 def test_e4m3_saturates():
     assert oracle.round_to_format(1e6, 2) == 448.0
     assert oracle.round_to_format(-465.0, 2) == -448.0
