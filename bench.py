@@ -430,68 +430,116 @@ def table6_leg(args, device: int) -> dict:
     return {"n": 5000, "k": 5000, "r": 128, "near_eps": 1e-4, "rho": 5.0, "c_A": 2.0, "modes": out}
 
 
+def _job_data(sp, seed: int, device: int):
+    """One served job's data, generated on the device (resident): a Gaussian
+    mixture as in the Lloyd workload (centre coordinates N(0, 25), cluster
+    std log-uniform [0.1, 2], uniform cluster choice), k initial centres =
+    k distinct seeded rows."""
+    import math
+    import torch
+    g = torch.Generator(device="cuda:%d" % device)
+    g.manual_seed(seed)
+    n, d, k = sp["n"], sp["d"], sp["k"]
+    dev = torch.device("cuda", device)
+    centres = torch.randn((k, d), generator=g, device=dev) * 5.0
+    stds = torch.exp(torch.empty(k, device=dev).uniform_(math.log(0.1), math.log(2.0), generator=g))
+    lab = torch.randint(0, k, (n,), generator=g, device=dev)
+    X = centres[lab] + torch.randn((n, d), generator=g, device=dev) * stds[lab, None]
+    C = X[torch.randperm(n, generator=g, device=dev)[:k]].contiguous()
+    return X.contiguous(), C
+
+
 def serving_leg(args, device: int) -> dict:
-    """Served stream through km_submit / km_poll: Lloyd jobs of uneven n, d, k
-    (n log-uniform in [1e3, 1e5], d in {2, 8, 32, 128, 256}, k log-uniform in
-    [4, 1024], Gaussian mixtures, 25 iterations; FP32 direct for d <= 8, BF16
-    below d = 64, E4M3 from d = 64), 80 GB arena budget.  A burst at t = 0
-    gives the saturated throughput; then a Poisson stream at half that job
-    rate.  Latency = submit -> result ready, measured by the library."""
+    """Served stream through km_submit / km_poll (continuous admission of
+    Lloyd jobs of uneven n, d, k; 25 iterations each; the library's format
+    rule (km_choose_low) for d > 8, FP32 direct below; 80 GB arena).  Job
+    data are generated on the device just before their arrival and read in
+    place (KM_JOB_DEVICE_DATA); at most 64 GB of job data is resident at once
+    (a submitter that would exceed it waits for completions).  First the
+    saturated stream (every job due at once), then Poisson arrivals at 0.5x
+    and 0.8x its job rate.  Latency = submit -> result ready, measured by the
+    library.  --serve-full: the stream of the served-batch workload (10,000
+    jobs, n log-uniform [1e3, 1e6], d in {2, 8, 32, 128, 256}, k log-uniform
+    [4, 1024]); by default a bounded stream of the same mix with n <= 1e5."""
     import numpy as np
+    import torch
     import paper_2407_12208_gb300 as pkg
     from paper_2407_12208_gb300 import workloads
-    import torch
-    specs = workloads.serving_jobs(args.serve_jobs, seed=2024, n_lo=1e3, n_hi=1e5)
+    full = args.serve_full
+    njobs = 10_000 if full else args.serve_jobs
+    specs = workloads.serving_jobs(njobs, seed=2024, n_lo=1e3, n_hi=1e6 if full else 1e5)
     ctx = pkg.Context(device, arena_bytes=80 << 30)
-    data = []
-    for i, sp in enumerate(specs):
-        X, C = workloads.gaussian_mixture(sp["n"], sp["d"], sp["k"], seed=3000 + i)
-        # small d: the direct path; else the library's rule (km_choose_low)
-        low = "fp32" if sp["d"] <= 8 else ctx.choose_low(torch.from_numpy(X).cuda(device),
-                                                          torch.from_numpy(C).cuda(device))[0]
-        data.append((X, C, pkg.params(low, max_iter=25, tau=0.0)))
+    budget = 64 << 30
+    lows = {}
 
-    def run(arrivals):
-        ids, t0 = [], time.perf_counter()
-        pending = {}
-        lat = []
-        for (X, C, p), ta in zip(data, arrivals):
-            while time.perf_counter() - t0 < ta:
-                for jid in list(pending):
+    def run(arrivals, tag):
+        t0 = time.perf_counter()
+        pending, lat, resident = {}, [], 0
+        pairs = 0.0
+
+        def reap(block):
+            nonlocal resident
+            while True:
+                done = []
+                for jid, (nb, keep) in pending.items():
                     r = ctx.poll(jid)
                     if r is not None:
+                        assert r["status"] == 0, (r["status"], r["message"])
                         lat.append(r["latency_ms"])
-                        ctx.release(jid)
-                        del pending[jid]
-                time.sleep(0.0005)
-            jid = ctx.submit(X, C, p, kind=0)
-            pending[jid] = True
-        while pending:
-            for jid in list(pending):
-                r = ctx.poll(jid)
-                if r is not None:
-                    assert r["status"] == 0, (r["status"], r["message"])
-                    lat.append(r["latency_ms"])
+                        done.append(jid)
+                for jid in done:
                     ctx.release(jid)
-                    del pending[jid]
-            time.sleep(0.0005)
-        return lat, time.perf_counter() - t0
+                    resident -= pending.pop(jid)[0]
+                if done or not block:
+                    return
+                time.sleep(0.0005)
 
-    run([0.0] * min(8, len(data)))  # warm-up: module loading, first launches
-    lat_b, span_b = run([0.0] * len(data))
-    pairs = sum(X.shape[0] * float(C.shape[0]) * 26 for X, C, _ in data)  # 25 iterations + final assignment
-    rate = 0.5 * len(data) / span_b
-    arr = workloads.poisson_arrivals(len(data), rate, seed=7)
-    lat_p, span_p = run(list(arr))
+        for i, (sp, ta) in enumerate(zip(specs, arrivals)):
+            nb = sp["n"] * sp["d"] * 4
+            while resident + nb > budget and pending:
+                reap(True)
+            while time.perf_counter() - t0 < ta:
+                reap(False)
+                time.sleep(0.0002)
+            X, C = _job_data(sp, 5000 + i, device)
+            key = i
+            if key not in lows:
+                lows[key] = "fp32" if sp["d"] <= 8 else ctx.choose_low(X, C)[0]
+            torch.cuda.synchronize(device)
+            jid = ctx.submit(X, C, pkg.params(lows[key], max_iter=25, tau=0.0), kind=0)
+            pending[jid] = (nb, (X, C))
+            resident += nb
+            pairs += sp["n"] * float(sp["k"]) * 26  # 25 iterations + final assignment
+            if i % 64 == 0:
+                reap(False)
+        while pending:
+            reap(True)
+        span = time.perf_counter() - t0
+        pct = lambda q: float(np.percentile(np.asarray(lat), q))
+        return {"p50_ms": pct(50), "p99_ms": pct(99), "pairs_per_s": pairs / span, "jobs_per_s": len(lat) / span,
+                "makespan_s": span}
+
+    warm = workloads.serving_jobs(8, seed=7, n_lo=1e3, n_hi=1e4)
+    for i, sp in enumerate(warm):  # module loading, first launches
+        X, C = _job_data(sp, 100 + i, device)
+        jid = ctx.submit(X, C, pkg.params("fp32" if sp["d"] <= 8 else "bf16", max_iter=2), kind=0)
+        while ctx.poll(jid) is None:
+            time.sleep(0.001)
+        ctx.release(jid)
+    sat = run([0.0] * njobs, "saturated")
+    out = {"jobs": njobs, "iterations_per_job": 25, "arena_gb": 80, "resident_budget_gb": 64,
+           "saturated": sat,
+           "sizes": "n log-uniform [1e3, %s], d in {2, 8, 32, 128, 256}, k log-uniform [4, 1024]" %
+                    ("1e6" if full else "1e5 (bounded stand-in for [1e3, 1e6])"),
+           "formats": {f: sum(1 for v in lows.values() if v == f) for f in set(lows.values())}}
+    for load in (0.5, 0.8):
+        rate = load * sat["jobs_per_s"]
+        arr = workloads.poisson_arrivals(njobs, rate, seed=int(load * 10))
+        res = run(list(arr), "poisson")
+        res["rate_jobs_per_s"] = rate
+        out["poisson_%d%%" % round(100 * load)] = res
     ctx.close()
-    pct = lambda v, q: float(np.percentile(np.asarray(v), q))
-    return {"jobs": len(data), "iterations_per_job": 25, "arena_gb": 80,
-            "burst": {"p50_ms": pct(lat_b, 50), "p99_ms": pct(lat_b, 99), "pairs_per_s": pairs / span_b,
-                      "makespan_s": span_b},
-            "poisson_half_load": {"rate_jobs_per_s": rate, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
-                                  "pairs_per_s": pairs / span_p},
-            "sizes": "n log-uniform [1e3, 1e5] (bounded stand-in for [1e3, 1e6]), d in {2, 8, 32, 128, 256}, "
-                     "k log-uniform [4, 1024]"}
+    return out
 
 
 def run_reference(args):
@@ -546,7 +594,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-table6", action="store_true", help="skip the distance-matrix precision leg")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
-    ap.add_argument("--serve-jobs", type=int, default=64)
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the served-batch workload at full size: 10,000 jobs, n up to 1e6 (minutes)")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step only: no end-to-end, FP64 or CPU legs (for profiler runs)")
     args = ap.parse_args()

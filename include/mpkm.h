@@ -315,9 +315,15 @@ km_status km_assign_static(km_ctx* ctx, const float* X, int64_t n, const float* 
 
 /* ---- serving (continuous batching on one GPU) ---------------------------- */
 
-/* A job: X (n x d) and C_init (k x d) are HOST pointers, copied into the
- * arena at admission.  kind 0 = Lloyd (Alg. 3, p.max_iter iterations),
- * kind 1 = one nearest-centre assignment against C_init. */
+/* A job: X (n x d) and C_init (k x d).  kind 0 = Lloyd (Alg. 3, p.max_iter
+ * iterations), kind 1 = one nearest-centre assignment against C_init.
+ * flags 0: X and C_init are HOST pointers, copied before km_submit returns
+ * and into the arena at admission.  flags KM_JOB_DEVICE_DATA: they are
+ * DEVICE pointers on the context's device that stay valid and unchanged
+ * until km_poll reports the job finished; X is read in place (resident
+ * points take no arena memory), C_init is copied into the arena at
+ * admission. */
+#define KM_JOB_DEVICE_DATA 1
 typedef struct {
     const float* X;
     int64_t n;
@@ -326,6 +332,7 @@ typedef struct {
     const float* C_init;
     km_params p;
     int32_t kind;
+    int32_t flags;
 } km_job;
 
 typedef struct {
@@ -340,9 +347,13 @@ typedef struct {
     const char* message;  /* why the job failed ("" when it did not), valid until km_release */
 } km_result;
 
-/* Queues a job; it is admitted when its memory fits in the arena.  The host
- * arrays are copied before the call returns.  KM_ENOMEM if the job could
- * never fit in the arena. */
+/* Queues a job; it is admitted as soon as its memory (centres, labels and
+ * workspace; the points too for host data) fits in the arena, up to 16 jobs
+ * running at once, each on its own stream so that their kernels overlap on
+ * the device; queued jobs are considered in arrival order on every change,
+ * so a small job can start while a large one waits for memory.  Host arrays
+ * are copied before the call returns.  KM_ENOMEM if the job could never fit
+ * in the arena. */
 km_status km_submit(km_ctx* ctx, const km_job* job, uint64_t* job_id);
 /* KM_ENOTREADY until the job is done; then fills *out. */
 km_status km_poll(km_ctx* ctx, uint64_t job_id, km_result* out);

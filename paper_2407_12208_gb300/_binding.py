@@ -57,9 +57,12 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+JOB_DEVICE_DATA = 1
+
+
 class Job(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("C_init", ctypes.c_void_p), ("p", Params), ("kind", ctypes.c_int32)]
+                ("C_init", ctypes.c_void_p), ("p", Params), ("kind", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -383,15 +386,25 @@ class Context:
 
     # ---- serving
     def submit(self, X, C_init, p: Params, kind: int = 0) -> int:
-        """X, C_init: C-contiguous float32 numpy arrays (host); copied before return."""
+        """X, C_init: C-contiguous float32 numpy arrays (host; copied before
+        return) or CUDA tensors (resident: read in place, they must stay
+        alive and unchanged until the job has finished)."""
         import numpy as np
-        X = np.ascontiguousarray(X, dtype=np.float32)
-        C = np.ascontiguousarray(C_init, dtype=np.float32)
         j = Job()
-        j.X = X.ctypes.data_as(ctypes.c_void_p)
-        j.n, j.d = X.shape
-        j.k = C.shape[0]
-        j.C_init = C.ctypes.data_as(ctypes.c_void_p)
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            assert X.is_contiguous() and C_init.is_contiguous() and C_init.is_cuda
+            j.X, j.C_init = ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(C_init.data_ptr())
+            j.n, j.d = X.shape
+            j.k = C_init.shape[0]
+            j.flags = JOB_DEVICE_DATA
+        else:
+            X = np.ascontiguousarray(X, dtype=np.float32)
+            C = np.ascontiguousarray(C_init, dtype=np.float32)
+            j.X = X.ctypes.data_as(ctypes.c_void_p)
+            j.n, j.d = X.shape
+            j.k = C.shape[0]
+            j.C_init = C.ctypes.data_as(ctypes.c_void_p)
+            j.flags = 0
         j.p = p
         j.kind = int(kind)
         jid = ctypes.c_uint64(0)

@@ -40,7 +40,14 @@ struct km_ctx {
     // against the caller's stream (created on first use)
     cudaStream_t copy_st[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> host_ev;
+    // km_lloyd_run's replayed iterations run on this stream when the caller's
+    // is a legacy default stream (which cannot be captured)
+    cudaStream_t graph_st = nullptr;
+    cudaEvent_t graph_ev[2] = {nullptr, nullptr};
     ~km_ctx() {
+        for (cudaEvent_t e : graph_ev)
+            if (e) cudaEventDestroy(e);
+        if (graph_st) cudaStreamDestroy(graph_st);
         for (auto& v : ev)
             for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         for (cudaEvent_t e : host_ev) cudaEventDestroy(e);
@@ -246,6 +253,8 @@ struct LloydWs {
     double* sse_hist;
     unsigned long long* flag_hist;
     int64_t* counts;
+    double* sse_slot;  // a replayed iteration's SSE, appended to sse_hist on the device
+    int* hist_len;     // entries of sse_hist / flag_hist written by replayed iterations
 };
 LloydWs carve_lloyd(Carve& cv, int64_t n, int d, int k, int low, int max_iter) {
     LloydWs L{};
@@ -257,6 +266,8 @@ LloydWs carve_lloyd(Carve& cv, int64_t n, int d, int k, int low, int max_iter) {
     L.sse_hist = cv.take<double>((size_t)max_iter + 1);
     L.flag_hist = cv.take<unsigned long long>((size_t)max_iter + 1);
     L.counts = cv.take<int64_t>((size_t)k);
+    L.sse_slot = cv.take<double>(1);
+    L.hist_len = cv.take<int>(1);
     return L;
 }
 
@@ -867,6 +878,73 @@ km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, con
 
 }  // extern "C"
 
+// Appends a replayed iteration's SSE and the flag count so far to the
+// histories (one thread).
+__global__ void k_record_iteration(const double* __restrict__ sse_slot, const DevCounters* __restrict__ cnt,
+                                   double* __restrict__ sse_hist, unsigned long long* __restrict__ flag_hist,
+                                   int* hist_len, int cap) {
+    const int i = *hist_len;
+    if (i < cap) {
+        sse_hist[i] = *sse_slot;
+        flag_hist[i] = cnt->flagged;
+    }
+    *hist_len = i + 1;
+}
+
+// One iteration of Alg. 3's loop from cur to nxt.  sse_out: the SSE's
+// destination; graph: the iteration is being recorded for replay (its SSE and
+// flag count go to the slot and are appended by k_record_iteration).
+static km_status lloyd_iteration(km_ctx* ctx, const float* X, int64_t n, int d, int k, const km_params* p,
+                                 int32_t* labels, const LloydWs& L, const float* cur, float* nxt, double* sse_out,
+                                 unsigned long long* flag_out, bool graph, int cap, cudaStream_t st) {
+    CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
+    km_status s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
+    if (s != KM_OK) return s;
+    if (!graph) CK(cudaMemcpyAsync(flag_out, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+    PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
+    s = accumulate(ctx, X, n, d, labels, k, L.u, cur, p->low == KM_FP64_DIRECT ? nullptr : L.min_dist, st);
+    if (s != KM_OK) return s;
+    KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, graph ? L.sse_slot : sse_out, st));
+    if ((s = finalize(ctx, L.u, n, k, d, cur, p, X, L.min_dist, nxt, L.counts, L.a.cnt, st)) != KM_OK) return s;
+    if (graph) {
+        k_record_iteration<<<1, 1, 0, st>>>(L.sse_slot, L.a.cnt, L.sse_hist, L.flag_hist, L.hist_len, cap);
+        ctx->launches++;
+        CK(cudaGetLastError());
+    }
+    return KM_OK;
+}
+
+// Records the two iterations C0 -> C1 and C1 -> C0 as CUDA graphs on gs
+// (every pointer the same whatever the iteration); false when the stream
+// cannot be captured (the caller then launches the iterations directly).
+static bool capture_iterations(km_ctx* ctx, const float* X, int64_t n, int d, int k, const km_params* p,
+                               int32_t* labels, const LloydWs& L, int cap, cudaStream_t gs, cudaGraphExec_t (&ge)[2],
+                               uint64_t (&nk)[2]) {
+    ge[0] = ge[1] = nullptr;
+    for (int par = 0; par < 2; par++) {
+        if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+        const uint64_t l0 = ctx->launches;
+        const std::string err0 = ctx->err;
+        km_status s = lloyd_iteration(ctx, X, n, d, k, p, labels, L, par ? L.C1 : L.C0, par ? L.C0 : L.C1, nullptr,
+                                      nullptr, true, cap, gs);
+        nk[par] = ctx->launches - l0;
+        ctx->launches = l0;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(gs, &g);
+        if (s != KM_OK || ec != cudaSuccess || !g || cudaGraphInstantiate(&ge[par], g, 0) != cudaSuccess) {
+            ctx->err = err0;
+            if (g) cudaGraphDestroy(g);
+            break;
+        }
+        cudaGraphDestroy(g);
+    }
+    if (ge[0] && ge[1]) return true;
+    for (cudaGraphExec_t& e : ge)
+        if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    cudaGetLastError();  // a refused capture leaves nothing behind
+    return false;
+}
+
 static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                             const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                             double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
@@ -883,6 +961,7 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
     CK(cudaMemsetAsync(L.a.cnt, 0, sizeof(DevCounters), st));
+    CK(cudaMemsetAsync(L.hist_len, 0, sizeof(int), st));
     CK(cudaMemcpyAsync(L.C0, C_init, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToDevice, st));
     // the quantised data and its norms are computed once (Section 3.2), and with
     // them the largest |x| that fixes the scale of the exact centre sums
@@ -897,30 +976,65 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     float* cur = L.C0;
     float* nxt = L.C1;
     int t = 0;
+    // Iterations as replays of two recorded graphs (C0 -> C1, C1 -> C0): one
+    // launch per iteration instead of one per kernel.  Phase timing needs the
+    // direct launches (its events sit between the kernels).
+    cudaGraphExec_t ge[2] = {nullptr, nullptr};
+    uint64_t nk[2] = {0, 0};
+    cudaStream_t gs = st;
+    bool graphs = false;
+    if (!ctx->prof && p->max_iter >= 2) {
+        const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+        if (legacy) {
+            if (!ctx->graph_st) CK(cudaStreamCreateWithFlags(&ctx->graph_st, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : ctx->graph_ev)
+                if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            gs = ctx->graph_st;
+        }
+        graphs = capture_iterations(ctx, X, n, d, k, p, labels, L, p->max_iter + 1, gs, ge, nk);
+        if (graphs && legacy) {  // the replays follow the caller's earlier work
+            CK(cudaEventRecord(ctx->graph_ev[0], st));
+            CK(cudaStreamWaitEvent(gs, ctx->graph_ev[0], 0));
+        }
+        if (!graphs) gs = st;
+    }
+    auto drop_graphs = [&]() {
+        for (cudaGraphExec_t& e : ge)
+            if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    };
     for (t = 0; t < p->max_iter; t++) {
-        CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
-        s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
-        if (s != KM_OK) return s;
-        CK(cudaMemcpyAsync(L.flag_hist + t, &L.a.cnt->flagged, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
-        {
-            PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-            s = accumulate(ctx, X, n, d, labels, k, L.u, cur, p->low == KM_FP64_DIRECT ? nullptr : L.min_dist, st);
+        if (graphs) {
+            const cudaError_t e = cudaGraphLaunch(ge[t & 1], gs);
+            if (e != cudaSuccess) {
+                drop_graphs();
+                return fail(ctx, KM_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+            }
+            ctx->launches += nk[t & 1];
+        } else {
+            s = lloyd_iteration(ctx, X, n, d, k, p, labels, L, cur, nxt, L.sse_hist + t, L.flag_hist + t, false, 0, st);
             if (s != KM_OK) return s;
-            KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, L.sse_hist + t, st));
-            if ((s = finalize(ctx, L.u, n, k, d, cur, p, X, L.min_dist, nxt, L.counts, L.a.cnt, st)) != KM_OK)
-                return s;
         }
         std::swap(cur, nxt);
         if (cancel && *cancel) {
-            CK(cudaStreamSynchronize(st));
+            drop_graphs();
+            CK(cudaStreamSynchronize(gs));
             return fail(ctx, KM_ECANCELLED, "cancelled");
         }
         if (p->tau > 0.0) {
             double shift = 0.0;
-            CK(cudaMemcpyAsync(&shift, L.u.shift, sizeof(double), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
+            cudaError_t e = cudaMemcpyAsync(&shift, L.u.shift, sizeof(double), cudaMemcpyDeviceToHost, gs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
+            if (e != cudaSuccess) {
+                drop_graphs();
+                return fail(ctx, KM_ECUDA, "shift read-back: %s", cudaGetErrorString(e));
+            }
             if (shift < p->tau) { t++; break; }
         }
+    }
+    drop_graphs();
+    if (gs != st) {  // back on the caller's stream
+        CK(cudaEventRecord(ctx->graph_ev[1], gs));
+        CK(cudaStreamWaitEvent(st, ctx->graph_ev[1], 0));
     }
     CK(cudaMemsetAsync(&L.a.cnt->amb_count, 0, 2 * sizeof(int), st));
     s = run_assign(ctx, X, n, cur, k, d, p, labels, L.min_dist, L.a, true, st);
@@ -1003,6 +1117,18 @@ km_status km_submit(km_ctx* ctx, const km_job* job, uint64_t* job_id) {
     if (!ctx->serve) return fail(ctx, KM_EINVAL, "context has no serving arena (km_init with arena_bytes > 0)");
     if (!job->X || !job->C_init || job->n < 1 || job->d < 1 || job->k < 1 || job->k > job->n)
         return fail(ctx, KM_EINVAL, "bad job shape");
+    if (job->flags & ~KM_JOB_DEVICE_DATA) return fail(ctx, KM_EINVAL, "unknown job flags 0x%x", job->flags);
+    if (job->flags & KM_JOB_DEVICE_DATA) {
+        for (const void* ptr : {(const void*)job->X, (const void*)job->C_init}) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+                at.device != ctx->device) {
+                cudaGetLastError();
+                return fail(ctx, KM_EINVAL, "KM_JOB_DEVICE_DATA: X and C_init must be device memory of device %d",
+                            ctx->device);
+            }
+        }
+    }
     km_status s = check_params(ctx, &job->p, job->d, job->k);
     if (s != KM_OK) return s;
     return serve_submit(ctx->serve, job, job_id, &ctx->err);

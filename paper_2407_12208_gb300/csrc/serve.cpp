@@ -4,12 +4,15 @@
 // are queued at km_submit.  A job is admitted as soon as (a) its memory --
 // data, centres, labels and its workspace -- fits in the caller's arena
 // (first-fit allocator, 256-byte blocks) and (b) one of the worker streams is
-// free; queued jobs are scanned in arrival order on every change, so a small
-// job can start while a large one waits for memory.  Each worker thread
-// drives its jobs on its own CUDA stream, so the kernels of concurrently
-// admitted jobs overlap on the device.  Results stay resident in the arena
-// until km_release.  Every device wait inside the kernels is bounded; a job
-// whose kernels time out finishes with KM_ETIMEOUT instead of hanging.
+// free (16 by default); queued jobs are scanned in arrival order on every
+// change, so a small job can start while a large one waits for memory.  Each
+// worker thread drives its jobs on its own CUDA stream, so the kernels of
+// concurrently admitted jobs overlap on the device; a Lloyd job replays its
+// iterations as recorded CUDA graphs (km_lloyd_run).  Jobs whose data is
+// resident on the device (KM_JOB_DEVICE_DATA) are read in place.  Results
+// stay resident in the arena until km_release.  Every device wait inside the
+// kernels is bounded; a job whose kernels time out finishes with KM_ETIMEOUT
+// instead of hanging.
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -69,7 +72,7 @@ struct km_serve {
     std::deque<Job*> ready;
     std::unordered_map<uint64_t, Job*> jobs;
     std::vector<std::thread> workers;
-    int n_workers = 4;
+    int n_workers = 16;
     int busy = 0;
     bool stop = false;
     uint64_t next_id = 1;
@@ -142,7 +145,8 @@ void km_serve::worker_loop() {
         char* base = arena + j->off;
         size_t o = 0;
         auto take = [&](size_t b) { char* p = base + o; o = up256(o + b); return p; };
-        j->dX = (float*)take(sizeof(float) * (size_t)s.n * s.d);
+        const bool resident = (s.flags & KM_JOB_DEVICE_DATA) != 0;
+        j->dX = resident ? const_cast<float*>(s.X) : (float*)take(sizeof(float) * (size_t)s.n * s.d);
         j->dC0 = (float*)take(sizeof(float) * (size_t)s.k * s.d);
         j->dC = (float*)take(sizeof(float) * (size_t)s.k * s.d);
         j->dlab = (int32_t*)take(sizeof(int32_t) * (size_t)s.n);
@@ -150,12 +154,19 @@ void km_serve::worker_loop() {
         j->dws = take(0);
         km_status rc = KM_OK;
         std::string err;
+        cudaError_t ce = cudaSuccess;
+        if (!j->cancel) {
+            if (resident) {
+                ce = cudaMemcpyAsync(j->dC0, s.C_init, sizeof(float) * (size_t)s.k * s.d, cudaMemcpyDeviceToDevice, st);
+            } else {
+                ce = cudaMemcpyAsync(j->dX, j->X.data(), sizeof(float) * j->X.size(), cudaMemcpyHostToDevice, st);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(j->dC0, j->C.data(), sizeof(float) * j->C.size(), cudaMemcpyHostToDevice, st);
+            }
+        }
         if (j->cancel) {
             rc = KM_ECANCELLED;
-        } else if (cudaMemcpyAsync(j->dX, j->X.data(), sizeof(float) * j->X.size(), cudaMemcpyHostToDevice, st) !=
-                       cudaSuccess ||
-                   cudaMemcpyAsync(j->dC0, j->C.data(), sizeof(float) * j->C.size(), cudaMemcpyHostToDevice, st) !=
-                       cudaSuccess) {
+        } else if (ce != cudaSuccess) {
             rc = KM_ECUDA;
             err = "copy into the arena failed";
         } else {
@@ -215,8 +226,9 @@ void serve_destroy(km_serve* s) {
 }
 
 km_status serve_submit(km_serve* s, const km_job* job, uint64_t* job_id, std::string* err) {
-    const size_t data = up256(sizeof(float) * (size_t)job->n * job->d) + 2 * up256(sizeof(float) * (size_t)job->k * job->d) +
-                        up256(sizeof(int32_t) * (size_t)job->n);
+    const bool resident = (job->flags & KM_JOB_DEVICE_DATA) != 0;
+    const size_t data = (resident ? 0 : up256(sizeof(float) * (size_t)job->n * job->d)) +
+                        2 * up256(sizeof(float) * (size_t)job->k * job->d) + up256(sizeof(int32_t) * (size_t)job->n);
     const size_t ws = km_internal_ws_bytes(job->n, job->d, job->k, &job->p);
     const size_t bytes = up256(data + ws);
     // a job larger than the whole arena can never be admitted (checked before
@@ -228,8 +240,10 @@ km_status serve_submit(km_serve* s, const km_job* job, uint64_t* job_id, std::st
     Job* j = new Job();
     j->spec = *job;
     j->bytes = bytes;
-    j->X.assign(job->X, job->X + (size_t)job->n * job->d);
-    j->C.assign(job->C_init, job->C_init + (size_t)job->k * job->d);
+    if (!resident) {
+        j->X.assign(job->X, job->X + (size_t)job->n * job->d);
+        j->C.assign(job->C_init, job->C_init + (size_t)job->k * job->d);
+    }
     j->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     j->id = s->next_id++;

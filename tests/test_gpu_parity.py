@@ -695,3 +695,32 @@ def test_precision_modes_rejected_where_undefined(ctx):
     with pytest.raises(pkg.KmError) as ei:
         ctx.distances(X, X[:4], pkg.params("e4m3", fallback="low"))
     assert ei.value.status == pkg._binding.KM_EUNSUPPORTED
+
+
+# ------------------------------------------- replayed (graph-recorded) iterations
+@pytest.mark.parametrize("low,shape", [("bf16", (30000, 128, 200)), ("fp16", (20000, 64, 64)),
+                                       ("fp32", (50000, 5, 16)), ("fp64", (5000, 16, 8))])
+def test_lloyd_graph_replay_equals_direct_launches(low, shape):
+    """km_lloyd_run replays its iterations as two recorded CUDA graphs; with
+    phase timing on it launches them kernel by kernel.  Both give the same
+    centres, labels, SSE and flag trajectories bit for bit, and the library
+    counts the same kernels."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = shape
+    X, C0 = workloads.gaussian_mixture(n, d, k, seed=90)
+    C0[-1] += 1e3  # an empty cluster in the first iteration
+    p = pkg.params(low, max_iter=7, empty="farthest")
+    out = []
+    for prof in (False, True):
+        c = pkg.Context(0)
+        c.set_profiling(prof)
+        l0 = c.launch_count()
+        C, lab, sse, eta, it = c.lloyd_run(_dev(X), _dev(C0), p)
+        torch.cuda.synchronize()
+        out.append((C.cpu().numpy(), lab.cpu().numpy(), sse.copy(), eta.copy(), it, c.launch_count() - l0))
+        c.close()
+    (Cg, lg, sg, eg, ig, ng), (Cd, ld, sd, ed, idd, nd) = out
+    assert ig == idd == 7 and ng == nd
+    assert np.array_equal(Cg.view(np.uint32), Cd.view(np.uint32))
+    assert np.array_equal(lg, ld)
+    assert np.array_equal(sg.view(np.uint64), sd.view(np.uint64)) and np.array_equal(eg, ed)

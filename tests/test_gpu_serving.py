@@ -99,3 +99,30 @@ def test_serving_cancel_and_release(sctx):
     r2 = _wait(sctx, j2)
     assert r2["status"] == pkg._binding.KM_OK
     sctx.release(j2)
+
+
+def test_serving_resident_data_equals_alone(sctx):
+    """Jobs whose points and centres are resident on the device
+    (KM_JOB_DEVICE_DATA, read in place) give the results of the same jobs
+    run alone, bit for bit, while they run side by side."""
+    import paper_2407_12208_gb300 as pkg
+    jobs = _jobs()
+    dev = [(torch.from_numpy(jb["X"]).cuda(), torch.from_numpy(jb["C"]).cuda()) for jb in jobs]
+    ids = [sctx.submit(Xd, Cd, pkg.params(jb["low"], max_iter=6), kind=jb["kind"]) for jb, (Xd, Cd) in zip(jobs, dev)]
+    results = [_wait(sctx, j) for j in ids]
+    for jb, (Xd, Cd), jid, r in zip(jobs, dev, ids, results):
+        assert r["status"] == pkg._binding.KM_OK, r["message"]
+        n, d = jb["X"].shape
+        k = jb["C"].shape[0]
+        lab_s = pkg.device_array(r["labels"], (n,), "<i4").cpu().numpy()
+        C_s = pkg.device_array(r["C"], (k, d), "<f4").cpu().numpy()
+        p = pkg.params(jb["low"], max_iter=6)
+        if jb["kind"] == 0:
+            C_a, lab_a, _, _, _ = sctx.lloyd_run(Xd, Cd, p)
+        else:
+            lab_a, _, _ = sctx.assign(Xd, Cd, p)
+            C_a = Cd
+        torch.cuda.synchronize()
+        assert np.array_equal(C_s.view(np.uint32), C_a.cpu().numpy().view(np.uint32))
+        assert np.array_equal(lab_s, lab_a.cpu().numpy())
+        sctx.release(jid)
