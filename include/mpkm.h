@@ -255,7 +255,15 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
  * receives the final centres, labels (n) the final reassignment.
  * sse_per_iter and eta_per_iter (nullable, host, max_iter + 1 doubles):
  * SSE and flagged fraction of every assignment, the last one being the
- * final reassignment.  iters_done (nullable, host). */
+ * final reassignment.  iters_done (nullable, host).
+ * The iterations are recorded once as two CUDA graphs (even and odd
+ * iterations) and replayed, one launch per iteration; with phase timing on
+ * (km_set_profiling) they are launched kernel by kernel, with the same
+ * results.  While the call records, another thread of the process must not
+ * synchronise the whole device (cudaDeviceSynchronize fails while any stream
+ * is being recorded); a stream the runtime refuses to record falls back to
+ * the direct launches.  With a legacy default stream the replays run on a
+ * stream of the context, ordered after and before the caller's work. */
 km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                        const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                        double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes,
@@ -350,7 +358,8 @@ typedef struct {
 /* Queues a job; it is admitted as soon as its memory (centres, labels and
  * workspace; the points too for host data) fits in the arena, up to 16 jobs
  * running at once, each on its own stream so that their kernels overlap on
- * the device; queued jobs are considered in arrival order on every change,
+ * the device (launched directly: no graph is recorded beside the caller's
+ * work); queued jobs are considered in arrival order on every change,
  * so a small job can start while a large one waits for memory.  Host arrays
  * are copied before the call returns.  KM_ENOMEM if the job could never fit
  * in the arena. */

@@ -867,13 +867,13 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
 static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                             const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                             double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
-                            const volatile int* cancel);
+                            const volatile int* cancel, bool allow_graphs);
 
 km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                        const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                        double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream) {
     return lloyd_impl(ctx, X, n, d, k, C_init, p, C_out, labels, sse_per_iter, eta_per_iter, iters_done, ws,
-                      ws_bytes, stream, nullptr);
+                      ws_bytes, stream, nullptr, true);
 }
 
 }  // extern "C"
@@ -948,7 +948,7 @@ static bool capture_iterations(km_ctx* ctx, const float* X, int64_t n, int d, in
 static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                             const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                             double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
-                            const volatile int* cancel) {
+                            const volatile int* cancel, bool allow_graphs) {
     km_status s = check_common(ctx, X, n, C_init, k, d);
     if (s != KM_OK) return s;
     if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
@@ -978,12 +978,15 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
     int t = 0;
     // Iterations as replays of two recorded graphs (C0 -> C1, C1 -> C0): one
     // launch per iteration instead of one per kernel.  Phase timing needs the
-    // direct launches (its events sit between the kernels).
+    // direct launches (its events sit between the kernels).  Recording happens
+    // here, in the caller's thread; the serving workers, which run beside the
+    // caller's own work, launch directly (a device-wide synchronisation
+    // elsewhere in the process fails while any stream is being recorded).
     cudaGraphExec_t ge[2] = {nullptr, nullptr};
     uint64_t nk[2] = {0, 0};
     cudaStream_t gs = st;
     bool graphs = false;
-    if (!ctx->prof && p->max_iter >= 2) {
+    if (allow_graphs && !ctx->prof && p->max_iter >= 2) {
         const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
         if (legacy) {
             if (!ctx->graph_st) CK(cudaStreamCreateWithFlags(&ctx->graph_st, cudaStreamNonBlocking));
@@ -1183,7 +1186,7 @@ km_status km_internal_run_job(km_ctx_view* v, const float* X, int64_t n, int d, 
     } else {
         std::vector<double> sh(p->max_iter + 1), eh(p->max_iter + 1);
         s = lloyd_impl(&ctx, X, n, d, k, C_init, p, C_out, labels, sh.data(), eh.data(), iters, ws, ws_bytes, st,
-                       cancel);
+                       cancel, false);
         if (s == KM_OK) {
             *sse = sh[*iters];
             double fl = 0;

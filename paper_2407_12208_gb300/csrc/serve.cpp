@@ -7,8 +7,9 @@
 // free (16 by default); queued jobs are scanned in arrival order on every
 // change, so a small job can start while a large one waits for memory.  Each
 // worker thread drives its jobs on its own CUDA stream, so the kernels of
-// concurrently admitted jobs overlap on the device; a Lloyd job replays its
-// iterations as recorded CUDA graphs (km_lloyd_run).  Jobs whose data is
+// concurrently admitted jobs overlap on the device (launched directly: a
+// graph recorded here would make a device-wide synchronisation in the
+// caller's threads fail while it is being recorded).  Jobs whose data is
 // resident on the device (KM_JOB_DEVICE_DATA) are read in place.  Results
 // stay resident in the arena until km_release.  Every device wait inside the
 // kernels is bounded; a job whose kernels time out finishes with KM_ETIMEOUT
