@@ -221,6 +221,43 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
                         int64_t* counts, double* shift_host, void* ws, size_t ws_bytes,
                         void* stream);
 
+/* ---- row-sharded updates: the exchange of a data-parallel Lloyd iteration --
+ * Eq. (center) is a sum over points, so with the rows of X split over
+ * several processes (one GPU each, C replicated) an iteration needs one
+ * exchange: the per-cluster sums and counts.  The library forms them as
+ * exact 64-bit fixed-point integers, so adding the shards' integers (an
+ * all-reduce of k (d + 1) int64, in any order) gives exactly the sums of the
+ * whole data and every process then finalises the same centres, bit for bit
+ * equal to one process holding all rows.  The fixed-point scale follows from
+ * the largest |x| over ALL shards and their total row count, agreed on first
+ * (a max- and a sum-reduction).  Empty clusters: each shard proposes its rows
+ * of largest min_dist (km_farthest_rows); the caller merges the candidates
+ * (largest min_dist first, ties to the lowest global row index). */
+
+/* max |x| over count floats as its binary32 bit pattern (non-negative floats
+ * order like their bits, so shards' values reduce with an integer maximum).
+ * ws: 256 bytes.  Synchronises `stream`. */
+km_status km_absmax(km_ctx* ctx, const float* X, int64_t count, uint32_t* bits_host, void* ws, size_t ws_bytes,
+                    void* stream);
+/* The shard's per-cluster fixed-point sums (k x d int64) and counts (k int64)
+ * of its rows (labels: n int32 in [0, k)), at the scale of absmax_bits (all
+ * shards' max |x|) and n_total (all shards' rows).  Device outputs; ws as
+ * km_workspace_size for the shard. */
+km_status km_update_partial(km_ctx* ctx, const float* X, int64_t n, int d, const int32_t* labels, int k,
+                            uint32_t absmax_bits, int64_t n_total, int64_t* sums, int64_t* counts, void* ws,
+                            size_t ws_bytes, void* stream);
+/* Centres from the summed integers: c_j = sum_j 2^-S / count_j in binary64,
+ * stored in fp32 (as km_update_centroids); an empty cluster keeps C_old's
+ * row (re-seed it afterwards); shift_host (nullable): max_j ||c_j - c_old_j||. */
+km_status km_update_finalize(km_ctx* ctx, const int64_t* sums, const int64_t* counts, int k, int d,
+                             uint32_t absmax_bits, int64_t n_total, const float* C_old, float* C_new,
+                             double* shift_host, void* ws, size_t ws_bytes, void* stream);
+/* The e rows of largest min_dist (ties to the lowest index), in that order:
+ * rows (e int64, device) and their min_dist (e doubles, device); 1 <= e <= n
+ * and e at most the k the workspace was sized for.  Synchronises `stream`. */
+km_status km_farthest_rows(km_ctx* ctx, const double* min_dist, int64_t n, int e, int64_t* rows, double* vals,
+                           void* ws, size_t ws_bytes, void* stream);
+
 /* Failure-path check (no paper counterpart): launches one warp that waits on
  * an mbarrier no thread arrives at.  The wait is the same bounded wait every
  * kernel of the library uses: after its budget (about a second) it sets the

@@ -31,7 +31,8 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_distances", "km_assign", "km_update_centroids", "km_lloyd_run", "km_get_stats",
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
-           "km_lloyd_step_host", "km_selftest_timeout", "km_quantize", "km_choose_low"]
+           "km_lloyd_step_host", "km_selftest_timeout", "km_quantize", "km_choose_low", "km_absmax",
+           "km_update_partial", "km_update_finalize", "km_farthest_rows"]
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -111,6 +112,11 @@ def load(path: str = LIB_PATH):
                                            sz, vp]
         lib.km_selftest_timeout.argtypes = [vp, vp, sz, vp]
         lib.km_quantize.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
+        lib.km_absmax.argtypes = [vp, vp, i64, c.POINTER(c.c_uint32), vp, sz, vp]
+        lib.km_update_partial.argtypes = [vp, vp, i64, i32, vp, i32, c.c_uint32, i64, vp, vp, vp, sz, vp]
+        lib.km_update_finalize.argtypes = [vp, vp, vp, i32, i32, c.c_uint32, i64, vp, vp, c.POINTER(c.c_double), vp, sz,
+                                           vp]
+        lib.km_farthest_rows.argtypes = [vp, vp, i64, i32, vp, vp, vp, sz, vp]
         lib.km_choose_low.argtypes = [vp, vp, i64, vp, i32, i32, c.c_double, c.POINTER(c.c_int32), vp, vp, sz, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
@@ -240,6 +246,51 @@ class Context:
                                            _stream(stream)))
         name = {v: kk for kk, v in LOW_NAMES.items()}[low.value]
         return name, {"bf16": (float(st[0]), float(st[1])), "e4m3": (float(st[2]), float(st[3]))}
+
+    # ---- row-sharded updates (the exchange of a data-parallel iteration)
+    def absmax(self, X, stream=None) -> int:
+        """km_absmax: max |x| of X as its binary32 bit pattern."""
+        import torch
+        ws = torch.empty(256, dtype=torch.uint8, device=X.device)
+        b = ctypes.c_uint32(0)
+        self._check(self.lib.km_absmax(self.h, _ptr(X), X.numel(), ctypes.byref(b), _ptr(ws), 256, _stream(stream)))
+        return b.value
+
+    def update_partial(self, X, labels, k, absmax_bits, n_total, p: Params = None, ws=None, stream=None):
+        """km_update_partial: (sums k x d int64, counts k int64) of this shard."""
+        import torch
+        n, d = X.shape
+        sums = torch.empty((k, d), dtype=torch.int64, device=X.device)
+        counts = torch.empty(k, dtype=torch.int64, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p or params("bf16"))
+        self._check(self.lib.km_update_partial(self.h, _ptr(X), n, d, _ptr(labels), int(k), ctypes.c_uint32(absmax_bits),
+                                               int(n_total), _ptr(sums), _ptr(counts), _ptr(ws), ws.numel(),
+                                               _stream(stream)))
+        return sums, counts
+
+    def update_finalize(self, sums, counts, C_old, absmax_bits, n_total, ws=None, stream=None):
+        """km_update_finalize: (C_new, shift); empty clusters keep C_old's rows."""
+        import torch
+        k, d = C_old.shape
+        C_new = torch.empty_like(C_old)
+        ws = ws if ws is not None else self.workspace(1, d, k, params("bf16"))
+        sh = ctypes.c_double(0.0)
+        self._check(self.lib.km_update_finalize(self.h, _ptr(sums), _ptr(counts), k, d, ctypes.c_uint32(absmax_bits),
+                                                int(n_total), _ptr(C_old), _ptr(C_new), ctypes.byref(sh), _ptr(ws),
+                                                ws.numel(), _stream(stream)))
+        return C_new, sh.value
+
+    def farthest_rows(self, min_dist, e, k=None, ws=None, stream=None):
+        """km_farthest_rows: (rows int64, min_dist values) of the e rows of
+        largest min_dist, ties to the lowest index."""
+        import torch
+        n = min_dist.numel()
+        rows = torch.empty(e, dtype=torch.int64, device=min_dist.device)
+        vals = torch.empty(e, dtype=torch.float64, device=min_dist.device)
+        ws = ws if ws is not None else self.workspace(n, 1, max(e, k or e), params("fp32"))
+        self._check(self.lib.km_farthest_rows(self.h, _ptr(min_dist), n, int(e), _ptr(rows), _ptr(vals), _ptr(ws),
+                                              ws.numel(), _stream(stream)))
+        return rows, vals
 
     def assign_static(self, X, C, labels, min_dist, stream=None):
         """km_assign_static: the fp32 direct assignment with the library's

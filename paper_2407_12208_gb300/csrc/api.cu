@@ -719,6 +719,96 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
     return KM_OK;
 }
 
+// ---- row-sharded centre updates (one exchange per Lloyd iteration) ----------
+km_status km_absmax(km_ctx* ctx, const float* X, int64_t count, uint32_t* bits_host, void* ws, size_t ws_bytes,
+                    void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!X || !bits_host || !ws) return fail(ctx, KM_EINVAL, "null argument");
+    if (count < 1) return fail(ctx, KM_EINVAL, "count must be >= 1");
+    if (!aligned256(ws) || ws_bytes < 256) return fail(ctx, KM_EINVAL, "workspace: 256 bytes, 256-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    unsigned* slot = reinterpret_cast<unsigned*>(ws);
+    KL(1, launch_absmax(X, count, slot, st));
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, slot, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *bits_host = h;
+    return KM_OK;
+}
+
+km_status km_update_partial(km_ctx* ctx, const float* X, int64_t n, int d, const int32_t* labels, int k,
+                            uint32_t absmax_bits, int64_t n_total, int64_t* sums, int64_t* counts, void* ws,
+                            size_t ws_bytes, void* stream) {
+    km_status s = check_common(ctx, X, n, labels, 1, d);
+    if (s != KM_OK) return s;
+    if (k < 1 || !sums || !counts || !ws) return fail(ctx, KM_EINVAL, "null output or workspace, or k < 1");
+    if (n_total < n) return fail(ctx, KM_EINVAL, "n_total=%lld is below this shard's n=%lld", (long long)n_total, (long long)n);
+    if (!(__builtin_isfinite(__builtin_bit_cast(float, absmax_bits))) || (absmax_bits >> 31))
+        return fail(ctx, KM_EINVAL, "absmax_bits is not a finite non-negative float");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    DevCounters* cnt = cv.take<DevCounters>(1);
+    UpdateWs u = carve_update(cv, n, d, k);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    (void)cnt;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(u.absmax, &absmax_bits, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    int nl = 0;
+    CK(launch_accumulate(X, n, d, labels, k, u.absmax, reinterpret_cast<long long*>(sums),
+                         reinterpret_cast<long long*>(counts), u.iscratch, u.perm, ctx->num_sms, st, nullptr, nullptr,
+                         &nl, n_total));
+    ctx->launches += (uint64_t)nl;
+    return KM_OK;
+}
+
+km_status km_update_finalize(km_ctx* ctx, const int64_t* sums, const int64_t* counts, int k, int d,
+                             uint32_t absmax_bits, int64_t n_total, const float* C_old, float* C_new,
+                             double* shift_host, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!sums || !counts || !C_old || !C_new || !ws) return fail(ctx, KM_EINVAL, "null argument");
+    if (k < 1 || d < 1 || n_total < 1) return fail(ctx, KM_EINVAL, "need k, d, n_total >= 1");
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    DevCounters* cnt = cv.take<DevCounters>(1);
+    UpdateWs u = carve_update(cv, 1, d, k);
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), st));
+    CK(cudaMemcpyAsync(u.absmax, &absmax_bits, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    int nl = 0;
+    CK(launch_finalize(reinterpret_cast<const long long*>(sums), reinterpret_cast<const long long*>(counts), u.absmax,
+                       n_total, k, d, C_old, KM_EMPTY_KEEP, nullptr, nullptr, C_new, nullptr, u.shift, u.esel,
+                       &cnt->status, ctx->num_sms, st, &nl, n_total));
+    ctx->launches += (uint64_t)nl;
+    if (shift_host) {
+        km_status s = sync_status(ctx, cnt, st);
+        if (s != KM_OK) return s;
+        CK(cudaMemcpy(shift_host, u.shift, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return KM_OK;
+}
+
+km_status km_farthest_rows(km_ctx* ctx, const double* min_dist, int64_t n, int e, int64_t* rows, double* vals,
+                           void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!min_dist || !rows || !vals || !ws) return fail(ctx, KM_EINVAL, "null argument");
+    if (n < 1 || e < 1 || (int64_t)e > n) return fail(ctx, KM_EINVAL, "need 1 <= e <= n (e=%d n=%lld)", e, (long long)n);
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    DevCounters* cnt = cv.take<DevCounters>(1);
+    void* esel = cv.take<unsigned char>(empty_select_bytes(e));
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(DevCounters), st));
+    KL(1, launch_farthest_rows(min_dist, n, e, reinterpret_cast<long long*>(rows), vals, esel, &cnt->status,
+                               ctx->num_sms, st));
+    return sync_status(ctx, cnt, st);
+}
+
 km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_old,
                         const km_params* p, int32_t* labels, double* min_dist, float* C_new, int64_t* counts,
                         double* shift_host, void* ws, size_t ws_bytes, void* stream) {

@@ -165,10 +165,12 @@ cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cud
 // md_out (nullable): each row's ||x_i - C_wd[labels[i]]||^2 to binary64
 // accuracy (the winner distances of launch_winner_dist, bit for bit), fused
 // into the pass over X where the kernel allows.  *nlaunch: kernels launched.
+// nscale (0: n): the row count that, with max |x|, fixes the fixed-point
+// scale (all shards' rows when the sums of several shards are added).
 cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
                               const unsigned* absmax_bits, long long* sums, long long* counts, int* iscratch,
                               int32_t* perm, int num_sms, cudaStream_t st, const float* C_wd, double* md_out,
-                              int* nlaunch);
+                              int* nlaunch, int64_t nscale = 0);
 // md[i] = ||x_i - C[labels[i]]||^2, Eq. (dist-direct), to binary64 accuracy
 // on the fp32 pipe (double-float arithmetic of df.cuh)
 cudaError_t launch_winner_dist(const float* X, int64_t n, int d, const float* C, const int32_t* labels, double* md,
@@ -182,7 +184,12 @@ size_t empty_select_bytes(int k);
 cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
                             int64_t n, int k, int d, const float* C_old, int empty_policy, const float* X,
                             const double* min_dist, float* C_new, int64_t* counts_out, double* shift,
-                            void* esel, unsigned* status, int num_sms, cudaStream_t st, int* nlaunch);
+                            void* esel, unsigned* status, int num_sms, cudaStream_t st, int* nlaunch,
+                            int64_t nscale = 0);
+// the e rows of largest min_dist (ties: lowest index), in that order, into
+// rows_out / vals_out; esel: empty_select_bytes(e) bytes
+cudaError_t launch_farthest_rows(const double* min_dist, int64_t n, int e, long long* rows_out, double* vals_out,
+                                 void* esel, unsigned* status, int num_sms, cudaStream_t st);
 // deterministic sum of n doubles (fixed two-level order)
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* partials, int nparts, double* out,
                            cudaStream_t st);

@@ -507,35 +507,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                     }
                 } else {
+                    // distance-matrix mode: Alg. 2's d = max(d^, 0) and its flag, every
+                    // pair; when K fits two 128-byte atoms the warp's 32 rows x 32
+                    // columns go through shared memory (lane = row, stride 33:
+                    // conflict-free both ways) so that each store writes 32
+                    // consecutive columns of one row
+                    float* tr = reinterpret_cast<float*>(smem + L.stage_off) + (size_t)(warp - 2) * 32 * 33;
+                    const int64_t row_w = rb * TC_BM + quarter * 32;  // the warp's first row
                     for (int ch = 0; ch < nch; ch++) {
                         const int col0 = nt * BN + ch * 32;
                         uint32_t v[32];
                         __syncwarp();
                         tmem_ld32_async(tbase + (uint32_t)(ch * 32), v);
                         tmem_wait_ld(v);
-                        if (!valid) continue;
                         const float4* q4 = reinterpret_cast<const float4*>(qg + col0);
                         const float4* s4 = reinterpret_cast<const float4*>(a.spad + col0);
-                        float e[32];
 #pragma unroll
                         for (int t4 = 0; t4 < 8; t4++) {
                             const float4 qq = __ldg(q4 + t4);
                             const float4 sc = FMT == 2 ? __ldg(s4 + t4) : make_float4(1.f, 1.f, 1.f, 1.f);
-                            e[4 * t4 + 0] = fmaf(__uint_as_float(v[4 * t4 + 0]) * sc.x, neg2s, qq.x);
-                            e[4 * t4 + 1] = fmaf(__uint_as_float(v[4 * t4 + 1]) * sc.y, neg2s, qq.y);
-                            e[4 * t4 + 2] = fmaf(__uint_as_float(v[4 * t4 + 2]) * sc.z, neg2s, qq.z);
-                            e[4 * t4 + 3] = fmaf(__uint_as_float(v[4 * t4 + 3]) * sc.w, neg2s, qq.w);
-                        }
-                        // distance-matrix mode: Alg. 2's d = max(d^, 0) and its flag, every pair
-                        float* drow = a.D + (size_t)row * a.k;
+                            const float ev[4] = {fmaf(__uint_as_float(v[4 * t4 + 0]) * sc.x, neg2s, qq.x),
+                                                 fmaf(__uint_as_float(v[4 * t4 + 1]) * sc.y, neg2s, qq.y),
+                                                 fmaf(__uint_as_float(v[4 * t4 + 2]) * sc.z, neg2s, qq.z),
+                                                 fmaf(__uint_as_float(v[4 * t4 + 3]) * sc.w, neg2s, qq.w)};
 #pragma unroll
-                        for (int t = 0; t < 32; t++) {
-                            const int j = col0 + t;
-                            if (j < a.k) {
-                                const float dh = fmaxf(p + e[t], 0.0f);
-                                const bool fl = (dh <= F) && KM_PAIR_FLAGGED(j, dh);
-                                // a flagged pair is marked -1 until its direct value replaces it
-                                drow[j] = fl ? -1.0f : dh;
+                            for (int c = 0; c < 4; c++) {
+                                const int t = 4 * t4 + c;
+                                const int j = col0 + t;
+                                const float dh = fmaxf(p + ev[c], 0.0f);
+                                const bool fl = valid && j < a.k && (dh <= F) && KM_PAIR_FLAGGED(j, dh);
                                 if (fl) {
                                     nflag++;
                                     const unsigned long long pos = atomicAdd(a.flag_queue_len, 1ull);
@@ -545,9 +545,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         atomicOr(&a.flag_bits[bit >> 5], 1u << (bit & 31));
                                     }
                                 }
+                                // a flagged pair is marked -1 until the fallback's value replaces it
+                                if constexpr (STG) tr[lane * 33 + t] = fl ? -1.0f : dh;
+                                else if (valid && j < a.k) a.D[(size_t)row * a.k + j] = fl ? -1.0f : dh;
                             }
                         }
-                    
+                        if constexpr (!STG) continue;  // (wide rows: no room to stage)
+                        __syncwarp();
+                        const int j = col0 + lane;
+#pragma unroll 4
+                        for (int r = 0; r < 32; r++) {
+                            const float val = tr[r * 33 + lane];
+                            if (row_w + r < a.n && j < a.k) a.D[(size_t)(row_w + r) * a.k + j] = val;
+                        }
                     }
                 }
                 tc_fence_before();
@@ -636,10 +646,10 @@ template <int FMT, int MODE>
 static cudaError_t launch_fmt(const CUtensorMap& mx, const CUtensorMap& mc, const TcArgs& a, int bn, int num_sms,
                               cudaStream_t st) {
     (void)bn;  // 128-column tiles: four TMEM accumulators
-    // assign mode stages the epilogue's values when K fits two 128-byte atoms
-    if constexpr (MODE == 0) {
-        if (a.kchunks <= 2) return launch_one<FMT, 128, MODE, true>(mx, mc, a, num_sms, st);
-    }
+    // both modes stage the epilogue's values in shared memory when K fits two
+    // 128-byte atoms (assign: the candidate walk; distance matrix: the
+    // transposed stores)
+    if (a.kchunks <= 2) return launch_one<FMT, 128, MODE, true>(mx, mc, a, num_sms, st);
     return launch_one<FMT, 128, MODE, false>(mx, mc, a, num_sms, st);
 }
 

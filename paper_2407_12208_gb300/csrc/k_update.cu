@@ -110,10 +110,10 @@ __global__ void k_absmax(const float* __restrict__ X, int64_t count, unsigned* o
 // the result does not depend on the order of the adds).
 template <bool SMEM>
 __global__ void k_accumulate(const float* __restrict__ X, int64_t n, int d, const int32_t* __restrict__ labels,
-                             int k, const unsigned* __restrict__ amax_bits, long long* __restrict__ sums,
+                             int k, const unsigned* __restrict__ amax_bits, int64_t nscale, long long* __restrict__ sums,
                              long long* __restrict__ counts) {
     extern __shared__ long long acc[];
-    const FixedScale fx(fixed_shift(*amax_bits, n));
+    const FixedScale fx(fixed_shift(*amax_bits, nscale));
     const int64_t kd = (int64_t)k * d;
     if (SMEM) {
         for (int64_t e = threadIdx.x; e < kd + k; e += blockDim.x) acc[e] = 0;
@@ -244,7 +244,7 @@ template <int NV4, int LPR, bool WD>
 __global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ? 1 : 2)) k_bucket_sum(const float* __restrict__ X, int64_t n, int d, int k, int seg,
                                                        const int* __restrict__ off,
                              const int* __restrict__ item_off, const int32_t* __restrict__ perm,
-                             const unsigned* __restrict__ amax_bits, long long* __restrict__ sums,
+                             const unsigned* __restrict__ amax_bits, int64_t nscale, long long* __restrict__ sums,
                              const float* __restrict__ C, double* __restrict__ md) {
     static_assert(LPR == 32 || NV4 == 1, "rows narrower than a warp take one float4 per lane");
     constexpr int G = 32 / LPR;                            // rows per warp load
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ?
     // per SM), else up to 16
     constexpr int RB = (NV4 == 1 && LPR == 32) ? 8 : ((16 / NV4) < (32 / G) ? 16 / NV4 : 32 / G);
     constexpr int STEP = RB * G;                           // rows per round (divides 32)
-    const FixedScale fx(fixed_shift(*amax_bits, n));
+    const FixedScale fx(fixed_shift(*amax_bits, nscale));
     const int lane = threadIdx.x & 31, sub = lane / LPR, cl = lane % LPR;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(256, (NV4 == 1 && LPR == 32) ? 3 : (NV4 == 4 ?
 template <int D>
 __global__ void k_bucket_sum_small(const float* __restrict__ X, int64_t n, int k, int seg, const int* __restrict__ off,
                                    const int* __restrict__ item_off, const int32_t* __restrict__ perm,
-                                   const unsigned* __restrict__ amax_bits, long long* __restrict__ sums) {
-    const FixedScale fx(fixed_shift(*amax_bits, n));
+                                   const unsigned* __restrict__ amax_bits, int64_t nscale, long long* __restrict__ sums) {
+    const FixedScale fx(fixed_shift(*amax_bits, nscale));
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -411,11 +411,11 @@ constexpr int AS_MAX_KD = 512;   // k * d bound of this path
 template <int D, bool WD>
 __global__ void __launch_bounds__(256) k_accum_small(const float* __restrict__ X, int64_t n, int k,
                                                      const int32_t* __restrict__ labels,
-                                                     const unsigned* __restrict__ amax_bits,
+                                                     const unsigned* __restrict__ amax_bits, int64_t nscale,
                                                      long long* __restrict__ sums, long long* __restrict__ counts,
                                                      const float* __restrict__ C, double* __restrict__ md) {
     extern __shared__ unsigned acc_sm[];  // per warp: 3 * k * D parts, then k counts; then C (WD)
-    const FixedScale fx(fixed_shift(*amax_bits, n));
+    const FixedScale fx(fixed_shift(*amax_bits, nscale));
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int kd = k * D;
     unsigned* a = acc_sm + (size_t)wib * (3 * kd + k);
@@ -596,9 +596,9 @@ cudaError_t launch_winner_dist(const float* X, int64_t n, int d, const float* C,
 
 // mean = sum 2^-S / m in binary64, stored in fp32 (the working precision).
 __global__ void k_means(const long long* __restrict__ sums, const long long* __restrict__ counts,
-                        const unsigned* __restrict__ amax_bits, int64_t n, int k, int d,
+                        const unsigned* __restrict__ amax_bits, int64_t nscale, int k, int d,
                         const float* __restrict__ C_old, float* __restrict__ C_new, int64_t* counts_out) {
-    const int S = fixed_shift(*amax_bits, n);
+    const int S = fixed_shift(*amax_bits, nscale);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)k * d;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / d);
@@ -688,12 +688,16 @@ KM_DEV void radix_pick(const unsigned* hist, bool descending, unsigned rank, uns
     }
 }
 
+// fixed_e > 0: no cluster lists; the fixed_e rows of largest min_dist go, in
+// that order, to rows_out / vals_out (a shard's candidates for the empty
+// clusters of a row-sharded update).
 __global__ void __launch_bounds__(256) k_empty_select(const long long* __restrict__ counts, int64_t n, int k, int d,
                                                       const float* __restrict__ X, const double* __restrict__ md,
                                                       float* __restrict__ C_new, EmptySel* es,
                                                       int* __restrict__ empties, unsigned long long* __restrict__ keys,
                                                       int* __restrict__ rows, int* __restrict__ order,
-                                                      unsigned* status) {
+                                                      unsigned* status, int fixed_e, long long* __restrict__ rows_out,
+                                                      double* __restrict__ vals_out) {
     __shared__ unsigned sh[256];
     __shared__ int wsum[8];
     const unsigned nb = gridDim.x;
@@ -702,7 +706,8 @@ __global__ void __launch_bounds__(256) k_empty_select(const long long* __restric
     if (blockIdx.x == 0) {
         for (int e = t; e < 12 * 256; e += blockDim.x) (&es->hist[0][0])[e] = 0u;
         int base = 0;
-        for (int j0 = 0; j0 < k; j0 += blockDim.x) {
+        if (fixed_e > 0) base = (int)min((int64_t)fixed_e, n);
+        for (int j0 = 0; fixed_e <= 0 && j0 < k; j0 += blockDim.x) {
             const int j = j0 + t;
             const int e = (j < k && counts[j] == 0) ? 1 : 0;
             int incl = e;
@@ -797,6 +802,14 @@ __global__ void __launch_bounds__(256) k_empty_select(const long long* __restric
         order[r] = rs;
     }
     if (!grid_barrier(es, nb, status)) return;
+    if (fixed_e > 0) {
+        for (int64_t r = gtid; r < E; r += gstride) {
+            const int row = __ldcg(order + r);
+            rows_out[r] = row;
+            vals_out[r] = md[row];
+        }
+        return;
+    }
     for (int64_t e = gtid; e < (int64_t)E * d; e += gstride) {
         const int r = (int)(e / d), l = (int)(e - (int64_t)r * d);
         C_new[(int64_t)__ldcg(empties + r) * d + l] = X[(int64_t)__ldcg(order + r) * d + l];
@@ -862,7 +875,8 @@ cudaError_t launch_absmax(const float* X, int64_t count, unsigned* out_bits, cud
 cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* labels, int k,
                               const unsigned* absmax_bits, long long* sums, long long* counts, int* iscratch,
                               int32_t* perm, int num_sms, cudaStream_t st, const float* C_wd, double* md_out,
-                              int* nlaunch) {
+                              int* nlaunch, int64_t nscale) {
+    if (nscale <= 0) nscale = n;  // the fixed-point scale of n rows (or of all shards' rows)
     // md_out: the rows' distances to their centres (C_wd) come out of the same
     // pass over X where the kernel has the row and its centre in hand, else
     // from the standalone kernel first (the same arithmetic either way)
@@ -883,12 +897,12 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         if (want_wd) {                                                                                              \
             e = allow_max_smem(k_accum_small<DD, true>);                                                            \
             if (e != cudaSuccess) return e;                                                                         \
-            k_accum_small<DD, true><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, sums, counts,  \
+            k_accum_small<DD, true><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, nscale, sums, counts,  \
                                                                        C_wd, md_out);                               \
         } else {                                                                                                    \
             e = allow_max_smem(k_accum_small<DD, false>);                                                           \
             if (e != cudaSuccess) return e;                                                                         \
-            k_accum_small<DD, false><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, sums, counts, \
+            k_accum_small<DD, false><<<(unsigned)blocks, 256, sm, st>>>(X, n, k, labels, absmax_bits, nscale, sums, counts, \
                                                                         nullptr, nullptr);                          \
         }                                                                                                           \
         break;
@@ -925,7 +939,7 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         // `seg` rows, about four per resident warp (fewer, longer items mean
         // fewer atomic adds per centre coordinate)
         typedef void (*BucketFn)(const float*, int64_t, int, int, int, const int*, const int*, const int32_t*,
-                                 const unsigned*, long long*, const float*, double*);
+                                 const unsigned*, int64_t, long long*, const float*, double*);
         BucketFn bfn = nullptr;
         if (d > 5) {
 #define KM_BS(NV, L) (fused ? (BucketFn)k_bucket_sum<NV, L, true> : (BucketFn)k_bucket_sum<NV, L, false>)
@@ -947,11 +961,11 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         const int64_t items = n / seg + k + 1;
         const unsigned blocks =
             (unsigned)std::max<int64_t>(1, std::min<int64_t>((items * 32 + 255) / 256, (int64_t)num_sms * std::max(per_sm, 1)));
-        if (d == 1) k_bucket_sum_small<1><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
-        else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, sums);
-        else bfn<<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, sums, C_wd, md_out);
+        if (d == 1) k_bucket_sum_small<1><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, nscale, sums);
+        else if (d == 2) k_bucket_sum_small<2><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, nscale, sums);
+        else if (d == 3) k_bucket_sum_small<3><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, nscale, sums);
+        else if (d == 5) k_bucket_sum_small<5><<<blocks, 256, 0, st>>>(X, n, k, seg, off, item_off, perm, absmax_bits, nscale, sums);
+        else bfn<<<blocks, 256, 0, st>>>(X, n, d, k, seg, off, item_off, perm, absmax_bits, nscale, sums, C_wd, md_out);
         if (nlaunch) *nlaunch = nl + 4;
         return cudaGetLastError();
     }
@@ -964,11 +978,11 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
         if (e != cudaSuccess) return e;
         const int64_t blk = std::min<int64_t>((int64_t)num_sms, (total + 511) / 512);
         k_accumulate<true><<<(unsigned)std::max<int64_t>(blk, 1), 512, smem, st>>>(X, n, d, labels, k, absmax_bits,
-                                                                                    sums, counts);
+                                                                                    nscale, sums, counts);
     } else {
         const int64_t blk = std::min<int64_t>((int64_t)num_sms * 8, (total + 511) / 512);
         k_accumulate<false><<<(unsigned)std::max<int64_t>(blk, 1), 512, 0, st>>>(X, n, d, labels, k, absmax_bits,
-                                                                                  sums, counts);
+                                                                                  nscale, sums, counts);
     }
     if (nlaunch) *nlaunch = nl + 1;
     return cudaGetLastError();
@@ -977,11 +991,12 @@ cudaError_t launch_accumulate(const float* X, int64_t n, int d, const int32_t* l
 cudaError_t launch_finalize(const long long* sums, const long long* counts, const unsigned* absmax_bits,
                             int64_t n, int k, int d, const float* C_old, int empty_policy, const float* X,
                             const double* min_dist, float* C_new, int64_t* counts_out, double* shift,
-                            void* esel, unsigned* status, int num_sms, cudaStream_t st, int* nlaunch) {
+                            void* esel, unsigned* status, int num_sms, cudaStream_t st, int* nlaunch, int64_t nscale) {
     int nl = 0;
     int64_t kd = (int64_t)k * d;
     int64_t blocks = min((int64_t)1024, (kd + 255) / 256);
-    k_means<<<(unsigned)blocks, 256, 0, st>>>(sums, counts, absmax_bits, n, k, d, C_old, C_new, counts_out);
+    k_means<<<(unsigned)blocks, 256, 0, st>>>(sums, counts, absmax_bits, nscale > 0 ? nscale : n, k, d, C_old, C_new,
+                                               counts_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     nl++;
@@ -999,8 +1014,13 @@ cudaError_t launch_finalize(const long long* sums, const long long* counts, cons
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_empty_select, 256, 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        void* args[] = {(void*)&counts, (void*)&n, (void*)&k, (void*)&d, (void*)&X, (void*)&min_dist, (void*)&C_new,
-                        (void*)&es, (void*)&empties, (void*)&keys, (void*)&rows, (void*)&order, (void*)&status};
+        int fixed_e = 0;
+        long long* rows_out = nullptr;
+        double* vals_out = nullptr;
+        void* args[] = {(void*)&counts, (void*)&n,     (void*)&k,     (void*)&d,      (void*)&X,
+                        (void*)&min_dist, (void*)&C_new, (void*)&es,   (void*)&empties, (void*)&keys,
+                        (void*)&rows,   (void*)&order, (void*)&status, (void*)&fixed_e, (void*)&rows_out,
+                        (void*)&vals_out};
         e = cudaLaunchCooperativeKernel((const void*)k_empty_select, dim3((unsigned)num_sms), dim3(256), args, 0, st);
         if (e != cudaSuccess) return e;
         nl++;
@@ -1013,6 +1033,30 @@ cudaError_t launch_finalize(const long long* sums, const long long* counts, cons
     nl++;
     if (nlaunch) *nlaunch = nl;
     return cudaGetLastError();
+}
+
+cudaError_t launch_farthest_rows(const double* min_dist, int64_t n, int e, long long* rows_out, double* vals_out,
+                                 void* esel, unsigned* status, int num_sms, cudaStream_t st) {
+    EmptySel* es = reinterpret_cast<EmptySel*>(esel);
+    char* tail = reinterpret_cast<char*>(esel) + ((sizeof(EmptySel) + 255) & ~(size_t)255);
+    int* empties = reinterpret_cast<int*>(tail);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(empties + e + (e & 1));
+    int* rows = reinterpret_cast<int*>(keys + e);
+    int* order = rows + e;
+    cudaError_t err = cudaMemsetAsync(es, 0, 2 * sizeof(unsigned), st);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_empty_select, 256, 0);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long* counts = nullptr;
+    int k = e, d = 0;
+    const float* X = nullptr;
+    float* C_new = nullptr;
+    void* args[] = {(void*)&counts, (void*)&n,     (void*)&k,     (void*)&d,  (void*)&X,    (void*)&min_dist,
+                    (void*)&C_new,  (void*)&es,    (void*)&empties, (void*)&keys, (void*)&rows, (void*)&order,
+                    (void*)&status, (void*)&e,     (void*)&rows_out, (void*)&vals_out};
+    return cudaLaunchCooperativeKernel((const void*)k_empty_select, dim3((unsigned)num_sms), dim3(256), args, 0, st);
 }
 
 cudaError_t launch_sum_f64(const double* v, int64_t n, double* partials, int nparts, double* out, cudaStream_t st) {

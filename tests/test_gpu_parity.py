@@ -725,3 +725,32 @@ def test_lloyd_graph_replay_equals_direct_launches(low, shape):
     assert np.array_equal(Cg.view(np.uint32), Cd.view(np.uint32))
     assert np.array_equal(lg, ld)
     assert np.array_equal(sg.view(np.uint64), sd.view(np.uint64)) and np.array_equal(eg, ed)
+
+
+# ------------------------------------------- row-sharded updates on one GPU
+def test_sharded_update_equals_whole(ctx):
+    """Two row shards' fixed-point partial sums, added as integers and
+    finalised, give km_update_centroids' centres of all rows bit for bit
+    (the exchange of a data-parallel iteration); km_farthest_rows orders the
+    rows by min_dist, ties to the lowest index."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = 30001, 32, 40
+    X, C = workloads.gaussian_mixture(n, d, k, seed=92)
+    lab = oracle.assign(X, C)[0]
+    lab[lab == 7] = 8  # an empty cluster
+    Xd, Cd, labd = _dev(X), _dev(C), _dev(lab)
+    bits = ctx.absmax(Xd)
+    assert bits == int(np.array([np.abs(X).max()], np.float32).view(np.uint32)[0])
+    cut = 12345
+    s1, c1 = ctx.update_partial(Xd[:cut], labd[:cut], k, bits, n)
+    s2, c2 = ctx.update_partial(Xd[cut:], labd[cut:], k, bits, n)
+    Cn, sh = ctx.update_finalize(s1 + s2, c1 + c2, Cd, bits, n)
+    Cr, cnt_r, sh_r = ctx.update_centroids(Xd, labd, Cd, pkg.params("bf16", empty="keep"))
+    torch.cuda.synchronize()
+    assert np.array_equal(Cn.cpu().numpy().view(np.uint32), Cr.cpu().numpy().view(np.uint32))
+    assert np.array_equal((c1 + c2).cpu().numpy(), cnt_r.cpu().numpy())
+    assert sh == sh_r
+    md = np.round(np.random.default_rng(3).random(n) * 1e3) / 1e3  # many ties
+    rows, vals = ctx.farthest_rows(_dev(md), 50, k=k)
+    ref = np.lexsort((np.arange(n), -md))[:50]
+    assert np.array_equal(rows.cpu().numpy(), ref) and np.array_equal(vals.cpu().numpy(), md[ref])

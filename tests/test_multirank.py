@@ -1,6 +1,6 @@
-"""Multi-rank host logic on CPU (gloo, world size 2): the bench's replicas
-report the slowest rank's time and the whole job's rate.  The assignment
-shards by rows with no exchange, so this is the whole N > 1 path."""
+"""Multi-rank host logic of the bench on CPU (gloo, world size 2): replicas
+report the slowest rank's time and the whole job's rate.  The exchange of a
+row-sharded Lloyd iteration is tested in test_sharded.py."""
 import os
 import socket
 import sys
