@@ -215,6 +215,12 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    # the screening kernel's epilogue variant for this shape, timed on this data
+    # (km_autotune: the fastest is kept for the shape class; results do not depend on it)
+    tuned = None
+    if tensor_path and not args.no_autotune:
+        v, tms = ctx.autotune(Xd, Cd, p, ws=ws, stream=stream)
+        tuned = {"variant": v, "ms_per_assign": dict(zip(("full", "half", "c32"), tms))}
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -372,7 +378,7 @@ def run_ours(args):
                        "step": "km_lloyd_step: quantise X (+ max |x|), screen, refine, certified argmin, min_dist, exact centre update",
                        "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "fp64_path": fp64, "serving": serving, "table6": table6,
+            "fp64_path": fp64, "serving": serving, "table6": table6, "autotune": tuned,
             "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},
             "eta": stats["flagged"] / max(stats["pairs"], 1),
             "assign_stats": {kk: stats[kk] for kk in ("fp32_evals", "fp64_evals", "ambiguous_rows", "overflow_rows")},
@@ -593,6 +599,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="rows (profiling a smaller case of the same kernels)")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-table6", action="store_true", help="skip the distance-matrix precision leg")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default screening variant (no km_autotune)")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-full", action="store_true",

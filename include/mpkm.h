@@ -196,6 +196,35 @@ km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int 
                     const km_params* p, int32_t* labels, double* min_dist,
                     uint64_t* n_flagged_host, void* ws, size_t ws_bytes, void* stream);
 
+/* Tuning of the screening kernel (no counterpart in the paper).  When K fits
+ * two 128-byte atoms (d <= 128 for FP16/BF16, d <= 256 for E4M3) the
+ * tensor-core kernel's epilogue comes in three variants that give the same
+ * labels, distances and counts: 64-column steps staging all 16 quads of a
+ * step in shared memory (KM_SV_FULL), 64-column steps staging 8 at a time,
+ * which leaves room for a second operand stage (KM_SV_HALF), and 32-column
+ * steps (KM_SV_C32).  Which is fastest depends on d, k and the data.  The
+ * context keeps one variant per shape class (format, ceil(d) in 128-byte
+ * atoms, ceil(k / 128), and whether n has fewer 128-row blocks than the GPU
+ * has SMs); its serving jobs use the same table.  Untuned classes take HALF
+ * when K is two atoms, else FULL. */
+enum { KM_SV_AUTO = -1, KM_SV_FULL = 0, KM_SV_HALF = 1, KM_SV_C32 = 2, KM_SV_REG = 3 };
+
+/* Times km_assign on the first min(n, 2^20) rows of X with each variant
+ * (one warm-up and three timed calls each, CUDA events on `stream`), keeps
+ * the fastest for this shape class and returns it in *variant_host
+ * (KM_SV_REG when K is wider than two atoms and nothing was timed; -1 for
+ * the direct formats).  ms_host (nullable, host, 3 floats): mean ms per call
+ * of FULL, HALF, C32.  labels: n int32 of device scratch.  ws: as km_assign.
+ * Synchronises `stream`. */
+km_status km_autotune(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
+                      int32_t* labels, int32_t* variant_host, float* ms_host, void* ws, size_t ws_bytes,
+                      void* stream);
+/* Sets the variant of the shape class of (n, d, k, low) to `variant`
+ * (KM_SV_FULL / HALF / C32), or with KM_SV_AUTO returns it to the default.
+ * KM_EUNSUPPORTED for a direct format or (unless KM_SV_AUTO) K wider than
+ * two atoms. */
+km_status km_set_screen_variant(km_ctx* ctx, int64_t n, int d, int k, int32_t low, int32_t variant);
+
 /* Centre update, Eq. (center), in precision higher than the working one
  * (Section 4.4): per-cluster sums are formed exactly in 64-bit fixed point
  * (order-independent, hence deterministic), divided in binary64 and stored

@@ -32,7 +32,9 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_submit", "km_poll", "km_release", "km_cancel", "km_set_profiling", "km_get_phase_times",
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
            "km_lloyd_step_host", "km_selftest_timeout", "km_quantize", "km_choose_low", "km_absmax",
-           "km_update_partial", "km_update_finalize", "km_farthest_rows"]
+           "km_update_partial", "km_update_finalize", "km_farthest_rows", "km_autotune",
+           "km_set_screen_variant"]
+SCREEN_VARIANTS = {"auto": -1, "full": 0, "half": 1, "c32": 2, "reg": 3}  # KM_SV_* of the C-ABI
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
 
@@ -118,6 +120,8 @@ def load(path: str = LIB_PATH):
                                            vp]
         lib.km_farthest_rows.argtypes = [vp, vp, i64, i32, vp, vp, vp, sz, vp]
         lib.km_choose_low.argtypes = [vp, vp, i64, vp, i32, i32, c.c_double, c.POINTER(c.c_int32), vp, vp, sz, vp]
+        lib.km_autotune.argtypes = [vp, vp, i64, vp, i32, i32, P, vp, c.POINTER(c.c_int32), vp, vp, sz, vp]
+        lib.km_set_screen_variant.argtypes = [vp, i64, i32, i32, i32, i32]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -216,6 +220,28 @@ class Context:
                                        _ptr(min_dist), ctypes.byref(nf) if want_flagged else None, _ptr(ws),
                                        ws.numel(), _stream(stream)))
         return labels, min_dist, (nf.value if want_flagged else None)
+
+    def autotune(self, X, C, p: Params, ws=None, stream=None):
+        """km_autotune: times the screening kernel's variants on this data and
+        keeps the fastest for the shape class.  Returns (variant name, ms per
+        call of full / half / c32, -1 where not timed)."""
+        import torch
+        n, d = X.shape
+        k = C.shape[0]
+        labels = torch.empty(n, dtype=torch.int32, device=X.device)
+        ws = ws if ws is not None else self.workspace(n, d, k, p)
+        v = ctypes.c_int32(0)
+        ms = (ctypes.c_float * 3)()
+        self._check(self.lib.km_autotune(self.h, _ptr(X), n, _ptr(C), k, d, ctypes.byref(p), _ptr(labels),
+                                         ctypes.byref(v), ms, _ptr(ws), ws.numel(), _stream(stream)))
+        names = {val: key for key, val in SCREEN_VARIANTS.items() if val >= 0}  # -1: a direct format
+        return names.get(v.value, "none"), [float(m) for m in ms]
+
+    def set_screen_variant(self, n, d, k, low, variant):
+        """km_set_screen_variant: pins ("full", "half", "c32") or clears ("auto")
+        the screening variant of the shape class."""
+        self._check(self.lib.km_set_screen_variant(self.h, n, d, k, LOW_NAMES[low] if isinstance(low, str) else int(low),
+                                                   SCREEN_VARIANTS[variant]))
 
     def quantize(self, X, low="bf16", stream=None):
         """km_quantize: (Xq as raw bytes n x (ldq * element size) uint8,

@@ -12,6 +12,7 @@
 #include <vector>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -21,6 +22,21 @@
 #include "serve.h"
 
 using namespace km;
+
+// Screening-kernel variant per shape class (format, K atoms, 128-column tiles
+// of C, fewer row blocks than SMs): set by km_autotune / km_set_screen_variant,
+// shared with the context's serving workers.
+struct km_tune {
+    std::mutex mu;
+    std::map<uint64_t, int> v;
+    static uint64_t key(int fmt, int kchunks, int k, int64_t n, int num_sms) {
+        const uint64_t nt = (uint64_t)((k + 127) / 128);
+        const uint64_t small = (n + 127) / 128 < num_sms ? 1 : 0;
+        return (uint64_t)fmt | ((uint64_t)kchunks << 4) | (nt << 8) | (small << 40);
+    }
+};
+// km_autotune's trial variant for the calling thread (-1: none)
+static thread_local int t_trial_variant = -1;
 
 struct km_ctx {
     int device = 0;
@@ -44,6 +60,10 @@ struct km_ctx {
     // is a legacy default stream (which cannot be captured)
     cudaStream_t graph_st = nullptr;
     cudaEvent_t graph_ev[2] = {nullptr, nullptr};
+    // screening-kernel variants: the context's own table, or (a serving job's
+    // context) the owning context's
+    km_tune tune_own;
+    km_tune* tune = &tune_own;
     ~km_ctx() {
         for (cudaEvent_t e : graph_ev)
             if (e) cudaEventDestroy(e);
@@ -342,6 +362,20 @@ km_status prepare_centres(km_ctx* ctx, const float* C, int k, int d, int fmt, co
 // One assignment of X against C into labels/min_dist (all device).
 // x_absmax (nullable, zeroed by the caller): max |x| over X, folded out of the
 // quantisation pass (tensor-core paths) or of the direct distances.
+// The epilogue variant of the screening kernel for this shape: km_autotune's
+// trial, else the tuned entry, else the default measured on GB300 (64-column
+// steps; half staging, and with it a second A stage, when K is two atoms).
+int screen_variant(km_ctx* ctx, int fmt, int kchunks, int k, int64_t n) {
+    if (kchunks > 2) return TC_SV_REG;
+    if (t_trial_variant >= 0) return t_trial_variant;
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune->mu);
+        auto it = ctx->tune->v.find(km_tune::key(fmt, kchunks, k, n, ctx->num_sms));
+        if (it != ctx->tune->v.end()) return it->second;
+    }
+    return kchunks == 2 ? TC_SV_HALF : TC_SV_FULL;
+}
+
 km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
                      int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st,
                      unsigned* x_absmax = nullptr) {
@@ -374,6 +408,7 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     a.kchunks = (ldq * esz + 127) / 128;
     a.xstat = w.xstat; a.xscale = w.xscale; a.cstat = w.cstat; a.qpad = w.qpad; a.spad = w.spad; a.colmax = w.colmax;
     a.tp = tp; a.mode = 0; a.cand = w.cand; a.rowinfo = w.rowinfo; a.cnt = w.cnt;
+    a.variant = screen_variant(ctx, fmt, a.kchunks, k, n);
     int qbits = 0;
     while ((1 << qbits) < (k + 3) / 4) qbits++;  // quad index bits (k <= 65535: at most 14)
     a.ebits = qbits + 4;
@@ -489,7 +524,7 @@ km_status km_init(km_ctx** out, int device, void* arena, size_t arena_bytes) {
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
     if (major != 10) { delete ctx; return KM_EUNSUPPORTED; }
     if (arena && arena_bytes) {
-        km_status s = serve_create(&ctx->serve, device, ctx->num_sms, arena, arena_bytes);
+        km_status s = serve_create(&ctx->serve, device, ctx->num_sms, ctx->tune, arena, arena_bytes);
         if (s != KM_OK) { delete ctx; return s; }
     }
     *out = ctx;
@@ -621,6 +656,87 @@ km_status km_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int 
         CK(cudaMemcpy(&f, &w.cnt->flagged, sizeof f, cudaMemcpyDeviceToHost));
         *n_flagged_host = f;
     }
+    return KM_OK;
+}
+
+namespace {
+struct TrialVariant {  // km_autotune's trial variant, cleared on every exit
+    explicit TrialVariant(int v) { t_trial_variant = v; }
+    ~TrialVariant() { t_trial_variant = -1; }
+};
+}  // namespace
+
+km_status km_autotune(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
+                      int32_t* labels, int32_t* variant_host, float* ms_host, void* ws, size_t ws_bytes,
+                      void* stream) {
+    km_status s = check_common(ctx, X, n, C, k, d);
+    if (s != KM_OK) return s;
+    if ((s = check_params(ctx, p, d, k)) != KM_OK) return s;
+    if (!labels || !variant_host) return fail(ctx, KM_EINVAL, "null argument");
+    if (ms_host)
+        for (int i = 0; i < 3; i++) ms_host[i] = -1.0f;
+    if (!is_tc(p->low)) {  // no screening kernel on the direct paths
+        *variant_host = -1;
+        return KM_OK;
+    }
+    const int fmt = fmt_of(p->low);
+    const int kchunks = (ldq_of(fmt, d) * (fmt == 2 ? 1 : 2) + 127) / 128;
+    if (kchunks > 2) {  // one variant only
+        *variant_host = TC_SV_REG;
+        return KM_OK;
+    }
+    const int64_t ns = std::min<int64_t>(n, (int64_t)1 << 20);  // rows timed (n >= k, so ns >= k)
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return fail(ctx, KM_ECUDA, "cudaEventCreate failed");
+    }
+    float best = INFINITY;
+    int bv = TC_SV_FULL;
+    for (int v = TC_SV_FULL; v <= TC_SV_C32 && s == KM_OK; v++) {
+        TrialVariant tv(v);
+        s = km_assign(ctx, X, ns, C, k, d, p, labels, nullptr, nullptr, ws, ws_bytes, stream);  // warm-up
+        if (s != KM_OK) break;
+        cudaEventRecord(ev[0], st);
+        for (int r = 0; r < 3 && s == KM_OK; r++)
+            s = km_assign(ctx, X, ns, C, k, d, p, labels, nullptr, nullptr, ws, ws_bytes, stream);
+        cudaEventRecord(ev[1], st);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+            if (s == KM_OK) s = fail(ctx, KM_ECUDA, "autotune timing failed");
+            break;
+        }
+        ms /= 3.0f;
+        if (ms_host) ms_host[v] = ms;
+        if (ms < best) { best = ms; bv = v; }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (s != KM_OK) return s;
+    if ((s = sync_status(ctx, ctx->last_cnt, st)) != KM_OK) return s;
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune->mu);
+        ctx->tune->v[km_tune::key(fmt, kchunks, k, n, ctx->num_sms)] = bv;
+    }
+    *variant_host = bv;
+    return KM_OK;
+}
+
+km_status km_set_screen_variant(km_ctx* ctx, int64_t n, int d, int k, int32_t low, int32_t variant) {
+    if (!ctx) return KM_EINVAL;
+    if (n < 1 || d < 1 || k < 1) return fail(ctx, KM_EINVAL, "need n, d, k >= 1");
+    if (!is_tc(low)) return fail(ctx, KM_EUNSUPPORTED, "no screening kernel for this format");
+    if (variant < -1 || variant > TC_SV_C32) return fail(ctx, KM_EINVAL, "variant %d out of range", variant);
+    const int fmt = fmt_of(low);
+    const int kchunks = (ldq_of(fmt, d) * (fmt == 2 ? 1 : 2) + 127) / 128;
+    if (kchunks > 2) return variant == -1 ? KM_OK : fail(ctx, KM_EUNSUPPORTED, "d=%d: one variant only", d);
+    std::lock_guard<std::mutex> lk(ctx->tune->mu);
+    const uint64_t key = km_tune::key(fmt, kchunks, k, n, ctx->num_sms);
+    if (variant == -1) ctx->tune->v.erase(key);
+    else ctx->tune->v[key] = variant;
     return KM_OK;
 }
 
@@ -1261,6 +1377,7 @@ km_status km_internal_run_job(km_ctx_view* v, const float* X, int64_t n, int d, 
     km_ctx ctx;
     ctx.device = v->device;
     ctx.num_sms = v->num_sms;
+    if (v->tune) ctx.tune = v->tune;
     km_status s;
     if (kind == 1) {
         s = km_assign(&ctx, X, n, C_init, k, d, p, labels, nullptr, nullptr, ws, ws_bytes, st);

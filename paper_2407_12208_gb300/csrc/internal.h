@@ -106,6 +106,11 @@ cudaError_t launch_rows_full(bool fp32_first, const float* X, const float* C, in
                              float gamma32, int num_sms, cudaStream_t st);
 
 // tensor-core screening kernel (tcgen05).  mode 0: candidates; mode 1: distance matrix.
+// Epilogue variants of mode 0 when K fits two 128-byte atoms (they give the same
+// results; which is fastest depends on the shape): 64-column steps with all 16
+// quads staged (FULL) or 8 at a time (HALF, which leaves shared memory for a
+// second A stage), or 32-column steps (C32).  Wider K: REG only.
+constexpr int TC_SV_FULL = 0, TC_SV_HALF = 1, TC_SV_C32 = 2, TC_SV_REG = 3;
 struct TcArgs {
     int64_t n;
     int k, d, fmt, kchunks;   // kchunks = number of 128-byte K atoms
@@ -117,6 +122,7 @@ struct TcArgs {
     const ColMax* colmax;
     TestParams tp;
     int mode;
+    int variant;              // mode 0 epilogue variant TC_SV_FULL / HALF / C32
     uint32_t* cand;           // mode 0: TC_GROUPS x TC_LIST x n quad entries (group, slot, row), common.cuh
     int ebits;                // low bits of an entry holding the quad index and mask: ceil(log2 ceil(k / 4)) + 4
     int4* rowinfo;            // n x TC_GROUPS: (count, overflow, window W bits, d^min bits) per epilogue group

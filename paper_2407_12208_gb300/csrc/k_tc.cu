@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -34,7 +35,6 @@
 namespace km {
 
 constexpr int TC_NG = TC_GROUPS;             // epilogue groups of four warps
-constexpr int TC_CW = 2;                     // 32-column TMEM chunks per epilogue step
 constexpr int TC_THREADS = 64 + 128 * TC_NG;  // producer warp, MMA warp, epilogue warps
 constexpr int TC_BM = 128;
 constexpr int TC_L = TC_LIST;  // candidate slots per row and epilogue group
@@ -45,10 +45,17 @@ struct TcLayout {
     size_t a_bytes, b_bytes, list_off, stage_off, bar_off, total;
 };
 
-// stg: each epilogue warp's staging area for its lanes' e values (8 TC_CW
-// float4 per lane, 4 TC_CW KB per warp)
-constexpr size_t TC_STAGE_BYTES = (size_t)TC_NG * 4 * (8 * TC_CW) * 32 * 16;
-__host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k, bool stg) {
+// Epilogue variants (TC_SV_*, internal.h): the columns per step (64, or 32
+// for C32) and the shared-memory staging of the walked quads: a float4 per
+// quad and lane, quad-major, for the step's 16 quads (FULL: 8 KB per warp) or
+// 8 quads at a time (HALF, C32: 4352 bytes per warp, which also holds the
+// distance-matrix mode's 32 x 33 transposed tile); REG stages nothing (quads
+// picked from registers).  Smaller staging leaves room for a second A stage.
+__host__ __device__ constexpr int tc_cw(int sv) { return sv == TC_SV_C32 ? 1 : 2; }
+__host__ __device__ constexpr size_t tc_stage_warp_bytes(int sv) {
+    return sv == TC_SV_REG ? 0 : (sv == TC_SV_FULL ? (size_t)16 * 32 * 16 : (size_t)4352);
+}
+__host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k, int sv) {
     TcLayout L;
     L.BN = BN;
     L.kchunks = kchunks;
@@ -57,7 +64,7 @@ __host__ __device__ inline TcLayout tc_layout(int BN, int kchunks, int k, bool s
     (void)k;
     const size_t lists = (size_t)TC_NG * (TC_L + 1) * TC_BM * 4   // per-row candidate lists (+1 dummy slot) of every group
                          + (size_t)TC_NG * TC_BM * 8;         // per-row running minimum published by each group
-    const size_t stage = stg ? TC_STAGE_BYTES : 0;
+    const size_t stage = (size_t)TC_NG * 4 * tc_stage_warp_bytes(sv);
     const size_t fixed = 1024 /*align slack*/ + lists + stage + 256 /*barriers*/;
     L.NA = 2;
     size_t rem = (size_t)SMEM_BUDGET - fixed - 2 * L.a_bytes;
@@ -153,7 +160,7 @@ KM_DEV float fmin3(float a, float b, float c) {
     return r;
 }
 
-template <int FMT, int BN, int MODE, bool STG>
+template <int FMT, int BN, int MODE, int SV>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, const TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
@@ -161,7 +168,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // every pointer below stays in the shared state space (LDS/STS, not generic)
     const uint32_t sraw = smem_u32(smem_raw);
     unsigned char* smem = smem_raw + (((sraw + 1023u) & ~1023u) - sraw);
-    const TcLayout L = tc_layout(BN, a.kchunks, a.k, STG);
+    constexpr bool STG = SV != TC_SV_REG;
+    constexpr int TC_CW = tc_cw(SV);  // 32-column TMEM chunks per epilogue step
+    const TcLayout L = tc_layout(BN, a.kchunks, a.k, SV);
     unsigned char* sA = smem;
     unsigned char* sB = smem + (size_t)L.NA * L.a_bytes;
     // q_j of every tile column (+inf on the padding: padded columns never win),
@@ -441,8 +450,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 fwhole = p + cmax <= Fall;  // padded columns hold +inf: never taken
                                 nflag += fwhole ? NCOL : 0;
                             }
-                            // one quad: its entry, and its flagged pairs while they are counted one by one
-                            auto take_quad = [&](float x0, float x1, float x2, float x3, int jq, bool act) {
+                            // one quad: its entry, and (FS) its flagged pairs while they are counted
+                            // one by one; the walk is compiled twice so that the common walk,
+                            // with no pair near its flag threshold, carries no flag arithmetic
+                            auto take_quad = [&](auto fs, float x0, float x1, float x2, float x3, int jq, bool act) {
+                                constexpr bool FS = decltype(fs)::value;
                                 const unsigned mk = (x0 <= cthr ? 1u : 0u) | (x1 <= cthr ? 2u : 0u) |
                                                     (x2 <= cthr ? 4u : 0u) | (x3 <= cthr ? 8u : 0u);
                                 const bool pc = act && mk != 0u && !ovf;
@@ -452,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 st_shared_u32(lbase + slot * (TC_BM * 4), quad_entry(jq >> 2, mk, p + qmn, emask));
                                 ovf |= (pc && !room);
                                 cnt += (pc && room) ? 1 : 0;
-                                if (fstep) {
+                                if constexpr (FS) {
                                     const float xs4[4] = {x0, x1, x2, x3};
 #pragma unroll
                                     for (int c = 0; c < 4; c++) {
@@ -465,45 +477,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             // A row whose list overflowed takes no more candidates: it walks
                             // its quads only while flagged pairs remain to be counted one by one.
                             const unsigned walk = (ovf && !(fstep && !fwhole)) ? 0u : qmask;
-                            if (STG) {
-                                // the lane's values staged in shared memory (quad-major: the
-                                // 32 lanes of a quad side by side, conflict-free both ways),
-                                // then one loop over all its quads: a 16-byte read per quad
-                                const uint32_t stg = smem_u32(smem) + (uint32_t)L.stage_off + (uint32_t)(((warp - 2) * NQ * 32 + lane) * 16);
+                            auto run_walk = [&](auto fs) {
+                                if constexpr (STG) {
+                                    // the lane's quads to walk staged in shared memory (quad-major:
+                                    // the 32 lanes of a quad side by side, conflict-free both ways),
+                                    // then one loop over them: a 16-byte read per quad.  Each lane
+                                    // reads back only what it wrote itself.  HALF stages and walks
+                                    // the step's two 32-column halves one after the other.
+                                    constexpr int NH = SV == TC_SV_HALF ? 2 : 1, QH = NQ / NH;
+                                    const uint32_t stg = smem_u32(smem) + (uint32_t)L.stage_off +
+                                                         (uint32_t)((warp - 2) * tc_stage_warp_bytes(SV) + lane * 16);
 #pragma unroll
-                                for (int qd = 0; qd < NQ; qd++)
-                                    st_shared_v4(stg + qd * 512, e[4 * qd], e[4 * qd + 1], e[4 * qd + 2], e[4 * qd + 3]);
-                                unsigned ph = walk;
-                                while (__any_sync(0xffffffffu, ph)) {
-                                    const bool act = ph != 0;
-                                    const int qd = act ? __ffs(ph) - 1 : 0;
-                                    ph &= ph - 1;
-                                    const float4 ev = ld_shared_v4(stg + qd * 512);
-                                    take_quad(ev.x, ev.y, ev.z, ev.w, col0 + 4 * qd, act);
-                                }
-                            } else {
+                                    for (int hh = 0; hh < NH; hh++) {
+                                        unsigned ph = (walk >> (QH * hh)) & ((1u << QH) - 1u);
 #pragma unroll
-                                for (int half = 0; half < TC_CW; half++) {
-                                    unsigned ph = (walk >> (8 * half)) & 0xffu;
-                                    const float* eh = e + 32 * half;
-                                    while (__any_sync(0xffffffffu, ph)) {
-                                        const bool act = ph != 0;
-                                        const int qd = act ? __ffs(ph) - 1 : 0;
-                                        ph &= ph - 1;
-                                        // the quad's values picked from registers by a select tree
-                                        const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
-                                        float et[4];
-#pragma unroll
-                                        for (int c = 0; c < 4; c++) {
-                                            const float s0 = b0 ? eh[4 + c] : eh[c], s1 = b0 ? eh[12 + c] : eh[8 + c];
-                                            const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
-                                            const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
-                                            et[c] = b2 ? t1 : t0;
+                                        for (int qd = 0; qd < QH; qd++)
+                                            if ((ph >> qd) & 1u)
+                                                st_shared_v4(stg + qd * 512, e[4 * (QH * hh + qd)], e[4 * (QH * hh + qd) + 1],
+                                                             e[4 * (QH * hh + qd) + 2], e[4 * (QH * hh + qd) + 3]);
+                                        while (__any_sync(0xffffffffu, ph)) {
+                                            const bool act = ph != 0;
+                                            const int qd = act ? __ffs(ph) - 1 : 0;
+                                            ph &= ph - 1;
+                                            const float4 ev = ld_shared_v4(stg + qd * 512);
+                                            take_quad(fs, ev.x, ev.y, ev.z, ev.w, col0 + 4 * (QH * hh + qd), act);
                                         }
-                                        take_quad(et[0], et[1], et[2], et[3], col0 + 32 * half + 4 * qd, act);
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int half = 0; half < TC_CW; half++) {
+                                        unsigned ph = (walk >> (8 * half)) & 0xffu;
+                                        const float* eh = e + 32 * half;
+                                        while (__any_sync(0xffffffffu, ph)) {
+                                            const bool act = ph != 0;
+                                            const int qd = act ? __ffs(ph) - 1 : 0;
+                                            ph &= ph - 1;
+                                            // the quad's values picked from registers by a select tree
+                                            const bool b0 = qd & 1, b1 = qd & 2, b2 = qd & 4;
+                                            float et[4];
+#pragma unroll
+                                            for (int c = 0; c < 4; c++) {
+                                                const float s0 = b0 ? eh[4 + c] : eh[c], s1 = b0 ? eh[12 + c] : eh[8 + c];
+                                                const float s2 = b0 ? eh[20 + c] : eh[16 + c], s3 = b0 ? eh[28 + c] : eh[24 + c];
+                                                const float t0 = b1 ? s1 : s0, t1 = b1 ? s3 : s2;
+                                                et[c] = b2 ? t1 : t0;
+                                            }
+                                            take_quad(fs, et[0], et[1], et[2], et[3], col0 + 32 * half + 4 * qd, act);
+                                        }
                                     }
                                 }
-                            }
+                            };
+                            if (fstep) run_walk(std::true_type{});
+                            else run_walk(std::false_type{});
                         }
                     }
                 } else {
@@ -624,21 +649,21 @@ size_t tc_smem_bytes(int fmt, int d, int k) {
     const int ldq = (fmt == 2) ? ((d + 15) / 16) * 16 : ((d + 7) / 8) * 8;
     const int kchunks = (ldq * esize + 127) / 128;
     const int bn = pick_bn(kchunks, k);
-    TcLayout L = tc_layout(bn, kchunks, k, kchunks <= 2);
+    TcLayout L = tc_layout(bn, kchunks, k, kchunks <= 2 ? TC_SV_HALF : TC_SV_REG);
     if (L.NS < 2) return 0;
     return L.total;
 }
 
-template <int FMT, int BN, int MODE, bool STG>
+template <int FMT, int BN, int MODE, int SV>
 static cudaError_t launch_one(const CUtensorMap& mx, const CUtensorMap& mc, const TcArgs& a, int num_sms,
                               cudaStream_t st) {
-    TcLayout L = tc_layout(BN, a.kchunks, a.k, STG);
+    TcLayout L = tc_layout(BN, a.kchunks, a.k, SV);
     if (L.NS < 2) return cudaErrorInvalidConfiguration;
-    cudaError_t e = allow_max_smem(k_tc<FMT, BN, MODE, STG>);
+    cudaError_t e = allow_max_smem(k_tc<FMT, BN, MODE, SV>);
     if (e != cudaSuccess) return e;
     const int64_t nrb = (a.n + TC_BM - 1) / TC_BM;
     const int grid = (int)std::min<int64_t>(nrb, (int64_t)num_sms);
-    k_tc<FMT, BN, MODE, STG><<<grid, TC_THREADS, L.total, st>>>(mx, mc, a);
+    k_tc<FMT, BN, MODE, SV><<<grid, TC_THREADS, L.total, st>>>(mx, mc, a);
     return cudaGetLastError();
 }
 
@@ -647,10 +672,16 @@ static cudaError_t launch_fmt(const CUtensorMap& mx, const CUtensorMap& mc, cons
                               cudaStream_t st) {
     (void)bn;  // 128-column tiles: four TMEM accumulators
     // both modes stage the epilogue's values in shared memory when K fits two
-    // 128-byte atoms (assign: the candidate walk; distance matrix: the
-    // transposed stores)
-    if (a.kchunks <= 2) return launch_one<FMT, 128, MODE, true>(mx, mc, a, num_sms, st);
-    return launch_one<FMT, 128, MODE, false>(mx, mc, a, num_sms, st);
+    // 128-byte atoms (assign: the candidate walk, in the variant a.variant
+    // names; distance matrix: the transposed stores)
+    if (a.kchunks > 2) return launch_one<FMT, 128, MODE, TC_SV_REG>(mx, mc, a, num_sms, st);
+    if constexpr (MODE == 1) {
+        return launch_one<FMT, 128, MODE, TC_SV_HALF>(mx, mc, a, num_sms, st);
+    } else {
+        if (a.variant == TC_SV_FULL) return launch_one<FMT, 128, MODE, TC_SV_FULL>(mx, mc, a, num_sms, st);
+        if (a.variant == TC_SV_C32) return launch_one<FMT, 128, MODE, TC_SV_C32>(mx, mc, a, num_sms, st);
+        return launch_one<FMT, 128, MODE, TC_SV_HALF>(mx, mc, a, num_sms, st);
+    }
 }
 
 cudaError_t launch_tc(const void* Xq, const void* Cq, int ldq, const TcArgs& a, int num_sms, cudaStream_t st) {

@@ -63,6 +63,7 @@ size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct km_serve {
     int device = 0, num_sms = 148;
+    km_tune* tune = nullptr;
     char* arena = nullptr;
     size_t arena_bytes = 0;
     size_t arena_usable = 0;  // the aligned part of the arena: no job larger than this ever fits
@@ -130,7 +131,7 @@ void km_serve::worker_loop() {
     cudaSetDevice(device);
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    km_ctx_view view{device, num_sms};
+    km_ctx_view view{device, num_sms, tune};
     for (;;) {
         Job* j = nullptr;
         {
@@ -193,10 +194,11 @@ void km_serve::worker_loop() {
     cudaStreamDestroy(st);
 }
 
-km_status serve_create(km_serve** out, int device, int num_sms, void* arena, size_t arena_bytes) {
+km_status serve_create(km_serve** out, int device, int num_sms, km_tune* tune, void* arena, size_t arena_bytes) {
     km_serve* s = new km_serve();
     s->device = device;
     s->num_sms = num_sms;
+    s->tune = tune;
     s->arena = (char*)arena;
     s->arena_bytes = arena_bytes;
     const uintptr_t a0 = (uintptr_t)arena, a1 = up256(a0);

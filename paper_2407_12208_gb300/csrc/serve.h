@@ -9,12 +9,14 @@
 #include "../../include/mpkm.h"
 
 struct km_serve;
+struct km_tune;  // the owning context's table of screening-kernel variants (api.cu)
 struct km_ctx_view {
     int device;
     int num_sms;
+    km_tune* tune;
 };
 
-km_status serve_create(km_serve** out, int device, int num_sms, void* arena, size_t arena_bytes);
+km_status serve_create(km_serve** out, int device, int num_sms, km_tune* tune, void* arena, size_t arena_bytes);
 void serve_destroy(km_serve* s);
 km_status serve_submit(km_serve* s, const km_job* job, uint64_t* job_id, std::string* err);
 km_status serve_poll(km_serve* s, uint64_t job_id, km_result* out);
