@@ -13,7 +13,8 @@ step end to end from pinned host buffers through km_lloyd_step_host (`e2e`),
 the oracle on the host cores (`cpu_baseline`), the plain FP64 path on a row
 sample (`fp64_path`), the served stream's latencies (`serving`), the
 distance-matrix precision modes in the structure of the paper's Tables 6.1 /
-6.2 (`table6`), SM clocks
+6.2 (`table6`), clustering quality in the structure of Tables 6.3-6.7
+(`quality`), SM clocks
 sampled during the timed region (`clocks`) and the library's own launch count
 (`gpu_launches`).  `--impl reference` times the CPU oracle instead (on a
 bounded sample of the same workload).  Multi-GPU (torchrun): independent
@@ -367,6 +368,12 @@ def run_ours(args):
     table6 = None
     if rank == 0 and not args.only_step and not args.no_table6:
         table6 = table6_leg(args, local)
+    quality = None
+    if rank == 0 and not args.only_step and not args.no_quality:
+        try:
+            quality = quality_leg(args, local)
+        except Exception as exc:  # a failing side leg must not lose the line
+            quality = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     if rank == 0:
         line = {
@@ -378,7 +385,7 @@ def run_ours(args):
                        "step": "km_lloyd_step: quantise X (+ max |x|), screen, refine, certified argmin, min_dist, exact centre update",
                        "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "fp64_path": fp64, "serving": serving, "table6": table6, "autotune": tuned,
+            "fp64_path": fp64, "serving": serving, "table6": table6, "quality": quality, "autotune": tuned,
             "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},
             "eta": stats["flagged"] / max(stats["pairs"], 1),
             "assign_stats": {kk: stats[kk] for kk in ("fp32_evals", "fp64_evals", "ambiguous_rows", "overflow_rows")},
@@ -398,6 +405,171 @@ TABLE6_MODES = [
     ("uniform FP16", "fp16", "off", "fp64"), ("uniform BF16", "bf16", "off", "fp64"),
     ("FP32 direct", "fp32", "tc", "fp64"), ("FP64 direct", "fp64", "tc", "fp64"),
 ]
+
+
+# ------------------------------------------------------- clustering quality
+# The measures of Section 6.2, written from their definitions: the adjusted
+# Rand index, the adjusted mutual information (arithmetic normalisation, the
+# expected mutual information under the hypergeometric model of Vinh, Epps
+# and Bailey 2010), and Table 6.7's `Diff`: the share of labels that differ
+# from a reference after the one-to-one matching of cluster ids that agrees
+# most.
+def contingency(a, b):
+    import numpy as np
+    ua, ia = np.unique(np.asarray(a), return_inverse=True)
+    ub, ib = np.unique(np.asarray(b), return_inverse=True)
+    m = np.bincount(ia.ravel() * len(ub) + ib.ravel(), minlength=len(ua) * len(ub))
+    return m.reshape(len(ua), len(ub)).astype(np.int64)
+
+
+def adjusted_rand_index(a, b) -> float:
+    import numpy as np
+    m = contingency(a, b)
+    n = int(m.sum())
+    c2 = lambda x: x * (x - 1) / 2.0
+    sij = float(c2(m.astype(np.float64)).sum())
+    sa = float(c2(m.sum(1).astype(np.float64)).sum())
+    sb = float(c2(m.sum(0).astype(np.float64)).sum())
+    expected = sa * sb / c2(float(n))
+    top = 0.5 * (sa + sb)
+    if top == expected:  # both partitions trivial in the same way
+        return 1.0
+    return (sij - expected) / (top - expected)
+
+
+def _entropy(counts, n) -> float:
+    import numpy as np
+    p = counts[counts > 0] / float(n)
+    return float(-(p * np.log(p)).sum())
+
+
+def _expected_mutual_info(av, bv, n) -> float:
+    """Sum over row sizes a, column sizes b and cell counts nij of
+    nij/n log(n nij / (a b)) times the hypergeometric probability of nij;
+    equal cluster sizes are summed once with their multiplicity."""
+    import numpy as np
+    from scipy.special import gammaln
+    ua, wa = np.unique(np.asarray(av, dtype=np.int64), return_counts=True)
+    ub, wb = np.unique(np.asarray(bv, dtype=np.int64), return_counts=True)
+    lgb, lgnb, lgn = gammaln(ub + 1.0), gammaln(n - ub + 1.0), gammaln(n + 1.0)
+    emi = 0.0
+    for ai, wi in zip(ua, wa):
+        lo = np.maximum(1, ai + ub - n)
+        hi = np.minimum(ai, ub)
+        cnt = np.maximum(hi - lo + 1, 0)
+        tot = int(cnt.sum())
+        if tot == 0:
+            continue
+        jj = np.repeat(np.arange(len(ub)), cnt)
+        nij = (lo[jj] + np.arange(tot) - np.repeat(np.cumsum(cnt) - cnt, cnt)).astype(np.float64)
+        b = ub[jj].astype(np.float64)
+        lp = (gammaln(ai + 1.0) + lgb[jj] + gammaln(n - ai + 1.0) + lgnb[jj] - lgn - gammaln(nij + 1.0)
+              - gammaln(ai - nij + 1.0) - gammaln(b - nij + 1.0) - gammaln(n - ai - b + nij + 1.0))
+        emi += float(wi) * float((wb[jj] * nij / n * np.log(n * nij / (ai * b)) * np.exp(lp)).sum())
+    return emi
+
+
+def adjusted_mutual_info(a, b) -> float:
+    import numpy as np
+    m = contingency(a, b)
+    n = int(m.sum())
+    av, bv = m.sum(1), m.sum(0)
+    if (len(av) == 1 and len(bv) == 1) or (len(av) == n and len(bv) == n):
+        return 1.0
+    nz = m > 0
+    outer = np.outer(av, bv).astype(np.float64)
+    mi = float((m[nz] / n * np.log(n * m[nz] / outer[nz])).sum())
+    emi = _expected_mutual_info(av, bv, n)
+    norm = 0.5 * (_entropy(av, n) + _entropy(bv, n))
+    den = norm - emi
+    den = min(den, -1e-15) if den < 0 else max(den, 1e-15)
+    return (mi - emi) / den
+
+
+def matched_label_diff(ref, lab) -> float:
+    """Share of labels that differ from ref after the best one-to-one matching
+    of cluster ids (Hungarian method on the contingency table)."""
+    from scipy.optimize import linear_sum_assignment
+    m = contingency(ref, lab)
+    r, c = linear_sum_assignment(-m)
+    return 1.0 - float(m[r, c].sum()) / float(m.sum())
+
+
+def quality_leg(args, device: int) -> dict:
+    """Clustering quality in the structure of Tables 6.3-6.6 (Gaussian blobs,
+    n = 1e5, d in {10, 128}, k in {100, 500}) and Table 6.7 (image
+    segmentation; a 1024 x 1024 Voronoi image with features (R, G, B, x, y)
+    stands in for the ImageNet images, k in {8, 32}): Lloyd runs to
+    tau = 1e-8 or 300 iterations from the same seeded initial centres, per
+    method the time (CUDA events around km_lloyd_run, after one warm-up run),
+    iterations, final SSE, ARI and AMI against the blobs' true labels, and
+    Diff against the FP64 run's labels.  The mixed methods certify every
+    argmin (labels equal the binary64 argmin wherever the margin exceeds the
+    proved bounds), so they are expected to reproduce the FP64 run."""
+    import numpy as np
+    import torch
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import workloads
+    ctx = pkg.Context(device)
+    dev = torch.device("cuda", device)
+    out = {"tau": 1e-8, "max_iter": 300, "blobs": {}, "image": {}}
+
+    def run(Xd, C0d, low, rho):
+        p = pkg.params(low, "tc", rho=rho, max_iter=300, tau=1e-8)
+        n, d = Xd.shape
+        ws = ctx.workspace(n, d, C0d.shape[0], p)
+        ctx.lloyd_run(Xd, C0d, p, ws=ws)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C, lab, sse, eta, it = ctx.lloyd_run(Xd, C0d, p, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, it, float(sse[-1]), lab.cpu().numpy(), float(np.mean(eta))
+
+    def methods(d):
+        m = [("FP64", "fp64", 5.0), ("FP32", "fp32", 5.0)]
+        for low, name in (("bf16", "BF16->FP64"), ("fp16", "FP16->FP64")):
+            for rho in (5.0, 10.0, 50.0):
+                m.append(("%s rho=%g" % (name, rho), low, rho))
+        if d >= 16:
+            m.append(("E4M3->FP64 rho=5", "e4m3", 5.0))
+        return m
+
+    for d, k in ((10, 100), (10, 500), (128, 100), (128, 500)):
+        X, C0, truth = workloads.blobs(100_000, d, k, seed=31 + d + k, with_labels=True)
+        Xd, C0d = torch.from_numpy(X).to(dev), torch.from_numpy(C0).to(dev)
+        rows, ref, cache = {}, None, {}
+        for name, low, rho in methods(d):
+            t, it, sse, lab, eta = run(Xd, C0d, low, rho)
+            key = lab.tobytes()
+            if key not in cache:
+                cache[key] = (adjusted_mutual_info(truth, lab), adjusted_rand_index(truth, lab))
+            ami, ari = cache[key]
+            if ref is None:
+                ref = lab
+            rows[name] = {"time_s": t, "iters": it, "sse": sse, "ami": ami, "ari": ari,
+                          "diff_vs_fp64": matched_label_diff(ref, lab), "eta": eta}
+        t64 = rows["FP64"]["time_s"]
+        for r in rows.values():
+            r["speedup_vs_fp64"] = t64 / r["time_s"]
+        out["blobs"]["n=100000 d=%d k=%d" % (d, k)] = rows
+    X, _ = workloads.voronoi_image(1024, 1024, 16, 8, seed=47)
+    Xd = torch.from_numpy(X).to(dev)
+    for k in (8, 32):
+        C0 = X[workloads.init_indices(X.shape[0], k, 48 + k)].copy()
+        C0d = torch.from_numpy(C0).to(dev)
+        rows, ref = {}, None
+        for name, low, rho in (("FP64", "fp64", 5.0), ("FP32", "fp32", 5.0), ("BF16->FP64 rho=5", "bf16", 5.0),
+                               ("FP16->FP64 rho=5", "fp16", 5.0)):
+            t, it, sse, lab, eta = run(Xd, C0d, low, rho)
+            if ref is None:
+                ref = lab
+            rows[name] = {"time_s": t, "iters": it, "sse": sse, "diff_vs_fp64": matched_label_diff(ref, lab),
+                          "eta": eta}
+        out["image"]["1024x1024 d=5 k=%d" % k] = rows
+    ctx.close()
+    return out
 
 
 def table6_leg(args, device: int) -> dict:
@@ -600,6 +772,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-table6", action="store_true", help="skip the distance-matrix precision leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default screening variant (no km_autotune)")
+    ap.add_argument("--no-quality", action="store_true", help="skip the clustering-quality leg (Tables 6.3-6.7)")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-full", action="store_true",

@@ -38,13 +38,18 @@ def init_indices(n: int, k: int, seed: int) -> np.ndarray:
     return np.sort(_rng(seed).choice(n, size=k, replace=False)).astype(np.int64)
 
 
-def blobs(n: int, d: int, k: int, seed: int, box: float = 10.0, std: float = 1.0):
+def blobs(n: int, d: int, k: int, seed: int, box: float = 10.0, std: float = 1.0, with_labels: bool = False):
+    """Isotropic Gaussian blobs: k centres uniform in [-box, box]^d, each
+    point picks a blob uniformly, noise N(0, std^2 I); init = k seeded
+    distinct points.  with_labels: also the blob of every point."""
     r = _rng(seed)
     centres = r.uniform(-box, box, size=(k, d))
     lab = r.integers(0, k, size=n)
     X = centres[lab] + r.normal(0.0, std, size=(n, d))
     X = X.astype(np.float32)
     C0 = X[init_indices(n, k, seed + 1)].copy()
+    if with_labels:
+        return X, C0, lab.astype(np.int32)
     return X, C0
 
 
