@@ -88,11 +88,15 @@ __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, 
 // of the groups' minima), each masked column written out as a (row, j) pair,
 // contiguous per row, one atomic reservation per block.  Rows whose list
 // overflowed, or that no longer fit in the pair buffer, get count -1
-// (whole-row recompute).
+// (whole-row recompute).  A row with a single candidate is decided here: the
+// window holds every centre that can be the nearest, so that one is; its
+// label is written and its count is 0 (no evaluation: every caller refines
+// the winner's distance afterwards, to binary64 accuracy).
 __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ rowinfo,
                                                      const uint32_t* __restrict__ cand, int64_t n, int ebits,
                                                      int2* __restrict__ pairs, int64_t cap,
-                                                     int2* __restrict__ rowpair, DevCounters* cnt) {
+                                                     int2* __restrict__ rowpair, int32_t* __restrict__ labels,
+                                                     DevCounters* cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t emask = (1u << ebits) - 1u;
     const float lscale = __uint_as_float((uint32_t)(127 + ebits - 23) << 23);  // 2^(ebits - 23)
@@ -144,6 +148,8 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
             }
             msk[g] = m;
         }
+        const bool single = valid && !full && c == 1;
+        if (single) c = 0;  // decided: nothing to evaluate
         // one reservation per block: lane prefix sums, then warp totals through
         // shared memory (every warp of the block takes part in each round)
         int incl = c;
@@ -166,7 +172,16 @@ __global__ void __launch_bounds__(256) k_cand_select(const int4* __restrict__ ro
         __syncthreads();
         const int64_t off0 = (int64_t)bbase + wpre + incl - c;
         const bool fits = off0 + c <= cap;
-        if (valid) {
+        if (single) {
+#pragma unroll
+            for (int g = 0; g < TC_GROUPS; g++) {
+                if (msk[g]) {
+                    const uint32_t e = c0[((size_t)g * TC_LIST + (__ffs(msk[g]) - 1)) * n];
+                    labels[row] = 4 * entry_quad(e, emask) + __ffs(entry_mask(e)) - 1;
+                }
+            }
+            rowpair[row] = make_int2(0, 0);
+        } else if (valid) {
             if (!full && !fits) {
                 // reserved but past the capacity: the part of the range below the
                 // capacity is marked empty (row -1), so the evaluation skips it
@@ -204,6 +219,7 @@ __global__ void __launch_bounds__(256) k_certify(const int2* __restrict__ rowpai
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
          row += (int64_t)gridDim.x * blockDim.x) {
         const int2 rp = rowpair[row];
+        if (rp.y == 0) continue;  // a single candidate: labelled by the selection
         if (rp.y < 0) {
             ovf_rows++;
             const int slot = atomicAdd(&cnt->ovf_count, 1);
@@ -339,7 +355,8 @@ cudaError_t launch_refine(const float* X, const float* C, const TcArgs& a, int32
     const int64_t rows_blocks = std::max<int64_t>(1, (a.n + 255) / 256);
     const int64_t rb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(sel_per_sm, 1));
     const int64_t cb = std::min<int64_t>(rows_blocks, (int64_t)num_sms * std::max(cert_per_sm, 1));
-    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.ebits, a.pairs, a.pair_cap, a.rowpair, a.cnt);
+    k_cand_select<<<(unsigned)rb, 256, 0, st>>>(a.rowinfo, a.cand, a.n, a.ebits, a.pairs, a.pair_cap, a.rowpair, labels,
+                                                a.cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *nlaunch = 4;
