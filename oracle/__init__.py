@@ -83,6 +83,8 @@ def _load():
         lib.orc_row_quant_stats.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, c.c_int, _f32p,
                                             _f64p, _f64p, _f64p, _f64p, _f64p]
         lib.orc_expanded_quantised.restype = c.c_double
+        lib.orc_kmeanspp.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _f64p, c.c_void_p, _i64p, c.c_void_p]
+        lib.orc_kmeanspp.restype = c.c_int
         lib.orc_expanded_quantised.argtypes = [_f32p, _f32p, c.c_int, c.c_double, c.c_double]
         _lib = lib
         return lib
@@ -189,6 +191,26 @@ def lloyd(X, C_init, max_iter: int, tau: float = 0.0, empty_policy: int = 1):
     if rc != 0:
         raise ValueError("oracle lloyd: invalid arguments")
     return Cout, lab, sse[: it.value + 1], it.value
+
+
+def kmeanspp(X, u, follow=None):
+    """D^2-sampling seeds with the draws u (k values in [0, 1)): (indices,
+    margins).  follow: continue each step from these indices instead of the
+    oracle's own (margins are then those of the followed sequence)."""
+    X = _f32(X)
+    n, d = X.shape
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    k = len(u)
+    idx = np.empty(k, dtype=np.int64)
+    mg = np.empty(k, dtype=np.float64)
+    fp = None
+    if follow is not None:
+        follow = np.ascontiguousarray(follow, dtype=np.int64)
+        fp = follow.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().orc_kmeanspp(X, n, d, k, u, fp, idx, mg.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError("oracle kmeanspp: invalid arguments")
+    return idx, mg
 
 
 # --- Alg. 2 ---------------------------------------------------------------

@@ -391,3 +391,64 @@ double orc_expanded_quantised(const float* xq, const float* cq, int d, double p,
     for (int l = 0; l < d; l++) g += (double)xq[l] * (double)cq[l];
     return p + q - 2.0 * g;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Seeding by D^2 sampling (k-means++; Section 2 names it as an alternative
+ * to uniform initial centres, and leaves it outside the method).  The
+ * random draws are inputs: u[0..k-1] in [0, 1).
+ *   i_0 = min(floor(u_0 n), n - 1);
+ *   D^2_i = d(x_i, x_{i_0})^2 (Eq. (dist-direct), binary64);
+ *   for t = 1..k-1: T = sum_i D^2_i (ascending i); when T > 0, i_t is the
+ *   smallest i whose prefix sum P_i = sum_{l <= i} D^2_l exceeds u_t T (the
+ *   largest i with D^2_i > 0 when rounding leaves none); when T = 0 (every
+ *   point on a chosen centre), i_t = min(floor(u_t n), n - 1); then
+ *   D^2_i = min(D^2_i, d(x_i, x_{i_t})^2).
+ * follow (nullable): after computing its own choice idx[t], continue from
+ * follow[t] instead (a check of another implementation's sequence, step by
+ * step).  margin (nullable): per step, min over i of |P_i - u_t T| / T, the
+ * distance of the draw from the nearest boundary between two choices
+ * (+inf at t = 0 and when T = 0).                                          */
+/* ------------------------------------------------------------------------ */
+int orc_kmeanspp(const float* X, int64_t n, int d, int k, const double* u, const int64_t* follow,
+                 int64_t* idx, double* margin) {
+    if (n < 1 || d < 1 || k < 1 || k > n) return ORC_EINVAL;
+    double* D2 = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!D2) return ORC_EINVAL;
+    int64_t cur = (int64_t)floor(u[0] * (double)n);
+    if (cur > n - 1) cur = n - 1;
+    idx[0] = cur;
+    if (margin) margin[0] = INFINITY;
+    if (follow) cur = follow[0];
+    for (int64_t i = 0; i < n; i++) D2[i] = orc_dist_direct_pair(X + i * d, X + cur * d, d);
+    for (int t = 1; t < k; t++) {
+        double T = 0.0;
+        for (int64_t i = 0; i < n; i++) T += D2[i];
+        int64_t pick = -1;
+        double mg = INFINITY;
+        if (T > 0.0) {
+            const double target = u[t] * T;
+            double P = 0.0;
+            int64_t last_pos = -1;
+            for (int64_t i = 0; i < n; i++) {
+                P += D2[i];
+                if (D2[i] > 0.0) last_pos = i;
+                const double gap = fabs(P - target) / T;
+                if (gap < mg) mg = gap;
+                if (pick < 0 && P > target) pick = i;
+            }
+            if (pick < 0) pick = last_pos;
+        } else {
+            pick = (int64_t)floor(u[t] * (double)n);
+            if (pick > n - 1) pick = n - 1;
+        }
+        idx[t] = pick;
+        if (margin) margin[t] = mg;
+        cur = follow ? follow[t] : pick;
+        for (int64_t i = 0; i < n; i++) {
+            const double v = orc_dist_direct_pair(X + i * d, X + cur * d, d);
+            if (v < D2[i]) D2[i] = v;
+        }
+    }
+    free(D2);
+    return ORC_OK;
+}

@@ -38,6 +38,12 @@ def init_indices(n: int, k: int, seed: int) -> np.ndarray:
     return np.sort(_rng(seed).choice(n, size=k, replace=False)).astype(np.int64)
 
 
+def seed_uniforms(k: int, seed: int) -> np.ndarray:
+    """k seeded draws in [0, 1) for D^2-sampling seeding (the method's random
+    numbers are inputs, the same for the library and the oracle)."""
+    return _rng(seed).random(k)
+
+
 def blobs(n: int, d: int, k: int, seed: int, box: float = 10.0, std: float = 1.0, with_labels: bool = False):
     """Isotropic Gaussian blobs: k centres uniform in [-box, box]^d, each
     point picks a blob uniformly, noise N(0, std^2 I); init = k seeded

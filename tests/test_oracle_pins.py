@@ -495,3 +495,49 @@ def test_predict_flags_consistent():
     assert (sure == (D == 0)).all()
     sure, maybe = oracle.predict_tc_flags(X, C, 1, 5.0, test="paper", c_A=1.0)
     assert sure.all()  # Alg. 2 with bf16 at r = 128: 100% fallback (Table 6.1)
+
+
+# ---- D^2-sampling seeding (k-means++) --------------------------------------
+def test_kmeanspp_hand_worked_1d():
+    """X = {0, 1, 3} on a line: u_0 = 0.1 picks row 0; D^2 = (0, 1, 9), T = 10,
+    so u_1 = 0.05 (target 0.5) picks row 1 and u_1 = 0.2 (target 2) row 2."""
+    X = np.array([[0.0], [1.0], [3.0]], dtype=np.float32)
+    idx, mg = oracle.kmeanspp(X, [0.1, 0.05])
+    assert idx.tolist() == [0, 1]
+    assert mg[1] == pytest.approx(0.05, rel=1e-15)  # |P_0 - 0.5| / 10 with P_0 = 0
+    idx, _ = oracle.kmeanspp(X, [0.1, 0.2])
+    assert idx.tolist() == [0, 2]
+    # after rows 0 and 2: D^2 = (0, 1, 0), so any third draw picks row 1
+    idx, _ = oracle.kmeanspp(X, [0.1, 0.2, 0.999])
+    assert idx.tolist() == [0, 2, 1]
+
+
+def test_kmeanspp_first_pick_and_coincident_points():
+    X = np.zeros((8, 3), dtype=np.float32)
+    idx, mg = oracle.kmeanspp(X, [0.0, 0.5, 0.999999])
+    # every point on the first centre: T = 0, the uniform rule
+    assert idx.tolist() == [0, 4, 7]
+    assert np.isinf(mg).all()
+
+
+def test_kmeanspp_draws_follow_the_d2_distribution():
+    """Second pick over a fine grid of draws: the share of draws that pick row
+    i equals D^2_i / T (the D^2 distribution), exactly up to the grid."""
+    r = np.random.default_rng(4)
+    X = r.normal(size=(7, 2)).astype(np.float32)
+    D2 = oracle.dist_direct(X, X[[2]])[:, 0]   # the first pick below is row 2 (u_0 = 0.3)
+    grid = (np.arange(20000) + 0.5) / 20000
+    picks = np.array([oracle.kmeanspp(X, [0.3, g])[0][1] for g in grid])
+    share = np.bincount(picks, minlength=7) / len(grid)
+    np.testing.assert_allclose(share, D2 / D2.sum(), atol=1.5 / len(grid))
+    assert share[2] == 0.0
+
+
+def test_kmeanspp_picks_distinct_points_and_follows():
+    r = np.random.default_rng(5)
+    X = r.normal(size=(300, 4)).astype(np.float32)
+    u = r.random(40)
+    idx, mg = oracle.kmeanspp(X, u)
+    assert len(set(idx.tolist())) == 40       # a chosen point has D^2 = 0
+    idx2, mg2 = oracle.kmeanspp(X, u, follow=idx)
+    assert np.array_equal(idx2, idx) and np.array_equal(mg2, mg)
