@@ -287,6 +287,24 @@ km_status km_update_finalize(km_ctx* ctx, const int64_t* sums, const int64_t* co
 km_status km_farthest_rows(km_ctx* ctx, const double* min_dist, int64_t n, int e, int64_t* rows, double* vals,
                            void* ws, size_t ws_bytes, void* stream);
 
+/* Initial centres by D^2 sampling (k-means++; Section 2 names it beside
+ * uniformly drawn initial centres and leaves it outside the method).  The
+ * random draws are inputs: u_host, k doubles in [0, 1) (host).
+ *   i_0 = min(floor(u_0 n), n - 1); D^2_i = d(x_i, x_{i_0})^2;
+ *   for t = 1..k-1: T = sum_i D^2_i; i_t = the first row whose prefix sum of
+ *   D^2 exceeds u_t T (the last row with D^2 > 0 when rounding leaves none;
+ *   min(floor(u_t n), n - 1) when T = 0); D^2_i = min(D^2_i, d(x_i, x_{i_t})^2).
+ * Distances by the direct formula to binary64 accuracy (relative error below
+ * 2^-40), sums in binary64 in a fixed order, so the picks do not depend on
+ * the launch; they equal the binary64 sequence except where a draw lies
+ * within rounding of a boundary between two rows.  C_out (k x d fp32,
+ * device) receives the picked rows, idx_host (nullable, host, k int64) their
+ * indices.  1 <= k <= n, d <= 512.  ws: device memory of at least
+ * 8 n + 16 k + 16 min(n, 16384) + 1280 bytes, 256-byte aligned.
+ * Synchronises `stream`. */
+km_status km_seed_pp(km_ctx* ctx, const float* X, int64_t n, int d, int k, const double* u_host, float* C_out,
+                     int64_t* idx_host, void* ws, size_t ws_bytes, void* stream);
+
 /* Failure-path check (no paper counterpart): launches one warp that waits on
  * an mbarrier no thread arrives at.  The wait is the same bounded wait every
  * kernel of the library uses: after its budget (about a second) it sets the

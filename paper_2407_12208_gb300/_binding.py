@@ -33,7 +33,7 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
            "km_lloyd_step_host", "km_selftest_timeout", "km_quantize", "km_choose_low", "km_absmax",
            "km_update_partial", "km_update_finalize", "km_farthest_rows", "km_autotune",
-           "km_set_screen_variant"]
+           "km_set_screen_variant", "km_seed_pp"]
 SCREEN_VARIANTS = {"auto": -1, "full": 0, "half": 1, "c32": 2, "reg": 3}  # KM_SV_* of the C-ABI
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
         lib.km_choose_low.argtypes = [vp, vp, i64, vp, i32, i32, c.c_double, c.POINTER(c.c_int32), vp, vp, sz, vp]
         lib.km_autotune.argtypes = [vp, vp, i64, vp, i32, i32, P, vp, c.POINTER(c.c_int32), vp, vp, sz, vp]
         lib.km_set_screen_variant.argtypes = [vp, i64, i32, i32, i32, i32]
+        lib.km_seed_pp.argtypes = [vp, vp, i64, i32, i32, c.POINTER(c.c_double), vp, c.POINTER(c.c_int64), vp, sz,
+                                   vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -242,6 +244,24 @@ class Context:
         the screening variant of the shape class."""
         self._check(self.lib.km_set_screen_variant(self.h, n, d, k, LOW_NAMES[low] if isinstance(low, str) else int(low),
                                                    SCREEN_VARIANTS[variant]))
+
+    def seed_pp(self, X, u, C_out=None, ws=None, stream=None):
+        """km_seed_pp: k = len(u) initial centres by D^2 sampling with the
+        draws u (in [0, 1)).  Returns (centres k x d on X's device, indices)."""
+        import numpy as np
+        import torch
+        n, d = X.shape
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        k = len(u)
+        if C_out is None:
+            C_out = torch.empty((k, d), dtype=torch.float32, device=X.device)
+        if ws is None:
+            ws = torch.empty(8 * n + 16 * k + 16 * min(n, 16384) + 1280, dtype=torch.uint8, device=X.device)
+        idx = np.empty(k, dtype=np.int64)
+        self._check(self.lib.km_seed_pp(self.h, _ptr(X), n, d, k, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        _ptr(C_out), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(ws),
+                                        ws.numel(), _stream(stream)))
+        return C_out, idx
 
     def quantize(self, X, low="bf16", stream=None):
         """km_quantize: (Xq as raw bytes n x (ldq * element size) uint8,

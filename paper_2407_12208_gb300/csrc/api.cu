@@ -19,6 +19,7 @@
 #include "../../include/mpkm.h"
 #include "common.cuh"
 #include "internal.h"
+#include "seed.h"
 #include "serve.h"
 
 using namespace km;
@@ -1446,7 +1447,35 @@ __global__ void k_wait_unsignalled(DevCounters* cnt) {
 }
 }  // namespace
 
-extern "C" km_status km_selftest_timeout(km_ctx* ctx, void* ws, size_t ws_bytes, void* stream) {
+extern "C" km_status km_seed_pp(km_ctx* ctx, const float* X, int64_t n, int d, int k, const double* u_host, float* C_out,
+                     int64_t* idx_host, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!X || !u_host || !C_out || !ws) return fail(ctx, KM_EINVAL, "null argument");
+    if (n < 1 || d < 1 || k < 1 || k > n) return fail(ctx, KM_EINVAL, "need 1 <= k <= n and d >= 1");
+    if (n > (int64_t)INT32_MAX) return fail(ctx, KM_EINVAL, "n too large");
+    if (d > 512) return fail(ctx, KM_EUNSUPPORTED, "d=%d: seeding takes d <= 512", d);
+    for (int t = 0; t < k; t++)
+        if (!(u_host[t] >= 0.0 && u_host[t] < 1.0)) return fail(ctx, KM_EINVAL, "draw %d outside [0, 1)", t);
+    if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");
+    Carve cv{(char*)ws};
+    double* D2 = cv.take<double>((size_t)n);
+    double* u = cv.take<double>((size_t)k);
+    int64_t* idx = cv.take<int64_t>((size_t)k);
+    double* csum = cv.take<double>(seed_chunk_count(n));
+    int64_t* clast = cv.take<int64_t>(seed_chunk_count(n));
+    if (ws_bytes < cv.off) return fail(ctx, KM_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, cv.off);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(u, u_host, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, st));
+    int nl = 0;
+    CK(launch_seed_pp(X, n, d, k, u, D2, idx, csum, clast, C_out, ctx->num_sms, st, &nl));
+    ctx->launches += (uint64_t)nl;
+    if (idx_host) CK(cudaMemcpyAsync(idx_host, idx, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return KM_OK;
+}
+
+km_status km_selftest_timeout(km_ctx* ctx, void* ws, size_t ws_bytes, void* stream) {
     if (!ctx) return KM_EINVAL;
     if (!ws) return fail(ctx, KM_EINVAL, "null workspace");
     if (!aligned256(ws)) return fail(ctx, KM_EINVAL, "workspace must be 256-byte aligned");

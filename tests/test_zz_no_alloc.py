@@ -4,6 +4,8 @@ give the same labels and min_dist as km_assign on the FP32 direct path, bit
 for bit, on consecutive calls (the second call sees the scratch the first one
 left), and reject sizes above its static limit before any launch.  The file
 sorts last so that it also runs after every other GPU test in one process."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -117,11 +119,19 @@ def test_static_allocates_no_device_memory(ctx):
     lab, md = _outputs(X.shape[0])
     ctx.assign_static(X, C, lab, md)
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    used0 = torch.cuda.memory_allocated()
-    for _ in range(3):
-        ctx.assign_static(X, C, lab, md)
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
+    # tensors of earlier tests still waiting for the cycle collector must not
+    # be freed inside the measured window
+    gc.collect()
+    gc.disable()
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        used0 = torch.cuda.memory_allocated()
+        for _ in range(3):
+            ctx.assign_static(X, C, lab, md)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        used1 = torch.cuda.memory_allocated()
+    finally:
+        gc.enable()
     assert free1 == free0
-    assert torch.cuda.memory_allocated() == used0
+    assert used1 == used0
