@@ -14,7 +14,7 @@ the oracle on the host cores (`cpu_baseline`), the plain FP64 path on a row
 sample (`fp64_path`), the served stream's latencies (`serving`), the
 distance-matrix precision modes in the structure of the paper's Tables 6.1 /
 6.2 (`table6`), clustering quality in the structure of Tables 6.3-6.7
-(`quality`), SM clocks
+(`quality`), the free-running config-3 SSE trajectories (`c3_trajectory`), SM clocks
 sampled during the timed region (`clocks`) and the library's own launch count
 (`gpu_launches`).  `--impl reference` times the CPU oracle instead (on a
 bounded sample of the same workload).  Multi-GPU (torchrun): independent
@@ -368,6 +368,12 @@ def run_ours(args):
     table6 = None
     if rank == 0 and not args.only_step and not args.no_table6:
         table6 = table6_leg(args, local)
+    c3 = None
+    if rank == 0 and not args.only_step and not args.no_c3:
+        try:
+            c3 = c3_trajectory_leg(args, local)
+        except Exception as exc:
+            c3 = {"error": "%s: %s" % (type(exc).__name__, exc)}
     quality = None
     if rank == 0 and not args.only_step and not args.no_quality:
         try:
@@ -385,7 +391,7 @@ def run_ours(args):
                        "step": "km_lloyd_step: quantise X (+ max |x|), screen, refine, certified argmin, min_dist, exact centre update",
                        "l2": "inputs larger than L2 (X %d MB fp32, L2 126 MB)" % (n * d * 4 // 1000000)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "fp64_path": fp64, "serving": serving, "table6": table6, "quality": quality, "autotune": tuned,
+            "fp64_path": fp64, "serving": serving, "table6": table6, "quality": quality, "c3_trajectory": c3, "autotune": tuned,
             "phases_ms_per_step": {k_: v[0] / max(args.steps, 1) for k_, v in phases.items()},
             "eta": stats["flagged"] / max(stats["pairs"], 1),
             "assign_stats": {kk: stats[kk] for kk in ("fp32_evals", "fp64_evals", "ambiguous_rows", "overflow_rows")},
@@ -568,6 +574,39 @@ def quality_leg(args, device: int) -> dict:
             rows[name] = {"time_s": t, "iters": it, "sse": sse, "diff_vs_fp64": matched_label_diff(ref, lab),
                           "eta": eta}
         out["image"]["1024x1024 d=5 k=%d" % k] = rows
+    ctx.close()
+    return out
+
+
+def c3_trajectory_leg(args, device: int) -> dict:
+    """Config 3 free-running: Gaussian mixture n = 4e6, d = 64, k = 256 from
+    the same seeded initial centres, 50 Lloyd iterations (km_lloyd_run) with
+    the plain FP64 direct path, FP32 direct, and the mixed BF16 / FP16 / E4M3
+    paths: the SSE of every iteration, the time of the run (CUDA events) and
+    whether the final labels equal the FP64 run's."""
+    import numpy as np
+    import torch
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300 import workloads
+    ctx = pkg.Context(device)
+    X, C0 = workloads.gaussian_mixture(4_000_000, 64, 256, seed=15)
+    Xd, C0d = torch.from_numpy(X).cuda(device), torch.from_numpy(C0).cuda(device)
+    out, ref_lab, ref_sse = {}, None, None
+    for low in ("fp64", "fp32", "bf16", "fp16", "e4m3"):
+        p = pkg.params(low, "tc", rho=5.0, max_iter=50, tau=0.0)
+        ws = ctx.workspace(X.shape[0], X.shape[1], C0.shape[0], p)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C, lab, sse, eta, it = ctx.lloyd_run(Xd, C0d, p, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        lab = lab.cpu().numpy()
+        if ref_lab is None:
+            ref_lab, ref_sse = lab, sse
+        out[low] = {"time_s": e0.elapsed_time(e1) / 1e3, "iters": it, "sse": [float(v) for v in sse],
+                    "labels_equal_fp64": bool(np.array_equal(lab, ref_lab)),
+                    "max_rel_sse_diff_vs_fp64": float(np.max(np.abs(sse - ref_sse) / ref_sse)),
+                    "eta_mean": float(np.mean(eta))}
     ctx.close()
     return out
 
@@ -773,6 +812,7 @@ def main():
     ap.add_argument("--no-table6", action="store_true", help="skip the distance-matrix precision leg")
     ap.add_argument("--no-autotune", action="store_true", help="use the default screening variant (no km_autotune)")
     ap.add_argument("--no-quality", action="store_true", help="skip the clustering-quality leg (Tables 6.3-6.7)")
+    ap.add_argument("--no-c3", action="store_true", help="skip the free-running config-3 trajectories")
     ap.add_argument("--clocks-csv", default=None, help="keep the nvidia-smi clock samples of the timed region here")
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-full", action="store_true",
