@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_seed_dist(const float* __restrict__ X, 
                                                    const int64_t* __restrict__ idx, int t, bool first,
                                                    double* __restrict__ D2) {
     constexpr int G = 32 / LPR;
-    constexpr int R = NV4 == 1 ? 8 : (NV4 == 2 ? 4 : 2);
+    constexpr int R = NV4 == 4 ? 2 : 4;  // rows per lane and pass
     constexpr int STEP = R * G;
     static_assert(R <= LPR, "rows per lane exceed the lanes of a row");
     const int lane = threadIdx.x & 31, sub = lane / LPR, cl = lane % LPR;
@@ -286,7 +286,7 @@ cudaError_t launch_seed_pp(const float* X, int64_t n, int d, int k, const double
         int per_sm = 1;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
         if (e != cudaSuccess) return e;
-        const int rows_per_warp_pass = (nv4 == 1 ? 8 : (nv4 == 2 ? 4 : 2)) * (32 / lpr);
+        const int rows_per_warp_pass = (nv4 == 4 ? 2 : 4) * (32 / lpr);
         const int64_t warps_needed = (n + rows_per_warp_pass - 1) / rows_per_warp_pass;
         blocks = (unsigned)std::max<int64_t>(
             1, std::min<int64_t>((warps_needed + 7) / 8, (int64_t)num_sms * std::max(per_sm, 1)));
