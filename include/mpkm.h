@@ -287,6 +287,29 @@ km_status km_update_finalize(km_ctx* ctx, const int64_t* sums, const int64_t* co
 km_status km_farthest_rows(km_ctx* ctx, const double* min_dist, int64_t n, int e, int64_t* rows, double* vals,
                            void* ws, size_t ws_bytes, void* stream);
 
+/* Alg. 3 for many small jobs at once (no counterpart in the paper): one
+ * launch runs every job's whole Lloyd loop, one thread block per job, instead
+ * of about ten launches per iteration each.  For low = KM_FP32_DIRECT and jobs
+ * with d <= 8, 1 <= k <= 64, k <= n <= 16384; all jobs share p (max_iter,
+ * tau, empty).  Every job's centres, labels, SSE per iteration and iteration
+ * count equal km_lloyd_run's on that job alone, bit for bit.  All pointers of
+ * a job are device pointers: sse_per_iter (max_iter + 1 doubles), iters (one
+ * int32), scratch (n doubles).  Asynchronous on `stream`; errors in the
+ * arguments return before any launch. */
+typedef struct {
+    const float* X;
+    int64_t n;
+    int d;
+    int k;
+    const float* C_init;
+    float* C_out;
+    int32_t* labels;
+    double* sse_per_iter;
+    int32_t* iters;
+    double* scratch;
+} km_batch_job;
+km_status km_lloyd_run_batch(km_ctx* ctx, const km_batch_job* jobs, int njobs, const km_params* p, void* stream);
+
 /* Initial centres by D^2 sampling (k-means++; Section 2 names it beside
  * uniformly drawn initial centres and leaves it outside the method).  The
  * random draws are inputs: u_host, k doubles in [0, 1) (host).

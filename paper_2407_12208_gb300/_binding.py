@@ -33,7 +33,7 @@ EXPORTS = ["km_default_params", "km_init", "km_destroy", "km_last_error", "km_wo
            "km_get_launch_count", "km_assign_static", "km_lloyd_step", "km_host_workspace_size",
            "km_lloyd_step_host", "km_selftest_timeout", "km_quantize", "km_choose_low", "km_absmax",
            "km_update_partial", "km_update_finalize", "km_farthest_rows", "km_autotune",
-           "km_set_screen_variant", "km_seed_pp"]
+           "km_set_screen_variant", "km_seed_pp", "km_lloyd_run_batch"]
 SCREEN_VARIANTS = {"auto": -1, "full": 0, "half": 1, "c32": 2, "reg": 3}  # KM_SV_* of the C-ABI
 STATIC_MAX_ROWS = 1048576  # KM_STATIC_MAX_ROWS of the C-ABI
 PHASES = ["quantise", "screen", "refine", "fullrow", "update", "direct"]
@@ -61,6 +61,12 @@ class Stats(ctypes.Structure):
 
 
 JOB_DEVICE_DATA = 1
+
+
+class BatchJob(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("C_init", ctypes.c_void_p), ("C_out", ctypes.c_void_p), ("labels", ctypes.c_void_p),
+                ("sse_per_iter", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("scratch", ctypes.c_void_p)]
 
 
 class Job(ctypes.Structure):
@@ -124,6 +130,7 @@ def load(path: str = LIB_PATH):
         lib.km_set_screen_variant.argtypes = [vp, i64, i32, i32, i32, i32]
         lib.km_seed_pp.argtypes = [vp, vp, i64, i32, i32, c.POINTER(c.c_double), vp, c.POINTER(c.c_int64), vp, sz,
                                    vp]
+        lib.km_lloyd_run_batch.argtypes = [vp, c.POINTER(BatchJob), i32, P, vp]
         lib.km_set_profiling.argtypes = [vp, i32]
         lib.km_get_phase_times.argtypes = [vp, vp, vp]
         lib.km_get_launch_count.argtypes = [vp, c.POINTER(c.c_uint64)]
@@ -244,6 +251,30 @@ class Context:
         the screening variant of the shape class."""
         self._check(self.lib.km_set_screen_variant(self.h, n, d, k, LOW_NAMES[low] if isinstance(low, str) else int(low),
                                                    SCREEN_VARIANTS[variant]))
+
+    def lloyd_run_batch(self, jobs, p: Params, stream=None):
+        """km_lloyd_run_batch: Alg. 3 for every (X, C_init) pair of device
+        tensors in one launch per 32 jobs of equal d.  Returns per job
+        (C_out, labels, sse[:iters + 1], iters)."""
+        import torch
+        arr = (BatchJob * len(jobs))()
+        keep = []
+        for q, (X, C0) in enumerate(jobs):
+            n, d = X.shape
+            k = C0.shape[0]
+            C = torch.empty_like(C0)
+            lab = torch.empty(n, dtype=torch.int32, device=X.device)
+            sse = torch.empty(p.max_iter + 1, dtype=torch.float64, device=X.device)
+            it = torch.zeros(1, dtype=torch.int32, device=X.device)
+            scr = torch.empty(n, dtype=torch.float64, device=X.device)
+            arr[q] = BatchJob(_ptr(X), n, d, k, _ptr(C0), _ptr(C), _ptr(lab), _ptr(sse), _ptr(it), _ptr(scr))
+            keep.append((C, lab, sse, it, scr))
+        self._check(self.lib.km_lloyd_run_batch(self.h, arr, len(jobs), ctypes.byref(p), _stream(stream)))
+        out = []
+        for C, lab, sse, it, _ in keep:
+            t = int(it.item())
+            out.append((C, lab, sse[: t + 1].cpu().numpy(), t))
+        return out
 
     def seed_pp(self, X, u, C_out=None, ws=None, stream=None):
         """km_seed_pp: k = len(u) initial centres by D^2 sampling with the

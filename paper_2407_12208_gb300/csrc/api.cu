@@ -18,6 +18,7 @@
 
 #include "../../include/mpkm.h"
 #include "common.cuh"
+#include "group.h"
 #include "internal.h"
 #include "seed.h"
 #include "serve.h"
@@ -1075,6 +1076,44 @@ static km_status lloyd_impl(km_ctx* ctx, const float* X, int64_t n, int d, int k
                             const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
                             double* eta_per_iter, int* iters_done, void* ws, size_t ws_bytes, void* stream,
                             const volatile int* cancel, bool allow_graphs);
+
+km_status km_lloyd_run_batch(km_ctx* ctx, const km_batch_job* jobs, int njobs, const km_params* p, void* stream) {
+    if (!ctx) return KM_EINVAL;
+    if (!jobs || !p || njobs < 0) return fail(ctx, KM_EINVAL, "null argument");
+    if (p->low != KM_FP32_DIRECT) return fail(ctx, KM_EUNSUPPORTED, "batched runs take low = KM_FP32_DIRECT");
+    if (p->max_iter < 0) return fail(ctx, KM_EINVAL, "max_iter must be >= 0");
+    km_status s;
+    for (int q = 0; q < njobs; q++) {
+        const km_batch_job& b = jobs[q];
+        if (!b.X || !b.C_init || !b.C_out || !b.labels || !b.sse_per_iter || !b.iters || !b.scratch)
+            return fail(ctx, KM_EINVAL, "job %d: null pointer", q);
+        if (b.d < 1 || b.d > GROUP_MAX_D || b.k < 1 || b.k > GROUP_MAX_K || b.n < b.k || b.n > GROUP_MAX_N)
+            return fail(ctx, KM_EUNSUPPORTED, "job %d: batched runs take d <= 8, 1 <= k <= 64, k <= n <= 16384", q);
+        if ((s = check_params(ctx, p, b.d, b.k)) != KM_OK) return s;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    for (int d = 1; d <= GROUP_MAX_D; d++) {
+        GroupArgs a{};
+        a.max_iter = p->max_iter;
+        a.empty_farthest = p->empty == KM_EMPTY_FARTHEST ? 1 : 0;
+        a.tau = p->tau;
+        a.gamma32 = make_tp(p, d).gamma32;
+        int m = 0;
+        for (int q = 0; q <= njobs; q++) {
+            if (q < njobs && jobs[q].d == d) {
+                const km_batch_job& b = jobs[q];
+                a.job[m++] = GroupJob{b.X, b.C_init, b.C_out, b.labels, b.scratch, b.sse_per_iter, b.iters,
+                                      (int)b.n, b.k};
+            }
+            if (m == GROUP_MAX || (q == njobs && m > 0)) {
+                KL(1, launch_group_lloyd(a, m, d, st));
+                m = 0;
+            }
+        }
+    }
+    return KM_OK;
+}
 
 km_status km_lloyd_run(km_ctx* ctx, const float* X, int64_t n, int d, int k, const float* C_init,
                        const km_params* p, float* C_out, int32_t* labels, double* sse_per_iter,
