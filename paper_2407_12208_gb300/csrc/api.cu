@@ -1409,6 +1409,30 @@ size_t km_internal_ws_bytes(int64_t n, int d, int k, const km_params* p) {
     return std::max(a.off, b.off) + 256;
 }
 
+bool km_internal_groupable(const km_job& job) {
+    return job.kind == 0 && job.p.low == KM_FP32_DIRECT && job.d >= 1 && job.d <= GROUP_MAX_D && job.k >= 1 &&
+           job.k <= GROUP_MAX_K && job.n >= job.k && job.n <= GROUP_MAX_N && job.p.max_iter >= 0;
+}
+
+km_status km_internal_run_batch(km_ctx_view* v, const km_batch_job* jobs, int njobs, const km_params* p,
+                                cudaStream_t st, std::string* err) {
+    km_ctx ctx;
+    ctx.device = v->device;
+    ctx.num_sms = v->num_sms;
+    if (v->tune) ctx.tune = v->tune;
+    km_status s = km_lloyd_run_batch(&ctx, jobs, njobs, p, st);
+    if (s == KM_OK) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            if (err) *err = cudaGetErrorString(e);
+            return KM_ECUDA;
+        }
+    } else if (err) {
+        *err = ctx.err;
+    }
+    return s;
+}
+
 // Used by the serving engine: one whole Lloyd / assign job on its own stream.
 km_status km_internal_run_job(km_ctx_view* v, const float* X, int64_t n, int d, int k, const float* C_init,
                               const km_params* p, int kind, float* C_out, int32_t* labels, void* ws, size_t ws_bytes,

@@ -26,6 +26,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "group.h"
 #include "serve.h"
 
 size_t km_internal_ws_bytes(int64_t n, int d, int k, const km_params* p);
@@ -75,7 +76,8 @@ struct km_serve {
     std::unordered_map<uint64_t, Job*> jobs;
     std::vector<std::thread> workers;
     int n_workers = 16;
-    int busy = 0;
+    int busy = 0;         // workers running a job or a group of jobs
+    int ready_group = 0;  // ready jobs that can run grouped
     bool stop = false;
     uint64_t next_id = 1;
 
@@ -107,10 +109,19 @@ struct km_serve {
             }
         }
     }
-    // Caller holds mu.  Admits queued jobs in arrival order while workers are free.
+    // Caller holds mu.  Admits queued jobs in arrival order while workers are
+    // free; small jobs that run grouped (up to GROUP_MAX per launch) take a
+    // worker per group, so more of them may wait ready.
+    bool has_room(bool group_next) const {
+        const int rg = ready_group + (group_next ? 1 : 0);
+        const int rn = (int)ready.size() - ready_group + (group_next ? 0 : 1);
+        return busy + rn + (rg + km::GROUP_MAX - 1) / km::GROUP_MAX <= n_workers;
+    }
     void try_admit() {
-        for (auto it = pending.begin(); it != pending.end() && busy + (int)ready.size() < n_workers;) {
+        for (auto it = pending.begin(); it != pending.end();) {
             Job* j = *it;
+            const bool g = km_internal_groupable(j->spec);
+            if (!has_room(g)) break;
             size_t off = 0;
             if (alloc(j->bytes, &off)) {
                 j->off = off;
@@ -118,6 +129,7 @@ struct km_serve {
                 j->t_admit = Clock::now();
                 it = pending.erase(it);
                 ready.push_back(j);
+                ready_group += g ? 1 : 0;
                 cv.notify_all();
             } else {
                 ++it;
@@ -133,31 +145,54 @@ void km_serve::worker_loop() {
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     km_ctx_view view{device, num_sms, tune};
     for (;;) {
-        Job* j = nullptr;
+        // one job, or a group of small jobs with the same loop parameters
+        std::vector<Job*> group;
         {
             std::unique_lock<std::mutex> lk(mu);
             cv.wait(lk, [&] { return stop || !ready.empty(); });
             if (stop && ready.empty()) break;
-            j = ready.front();
+            Job* j = ready.front();
             ready.pop_front();
+            group.push_back(j);
+            if (km_internal_groupable(j->spec)) {
+                ready_group--;
+                const km_params& p0 = j->spec.p;
+                for (auto it = ready.begin(); it != ready.end() && (int)group.size() < km::GROUP_MAX;) {
+                    const km_job& o = (*it)->spec;
+                    if (km_internal_groupable(o) && o.p.max_iter == p0.max_iter && o.p.empty == p0.empty &&
+                        o.p.tau == p0.tau) {
+                        group.push_back(*it);
+                        it = ready.erase(it);
+                        ready_group--;
+                    } else {
+                        ++it;
+                    }
+                }
+            }
             busy++;
-            j->state = JobState::Running;
+            for (Job* g : group) g->state = JobState::Running;
         }
-        const km_job& s = j->spec;
-        char* base = arena + j->off;
-        size_t o = 0;
-        auto take = [&](size_t b) { char* p = base + o; o = up256(o + b); return p; };
-        const bool resident = (s.flags & KM_JOB_DEVICE_DATA) != 0;
-        j->dX = resident ? const_cast<float*>(s.X) : (float*)take(sizeof(float) * (size_t)s.n * s.d);
-        j->dC0 = (float*)take(sizeof(float) * (size_t)s.k * s.d);
-        j->dC = (float*)take(sizeof(float) * (size_t)s.k * s.d);
-        j->dlab = (int32_t*)take(sizeof(int32_t) * (size_t)s.n);
-        j->ws_bytes = j->bytes - o;
-        j->dws = take(0);
-        km_status rc = KM_OK;
-        std::string err;
-        cudaError_t ce = cudaSuccess;
-        if (!j->cancel) {
+        // each job's place in the arena and its inputs
+        std::vector<km_status> rc(group.size(), KM_OK);
+        std::vector<std::string> err(group.size());
+        for (size_t q = 0; q < group.size(); q++) {
+            Job* j = group[q];
+            const km_job& s = j->spec;
+            char* base = arena + j->off;
+            size_t o = 0;
+            auto take = [&](size_t b) { char* p = base + o; o = up256(o + b); return p; };
+            const bool resident = (s.flags & KM_JOB_DEVICE_DATA) != 0;
+            j->dX = resident ? const_cast<float*>(s.X) : (float*)take(sizeof(float) * (size_t)s.n * s.d);
+            j->dC0 = (float*)take(sizeof(float) * (size_t)s.k * s.d);
+            j->dC = (float*)take(sizeof(float) * (size_t)s.k * s.d);
+            j->dlab = (int32_t*)take(sizeof(int32_t) * (size_t)s.n);
+            j->ws_bytes = j->bytes - o;
+            j->dws = take(0);
+            cudaError_t ce = cudaSuccess;
+            if (j->cancel) {
+                rc[q] = KM_ECANCELLED;
+                continue;
+            }
             if (resident) {
                 ce = cudaMemcpyAsync(j->dC0, s.C_init, sizeof(float) * (size_t)s.k * s.d, cudaMemcpyDeviceToDevice, st);
             } else {
@@ -165,29 +200,88 @@ void km_serve::worker_loop() {
                 if (ce == cudaSuccess)
                     ce = cudaMemcpyAsync(j->dC0, j->C.data(), sizeof(float) * j->C.size(), cudaMemcpyHostToDevice, st);
             }
+            if (ce != cudaSuccess) {
+                rc[q] = KM_ECUDA;
+                err[q] = "copy into the arena failed";
+            }
         }
-        if (j->cancel) {
-            rc = KM_ECANCELLED;
-        } else if (ce != cudaSuccess) {
-            rc = KM_ECUDA;
-            err = "copy into the arena failed";
+        if (group.size() == 1 && !km_internal_groupable(group[0]->spec)) {
+            Job* j = group[0];
+            const km_job& s = j->spec;
+            if (rc[0] == KM_OK)
+                rc[0] = km_internal_run_job(&view, j->dX, s.n, s.d, s.k, j->dC0, &s.p, s.kind, j->dC, j->dlab, j->dws,
+                                            j->ws_bytes, st, &j->sse, &j->eta, &j->iters, &err[0], &j->cancel);
         } else {
-            rc = km_internal_run_job(&view, j->dX, s.n, s.d, s.k, j->dC0, &s.p, s.kind, j->dC, j->dlab, j->dws,
-                                     j->ws_bytes, st, &j->sse, &j->eta, &j->iters, &err, &j->cancel);
+            // grouped: one launch for the jobs still to run; their scratch, SSE
+            // trajectory and iteration count sit in each job's workspace
+            std::vector<km_batch_job> bj;
+            std::vector<size_t> which;
+            std::vector<double> sse_last(group.size(), 0.0);
+            for (size_t q = 0; q < group.size(); q++) {
+                if (rc[q] != KM_OK) continue;
+                Job* j = group[q];
+                const km_job& s = j->spec;
+                char* w = (char*)j->dws;
+                const size_t need = up256(sizeof(double) * (size_t)s.n) + up256(sizeof(double) * (size_t)(s.p.max_iter + 1)) + 256;
+                if (need > j->ws_bytes) {
+                    rc[q] = KM_ENOMEM;
+                    err[q] = "workspace too small for the grouped run";
+                    continue;
+                }
+                km_batch_job b{};
+                b.X = j->dX; b.n = s.n; b.d = s.d; b.k = s.k; b.C_init = j->dC0; b.C_out = j->dC; b.labels = j->dlab;
+                b.scratch = (double*)w;
+                b.sse_per_iter = (double*)(w + up256(sizeof(double) * (size_t)s.n));
+                b.iters = (int32_t*)(w + up256(sizeof(double) * (size_t)s.n) + up256(sizeof(double) * (size_t)(s.p.max_iter + 1)));
+                bj.push_back(b);
+                which.push_back(q);
+            }
+            if (!bj.empty()) {
+                std::string e;
+                const km_status r = km_internal_run_batch(&view, bj.data(), (int)bj.size(), &group[which[0]]->spec.p, st, &e);
+                // each job's trajectory and iteration count back on the worker's stream
+                const int T = group[which[0]]->spec.p.max_iter + 1;
+                std::vector<double> sse((size_t)T * which.size());
+                std::vector<int32_t> its(which.size());
+                cudaError_t ce = cudaSuccess;
+                for (size_t m = 0; m < which.size() && r == KM_OK && ce == cudaSuccess; m++) {
+                    ce = cudaMemcpyAsync(sse.data() + (size_t)T * m, bj[m].sse_per_iter, sizeof(double) * T,
+                                         cudaMemcpyDeviceToHost, st);
+                    if (ce == cudaSuccess)
+                        ce = cudaMemcpyAsync(&its[m], bj[m].iters, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+                }
+                if (r == KM_OK && ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+                for (size_t m = 0; m < which.size(); m++) {
+                    Job* j = group[which[m]];
+                    if (r != KM_OK || ce != cudaSuccess) {
+                        rc[which[m]] = r != KM_OK ? r : KM_ECUDA;
+                        err[which[m]] = r != KM_OK ? e : std::string(cudaGetErrorString(ce));
+                        continue;
+                    }
+                    j->iters = its[m];
+                    j->sse = sse[(size_t)T * m + (size_t)its[m]];
+                    j->eta = 0.0;  // the FP32 direct path flags no pair
+                }
+            }
         }
         {
             std::lock_guard<std::mutex> lk(mu);
-            j->status = rc;
-            j->err = err;
-            j->t_done = Clock::now();
-            j->state = rc == KM_OK ? JobState::Done : (rc == KM_ECANCELLED ? JobState::Cancelled : JobState::Failed);
-            std::vector<float>().swap(j->X);
-            std::vector<float>().swap(j->C);
-            busy--;
-            if (j->state != JobState::Done && j->has_mem) {  // failed jobs hold no results
-                release_mem(j->off, j->bytes);
-                j->has_mem = false;
+            const Clock::time_point now = Clock::now();
+            for (size_t q = 0; q < group.size(); q++) {
+                Job* j = group[q];
+                j->status = rc[q];
+                j->err = err[q];
+                j->t_done = now;
+                j->state = rc[q] == KM_OK ? JobState::Done
+                                          : (rc[q] == KM_ECANCELLED ? JobState::Cancelled : JobState::Failed);
+                std::vector<float>().swap(j->X);
+                std::vector<float>().swap(j->C);
+                if (j->state != JobState::Done && j->has_mem) {  // failed jobs hold no results
+                    release_mem(j->off, j->bytes);
+                    j->has_mem = false;
+                }
             }
+            busy--;
             try_admit();
         }
     }

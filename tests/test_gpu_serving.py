@@ -126,3 +126,37 @@ def test_serving_resident_data_equals_alone(sctx):
         assert np.array_equal(C_s.view(np.uint32), C_a.cpu().numpy().view(np.uint32))
         assert np.array_equal(lab_s, lab_a.cpu().numpy())
         sctx.release(jid)
+
+
+def test_serving_groups_small_jobs(sctx):
+    """120 small FP32 Lloyd jobs (d <= 8, k <= 64, n <= 16384: grouped launches
+    of up to 32 jobs) submitted among larger ones: each small job's centres,
+    labels, SSE and iteration count equal km_lloyd_run on it alone."""
+    import paper_2407_12208_gb300 as pkg
+    r = np.random.default_rng(9)
+    big = workloads.gaussian_mixture(60000, 64, 128, seed=9)
+    small, others = [], []
+    for q in range(120):
+        d, k = int(r.integers(1, 9)), int(r.integers(1, 65))
+        n = int(r.integers(k, 16385))
+        X, C = workloads.blobs(n, d, k, seed=500 + q)
+        p = pkg.params("fp32", max_iter=10, empty="farthest")
+        small.append((sctx.submit(X, C, p, kind=0), X, C, p))
+        if q % 40 == 0:
+            others.append(sctx.submit(big[0], big[1], pkg.params("bf16", max_iter=4), kind=0))
+    for jid in others:
+        assert _wait(sctx, jid)["status"] == pkg._binding.KM_OK
+    for q, (jid, X, C, p) in enumerate(small):
+        out = _wait(sctx, jid)
+        assert out["status"] == pkg._binding.KM_OK, q
+        n, d = X.shape
+        k = C.shape[0]
+        C_a, lab_a, sse_a, _, it_a = sctx.lloyd_run(torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), p)
+        torch.cuda.synchronize()
+        C_s = pkg.device_array(out["C"], (k, d), "<f4").cpu().numpy()
+        lab_s = pkg.device_array(out["labels"], (n,), "<i4").cpu().numpy()
+        assert np.array_equal(C_s.view(np.uint32), C_a.cpu().numpy().view(np.uint32)), q
+        assert np.array_equal(lab_s, lab_a.cpu().numpy()), q
+        assert out["iters"] == it_a and out["sse"] == sse_a[-1], q
+    for jid in others + [s_[0] for s_ in small]:
+        sctx.release(jid)
