@@ -343,9 +343,9 @@ km_status km_selftest_timeout(km_ctx* ctx, void* ws, size_t ws_bytes, void* stre
  * counts_host (nullable, k int64) and shift_host (nullable) written, all in
  * host memory; the call returns when they are there (it synchronises
  * `stream`).  The rows travel in up to four chunks of whole 128-row blocks on
- * two copy streams owned by the context: each chunk is assigned as soon as
- * it has arrived and its labels go back while the next chunk is assigned;
- * the centre update follows the last chunk.  With pinned (page-locked) host
+ * two copy streams owned by the context: each chunk is assigned (labels and
+ * min_dist) as soon as it has arrived and its results go back while the next
+ * chunk is assigned; the centre update follows the last chunk.  With pinned (page-locked) host
  * buffers the copies overlap the kernels; pageable ones still give the same
  * results.  The results equal km_lloyd_step on device copies of the same
  * inputs bit for bit.  ws: device memory of km_host_workspace_size bytes

@@ -1035,23 +1035,27 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
             CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
             s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
             if (s != KM_OK) return s;
-            // this chunk's labels go back while the next chunk is assigned
+            // the chunk's winner distances (binary64 accuracy) while the next
+            // chunk is still on its way: the update's pass then only sums
+            if ((s = refine_winners(ctx, h.X + r0 * d, rows, d, h.C, p, h.labels + r0, h.min_dist + r0, st)) != KM_OK)
+                return s;
+            // this chunk's labels and distances go back while the next chunk is assigned
             CK(cudaEventRecord(ev_out[c], st));
             CK(cudaStreamWaitEvent(cs, ev_out[c], 0));
             CK(cudaMemcpyAsync(labels_host + r0, h.labels + r0, sizeof(int32_t) * (size_t)rows, cudaMemcpyDeviceToHost, cs));
+            if (min_dist_host)
+                CK(cudaMemcpyAsync(min_dist_host + r0, h.min_dist + r0, sizeof(double) * (size_t)rows,
+                                   cudaMemcpyDeviceToHost, cs));
             CK(cudaEventRecord(ev_back[c], cs));
         }
         {
-            // the update's pass over X also refines the winners' distances
             PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
-            s = accumulate(ctx, h.X, n, d, h.labels, k, u, h.C, p->low == KM_FP64_DIRECT ? nullptr : h.min_dist, st);
+            s = accumulate(ctx, h.X, n, d, h.labels, k, u, h.C, nullptr, st);
             if (s != KM_OK) return s;
             KL(2, launch_sum_f64(h.min_dist, n, w.partials, kSumParts, w.sse, st));
             if ((s = finalize(ctx, u, n, k, d, h.C, p, h.X, h.min_dist, h.C_new, h.counts, w.cnt, st)) != KM_OK)
                 return s;
         }
-        if (min_dist_host)
-            CK(cudaMemcpyAsync(min_dist_host, h.min_dist, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(C_new_host, h.C_new, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToHost, st));
         if (counts_host) CK(cudaMemcpyAsync(counts_host, h.counts, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, st));
         for (int c = 0; c < nch; c++) CK(cudaStreamWaitEvent(st, ev_back[c], 0));
