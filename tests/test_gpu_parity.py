@@ -754,3 +754,39 @@ def test_sharded_update_equals_whole(ctx):
     rows, vals = ctx.farthest_rows(_dev(md), 50, k=k)
     ref = np.lexsort((np.arange(n), -md))[:50]
     assert np.array_equal(rows.cpu().numpy(), ref) and np.array_equal(vals.cpu().numpy(), md[ref])
+
+
+def test_data_parallel_iteration_on_the_gpu(ctx):
+    """ShardedLloyd (the row-sharded iteration with its exact integer
+    exchange) driving the library on this GPU through a one-rank NCCL group:
+    centres, labels, min_dist and SSE equal km_lloyd_step's, iteration after
+    iteration, empty clusters re-seeded the same way."""
+    import socket
+    import torch.distributed as dist
+    import paper_2407_12208_gb300 as pkg
+    from paper_2407_12208_gb300.dp import ShardedLloyd
+    X, C = workloads.gaussian_mixture(20000, 32, 48, seed=93)
+    C[::7] += 500.0  # far centres: empty clusters in the first iteration
+    Xd, Cd = _dev(X), _dev(C)
+    p = pkg.params("bf16", empty="farthest")
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, world_size=1, rank=0)
+    try:
+        sl = ShardedLloyd(ctx, Xd, C.shape[0], p)
+        Cs, Cr = Cd.clone(), Cd.clone()
+        for it in range(4):
+            Cs, lab_s, md_s, sse_s, sh_s = sl.step(Cs)
+            lab_r, md_r, Cr2, cnt_r, sh_r = ctx.lloyd_step(Xd, Cr, p)
+            sse_r = ctx.stats()["sse"]
+            torch.cuda.synchronize()
+            assert np.array_equal(lab_s.cpu().numpy(), lab_r.cpu().numpy()), it
+            assert np.array_equal(md_s.cpu().numpy().view(np.uint64), md_r.cpu().numpy().view(np.uint64)), it
+            assert np.array_equal(Cs.cpu().numpy().view(np.uint32), Cr2.cpu().numpy().view(np.uint32)), it
+            assert sse_s == sse_r, it
+            assert sh_s == pytest.approx(sh_r, rel=1e-12), it
+            Cr = Cr2
+    finally:
+        dist.destroy_process_group()
