@@ -27,59 +27,63 @@ namespace km {
 
 // fp32 direct values of the candidate pairs.  NV float4 of a row per lane
 // (lane l of a pair's 8 takes float4 l, l + 8, ...); NV == 0: scalar loads
-// for any d and alignment.
+// for any d and alignment.  A group of eight lanes takes two pairs per round
+// (pi and pi + G, G the number of groups), all their loads issued first.
+template <int NV>
+KM_DEV float pair_value(const float* __restrict__ X, const float* __restrict__ C, int d, int2 pr, int sl) {
+    float acc = 0.0f;
+    if (NV > 0) {
+        const int d4 = d >> 2;
+        const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)pr.x * d);
+        const float4* c4 = reinterpret_cast<const float4*>(C + (int64_t)pr.y * d);
+#pragma unroll
+        for (int u = 0; u < NV; u++) {
+            const int c = sl + 8 * u;
+            const float4 xv = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 cv = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float t0 = xv.x - cv.x, t1 = xv.y - cv.y, t2 = xv.z - cv.z, t3 = xv.w - cv.w;
+            acc = fmaf(t0, t0, acc);
+            acc = fmaf(t1, t1, acc);
+            acc = fmaf(t2, t2, acc);
+            acc = fmaf(t3, t3, acc);
+        }
+    } else {
+        const float* x = X + (int64_t)pr.x * d;
+        const float* c = C + (int64_t)pr.y * d;
+        for (int l = sl; l < d; l += 8) {
+            const float t = x[l] - c[l];
+            acc = fmaf(t, t, acc);
+        }
+    }
+    return acc;
+}
+
 template <int NV>
 __global__ void __launch_bounds__(256) k_pair_eval(const float* __restrict__ X, const float* __restrict__ C, int d,
                                                    const int2* __restrict__ pairs,
                                                    const unsigned long long* __restrict__ npairs, int64_t cap,
                                                    float* __restrict__ v32) {
-    constexpr int NVV = NV > 0 ? NV : 1;
     const int lane = threadIdx.x & 31, sl = lane & 7, gbase = lane & ~7;
     const unsigned gmask = 0xFFu << gbase;
     const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + (lane >> 3);
     const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * 4;
     const int64_t np = min((int64_t)*npairs, cap);
-    const int d4 = d >> 2;
-    int2 nxt = (gid < np) ? pairs[gid] : make_int2(0, 0);
-    for (int64_t pi = gid; pi < np; pi += ngroups) {
-        const int2 pr = nxt;
-        if (pi + ngroups < np) nxt = pairs[pi + ngroups];  // the next pair's index, ahead of its use
-        if (pr.x < 0) continue;  // a slot of a row that did not fit (the group's eight lanes alike)
-        float acc = 0.0f;
-        if (NV > 0) {
-            const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)pr.x * d);
-            const float4* c4 = reinterpret_cast<const float4*>(C + (int64_t)pr.y * d);
-            float4 xv[NVV], cv[NVV];
+    for (int64_t pi = gid; pi < np; pi += 2 * ngroups) {
+        const int64_t pj = pi + ngroups;
+        const int2 pa = pairs[pi];
+        const int2 pb = pj < np ? pairs[pj] : make_int2(-1, 0);
+        // a slot of a row that did not fit is marked row -1 (the group's eight lanes alike)
+        float va = pa.x >= 0 ? pair_value<NV>(X, C, d, pa, sl) : 0.0f;
+        float vb = pb.x >= 0 ? pair_value<NV>(X, C, d, pb, sl) : 0.0f;
 #pragma unroll
-            for (int u = 0; u < NVV; u++) {
-                const int c = sl + 8 * u;
-                xv[u] = (c < d4) ? x4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                cv[u] = (c < d4) ? c4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            // the next pair's point row on its way to L2 while this one is
-            // evaluated (rows of 512 bytes or more: measured to pay off there)
-            if (d >= 128 && sl == 0 && pi + ngroups < np && nxt.x >= 0 && nxt.x != pr.x)
-                prefetch_l2_bulk(X + (int64_t)nxt.x * d, (uint32_t)d * 4u);
-#pragma unroll
-            for (int u = 0; u < NVV; u++) {
-                const float t0 = xv[u].x - cv[u].x, t1 = xv[u].y - cv[u].y;
-                const float t2 = xv[u].z - cv[u].z, t3 = xv[u].w - cv[u].w;
-                acc = fmaf(t0, t0, acc);
-                acc = fmaf(t1, t1, acc);
-                acc = fmaf(t2, t2, acc);
-                acc = fmaf(t3, t3, acc);
-            }
-        } else {
-            const float* x = X + (int64_t)pr.x * d;
-            const float* c = C + (int64_t)pr.y * d;
-            for (int l = sl; l < d; l += 8) {
-                const float t = x[l] - c[l];
-                acc = fmaf(t, t, acc);
-            }
+        for (int off = 4; off > 0; off >>= 1) {
+            va += __shfl_xor_sync(gmask, va, off);
+            vb += __shfl_xor_sync(gmask, vb, off);
         }
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) acc += __shfl_xor_sync(gmask, acc, off);
-        if (sl == 0) v32[pi] = acc;
+        if (sl == 0) {
+            if (pa.x >= 0) v32[pi] = va;
+            if (pb.x >= 0) v32[pj] = vb;
+        }
     }
 }
 
