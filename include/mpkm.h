@@ -342,10 +342,12 @@ km_status km_selftest_timeout(km_ctx* ctx, void* ws, size_t ws_bytes, void* stre
  * (n int32), min_dist_host (nullable, n doubles), C_new_host (k x d),
  * counts_host (nullable, k int64) and shift_host (nullable) written, all in
  * host memory; the call returns when they are there (it synchronises
- * `stream`).  The rows travel in up to four chunks of whole 128-row blocks on
- * two copy streams owned by the context: each chunk is assigned (labels and
- * min_dist) as soon as it has arrived and its results go back while the next
- * chunk is assigned; the centre update follows the last chunk.  With pinned (page-locked) host
+ * `stream`).  The rows travel in up to four chunks of whole 128-row blocks,
+ * each about half the size of the one before, on a copy stream owned by the
+ * context (a second one carries the results back): each chunk is assigned
+ * (labels and min_dist) as soon as it has arrived and its results go back
+ * while the next chunk is assigned; the centre update follows the last
+ * chunk.  With pinned (page-locked) host
  * buffers the copies overlap the kernels; pageable ones still give the same
  * results.  The results equal km_lloyd_step on device copies of the same
  * inputs bit for bit.  ws: device memory of km_host_workspace_size bytes

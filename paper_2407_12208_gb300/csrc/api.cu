@@ -997,10 +997,29 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
     // rows in up to kHostChunks chunks of whole 128-row blocks; each chunk is
-    // assigned as soon as it has arrived, while the next one is being copied
+    // assigned as soon as it has arrived, while the next one is being copied.
+    // Each chunk holds about half the rows of the one before (8:4:2:1): a
+    // chunk's assignment takes about a third of the time the host link needs
+    // for the same rows, so the link stays busy, and the last chunk, whose
+    // assignment and the centre update run after the last copy, is small.
     constexpr int kHostChunks = 4;
-    const int64_t R = ((n + kHostChunks - 1) / kHostChunks + 127) / 128 * 128;
-    const int nch = (int)((n + R - 1) / R);
+    constexpr int kChunkWeight[kHostChunks] = {8, 4, 2, 1};
+    int64_t cend[kHostChunks];  // end row of each chunk
+    int nch = 0;
+    {
+        const int64_t nblk = (n + 127) / 128;
+        int wsum = 0, wall = 0;
+        for (int c = 0; c < kHostChunks; c++) wall += kChunkWeight[c];
+        int64_t prev = 0;
+        for (int c = 0; c < kHostChunks; c++) {
+            wsum += kChunkWeight[c];
+            const int64_t eb = (nblk * wsum + wall - 1) / wall;  // end block, rounded up
+            const int64_t er = std::min<int64_t>(eb * 128, n);
+            if (er > prev) cend[nch++] = er;
+            prev = er;
+        }
+    }
+    auto chunk_r0 = [&](int c) -> int64_t { return c == 0 ? 0 : cend[c - 1]; };
     for (int i = 0; i < 2; i++)
         if (!ctx->copy_st[i]) CK(cudaStreamCreateWithFlags(&ctx->copy_st[i], cudaStreamNonBlocking));
     while ((int)ctx->host_ev.size() < 3 * kHostChunks + 1) {
@@ -1019,18 +1038,21 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
         // the copies into the workspace wait for earlier work on the stream
         CK(cudaEventRecord(ev_start, st));
         CK(cudaMemcpyAsync(h.C, C_host, sizeof(float) * (size_t)k * d, cudaMemcpyHostToDevice, st));
+        // host -> device on copy stream 0 in chunk order (each chunk at the
+        // link's full rate), device -> host on copy stream 1
+        CK(cudaStreamWaitEvent(ctx->copy_st[0], ev_start, 0));
+        CK(cudaStreamWaitEvent(ctx->copy_st[1], ev_start, 0));
         for (int c = 0; c < nch; c++) {
-            const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
-            cudaStream_t cs = ctx->copy_st[c & 1];
-            CK(cudaStreamWaitEvent(cs, ev_start, 0));
+            const int64_t r0 = chunk_r0(c), rows = cend[c] - r0;
+            cudaStream_t cs = ctx->copy_st[0];
             CK(cudaMemcpyAsync(h.X + r0 * d, X_host + r0 * d, sizeof(float) * (size_t)rows * d, cudaMemcpyHostToDevice, cs));
             CK(cudaEventRecord(ev_in[c], cs));
         }
         CK(cudaMemsetAsync(w.cnt, 0, sizeof(DevCounters), st));
         CK(cudaMemsetAsync(u.absmax, 0, sizeof(unsigned), st));
         for (int c = 0; c < nch; c++) {
-            const int64_t r0 = c * R, rows = std::min<int64_t>(R, n - r0);
-            cudaStream_t cs = ctx->copy_st[c & 1];
+            const int64_t r0 = chunk_r0(c), rows = cend[c] - r0;
+            cudaStream_t cs = ctx->copy_st[1];
             CK(cudaStreamWaitEvent(st, ev_in[c], 0));
             CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
             s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
