@@ -160,3 +160,38 @@ def test_serving_groups_small_jobs(sctx):
         assert out["iters"] == it_a and out["sse"] == sse_a[-1], q
     for jid in others + [s_[0] for s_ in small]:
         sctx.release(jid)
+
+
+def test_serving_hundred_mixed_jobs_equal_alone(sctx):
+    """100 jobs drawn like the served stream (n log-uniform [1e3, 3e4], d in
+    {2, 8, 32, 128, 256}, k log-uniform [4, 256]; BF16, FP16 and E4M3 on the
+    tensor cores, FP32 and FP64 direct for d <= 8; one in four a single
+    assignment) submitted at once: every result equals the same job run alone
+    through km_lloyd_run / km_assign, bit for bit."""
+    import paper_2407_12208_gb300 as pkg
+    specs = workloads.serving_jobs(100, seed=77, n_lo=1e3, n_hi=3e4, k_hi=256)
+    jobs = []
+    for i, s in enumerate(specs):
+        n, d, k = s["n"], s["d"], s["k"]
+        low = ("fp32", "fp64")[i % 2] if d <= 8 else ("bf16", "fp16", "e4m3")[i % 3]
+        kind = 1 if i % 4 == 3 else 0
+        X, C = workloads.gaussian_mixture(n, d, k, seed=700 + i)
+        p = pkg.params(low, max_iter=5)
+        jobs.append((sctx.submit(X, C, p, kind=kind), X, C, p, kind))
+    for i, (jid, X, C, p, kind) in enumerate(jobs):
+        out = _wait(sctx, jid)
+        assert out["status"] == pkg._binding.KM_OK, (i, out["message"])
+        n, d = X.shape
+        k = C.shape[0]
+        lab_s = pkg.device_array(out["labels"], (n,), "<i4").cpu().numpy()
+        C_s = pkg.device_array(out["C"], (k, d), "<f4").cpu().numpy()
+        Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+        if kind == 0:
+            C_a, lab_a, _, _, _ = sctx.lloyd_run(Xd, Cd, p)
+            torch.cuda.synchronize()
+            assert np.array_equal(C_s.view(np.uint32), C_a.cpu().numpy().view(np.uint32)), i
+        else:
+            lab_a, _, _ = sctx.assign(Xd, Cd, p)
+            torch.cuda.synchronize()
+        assert np.array_equal(lab_s, lab_a.cpu().numpy()), i
+        sctx.release(jid)
