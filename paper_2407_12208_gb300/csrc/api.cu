@@ -378,9 +378,11 @@ int screen_variant(km_ctx* ctx, int fmt, int kchunks, int k, int64_t n) {
     return kchunks == 2 ? TC_SV_HALF : TC_SV_FULL;
 }
 
+// c_prepared: the workspace already holds C's low-precision copy, statistics
+// and column maxima for this C and format (later row chunks of one call).
 km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int k, int d, const km_params* p,
                      int32_t* labels, double* min_dist, const AssignWs& w, bool x_prepared, cudaStream_t st,
-                     unsigned* x_absmax = nullptr) {
+                     unsigned* x_absmax = nullptr, bool c_prepared = false) {
     const TestParams tp = make_tp(p, d);
     km_status s = KM_OK;
     if (p->low == KM_FP64_DIRECT || p->low == KM_FP32_DIRECT) {
@@ -403,7 +405,7 @@ km_status run_assign(km_ctx* ctx, const float* X, int64_t n, const float* C, int
     {
         PhaseScope ps(ctx, KM_PHASE_QUANTISE, st);
         if (!x_prepared) KL(1, launch_quantize(X, n, d, fmt, ldq, w.Xq, w.xstat, w.xscale, st, x_absmax));
-        if ((s = prepare_centres(ctx, C, k, d, fmt, w, st)) != KM_OK) return s;
+        if (!c_prepared && (s = prepare_centres(ctx, C, k, d, fmt, w, st)) != KM_OK) return s;
     }
     TcArgs a{};
     a.n = n; a.k = k; a.d = d; a.fmt = fmt;
@@ -468,12 +470,13 @@ km_status accumulate(km_ctx* ctx, const float* X, int64_t n, int d, const int32_
     return KM_OK;
 }
 
-// Means, empty clusters and shift of the centre update.
+// Means, empty clusters and (want_shift) the shift of the centre update.
 km_status finalize(km_ctx* ctx, const UpdateWs& u, int64_t n, int k, int d, const float* C_old, const km_params* p,
-                   const float* X, const double* md, float* C_new, int64_t* counts, DevCounters* cnt, cudaStream_t st) {
+                   const float* X, const double* md, float* C_new, int64_t* counts, DevCounters* cnt, cudaStream_t st,
+                   bool want_shift) {
     int nl = 0;
-    CK(launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts, u.shift, u.esel,
-                       &cnt->status, ctx->num_sms, st, &nl));
+    CK(launch_finalize(u.sums, u.counts, u.absmax, n, k, d, C_old, p->empty, X, md, C_new, counts,
+                       want_shift ? u.shift : nullptr, u.esel, &cnt->status, ctx->num_sms, st, &nl));
     ctx->launches += (uint64_t)nl;
     return KM_OK;
 }
@@ -828,7 +831,8 @@ km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d, con
         PhaseScope ps(ctx, KM_PHASE_UPDATE, st);
         KL(1, launch_absmax(X, n * (int64_t)d, u.absmax, st));
         if ((s = accumulate(ctx, X, n, d, labels, k, u, nullptr, nullptr, st)) != KM_OK) return s;
-        if ((s = finalize(ctx, u, n, k, d, C_old, p, X, min_dist, C_new, counts, cnt, st)) != KM_OK) return s;
+        if ((s = finalize(ctx, u, n, k, d, C_old, p, X, min_dist, C_new, counts, cnt, st, shift_host != nullptr)) != KM_OK)
+            return s;
     }
     if (shift_host) {
         if ((s = sync_status(ctx, cnt, st)) != KM_OK) return s;
@@ -955,7 +959,8 @@ km_status km_lloyd_step(km_ctx* ctx, const float* X, int64_t n, int d, int k, co
         s = accumulate(ctx, X, n, d, labels, k, u, C_old, p->low == KM_FP64_DIRECT ? nullptr : md, st);
         if (s != KM_OK) return s;
         KL(2, launch_sum_f64(md, n, w.partials, kSumParts, w.sse, st));
-        if ((s = finalize(ctx, u, n, k, d, C_old, p, X, md, C_new, counts, w.cnt, st)) != KM_OK) return s;
+        if ((s = finalize(ctx, u, n, k, d, C_old, p, X, md, C_new, counts, w.cnt, st, shift_host != nullptr)) != KM_OK)
+            return s;
     }
     ctx->last_cnt = w.cnt;
     ctx->last_sse = w.sse;
@@ -1055,7 +1060,9 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
             cudaStream_t cs = ctx->copy_st[1];
             CK(cudaStreamWaitEvent(st, ev_in[c], 0));
             CK(cudaMemsetAsync(&w.cnt->amb_count, 0, 2 * sizeof(int), st));
-            s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax);
+            // the centres are prepared once, with the first chunk
+            s = run_assign(ctx, h.X + r0 * d, rows, h.C, k, d, p, h.labels + r0, h.min_dist + r0, w, false, st, u.absmax,
+                           c > 0);
             if (s != KM_OK) return s;
             // the chunk's winner distances (binary64 accuracy) while the next
             // chunk is still on its way: the update's pass then only sums
@@ -1075,7 +1082,8 @@ km_status km_lloyd_step_host(km_ctx* ctx, const float* X_host, int64_t n, int d,
             s = accumulate(ctx, h.X, n, d, h.labels, k, u, h.C, nullptr, st);
             if (s != KM_OK) return s;
             KL(2, launch_sum_f64(h.min_dist, n, w.partials, kSumParts, w.sse, st));
-            if ((s = finalize(ctx, u, n, k, d, h.C, p, h.X, h.min_dist, h.C_new, h.counts, w.cnt, st)) != KM_OK)
+            if ((s = finalize(ctx, u, n, k, d, h.C, p, h.X, h.min_dist, h.C_new, h.counts, w.cnt, st,
+                              shift_host != nullptr)) != KM_OK)
                 return s;
         }
         CK(cudaMemcpyAsync(C_new_host, h.C_new, sizeof(float) * (size_t)k * d, cudaMemcpyDeviceToHost, st));
@@ -1177,7 +1185,7 @@ static km_status lloyd_iteration(km_ctx* ctx, const float* X, int64_t n, int d, 
     s = accumulate(ctx, X, n, d, labels, k, L.u, cur, p->low == KM_FP64_DIRECT ? nullptr : L.min_dist, st);
     if (s != KM_OK) return s;
     KL(2, launch_sum_f64(L.min_dist, n, L.a.partials, kSumParts, graph ? L.sse_slot : sse_out, st));
-    if ((s = finalize(ctx, L.u, n, k, d, cur, p, X, L.min_dist, nxt, L.counts, L.a.cnt, st)) != KM_OK) return s;
+    if ((s = finalize(ctx, L.u, n, k, d, cur, p, X, L.min_dist, nxt, L.counts, L.a.cnt, st, true)) != KM_OK) return s;
     if (graph) {
         k_record_iteration<<<1, 1, 0, st>>>(L.sse_slot, L.a.cnt, L.sse_hist, L.flag_hist, L.hist_len, cap);
         ctx->launches++;

@@ -625,8 +625,19 @@ __global__ void __launch_bounds__(256) k_empty_select(const long long* __restric
                                                       double* __restrict__ vals_out) {
     __shared__ unsigned sh[256];
     __shared__ int wsum[8];
+    __shared__ int any_empty;
     const unsigned nb = gridDim.x;
     const int t = threadIdx.x;
+    // 0. no empty cluster (the usual case): every block sees it in the counts
+    //    and leaves at once, before any grid barrier
+    if (fixed_e <= 0) {
+        if (t == 0) any_empty = 0;
+        __syncthreads();
+        for (int j = t; j < k; j += blockDim.x)
+            if (counts[j] == 0) any_empty = 1;
+        __syncthreads();
+        if (!any_empty) return;
+    }
     // 1. the empty clusters in ascending j (block 0), histograms cleared
     if (blockIdx.x == 0) {
         for (int e = t; e < 12 * 256; e += blockDim.x) (&es->hist[0][0])[e] = 0u;
@@ -950,12 +961,14 @@ cudaError_t launch_finalize(const long long* sums, const long long* counts, cons
         if (e != cudaSuccess) return e;
         nl++;
     }
-    e = cudaMemsetAsync(shift, 0, sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    const int64_t sblocks = std::min<int64_t>(((int64_t)k * 32 + 255) / 256, (int64_t)num_sms * 8);
-    k_shift<<<(unsigned)std::max<int64_t>(sblocks, 1), 256, 0, st>>>(k, d, C_old, C_new,
-                                                                   reinterpret_cast<unsigned long long*>(shift));
-    nl++;
+    if (shift) {  // null: the caller does not want the shift
+        e = cudaMemsetAsync(shift, 0, sizeof(double), st);
+        if (e != cudaSuccess) return e;
+        const int64_t sblocks = std::min<int64_t>(((int64_t)k * 32 + 255) / 256, (int64_t)num_sms * 8);
+        k_shift<<<(unsigned)std::max<int64_t>(sblocks, 1), 256, 0, st>>>(k, d, C_old, C_new,
+                                                                       reinterpret_cast<unsigned long long*>(shift));
+        nl++;
+    }
     if (nlaunch) *nlaunch = nl;
     return cudaGetLastError();
 }
