@@ -424,6 +424,55 @@ def test_update_small_d_long_label_runs(ctx):
     np.testing.assert_allclose(Cn.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
 
 
+@pytest.mark.parametrize("d", [1, 3, 5, 8])
+@pytest.mark.parametrize("pattern", ["runs", "random", "mixed"])
+def test_small_d_sums_label_patterns(ctx, d, pattern):
+    """The small-d centre sums (one warp scan over runs of equal labels) for
+    labels in long runs, in no order, and both mixed, at ragged row counts:
+    counts exact and centres within the Lemma 4.4 bound of the oracle's."""
+    import paper_2407_12208_gb300 as pkg
+    k = 16 if d <= 5 else 40
+    r = np.random.default_rng(100 + d)
+    for n in (777, 262_417, 1_500_001):
+        X = (r.standard_normal((n, d)) * 3.0 + 1.0).astype(np.float32)
+        if pattern == "runs":
+            lab = ((np.arange(n) // 613) % k).astype(np.int32)
+        elif pattern == "random":
+            lab = r.integers(0, k, size=n).astype(np.int32)
+        else:
+            lab = ((np.arange(n) // 4001) % k).astype(np.int32)
+            noisy = r.random(n) < 0.02
+            lab[noisy] = r.integers(0, k, size=int(noisy.sum())).astype(np.int32)
+        C = r.standard_normal((k, d)).astype(np.float32)
+        p = pkg.params("fp64", empty="keep")
+        Cn, cnt, _ = ctx.update_centroids(_dev(X), _dev(lab), _dev(C), p, min_dist=None)
+        torch.cuda.synchronize()
+        oC, ocnt, _ = oracle.update(X, lab, C, 0, np.zeros(n))
+        assert np.array_equal(cnt.cpu().numpy(), ocnt)
+        np.testing.assert_allclose(Cn.cpu().numpy(), oC, rtol=2 ** -22, atol=1e-30)
+
+
+def test_small_d_image_step_equals_assign_then_update(ctx):
+    """A Voronoi image's pixels (d = 5, labels in long runs): km_lloyd_step,
+    whose small-d centre sums carry each row's distance in the same pass over
+    X, equals km_assign followed by km_update_centroids bit for bit."""
+    import paper_2407_12208_gb300 as pkg
+    X, C = workloads.voronoi_image(640, 480, 12, 12, seed=66)
+    Xd, Cd = _dev(X), _dev(C)
+    p = pkg.params("fp32", empty="keep")
+    lab1, md1, _ = ctx.assign(Xd, Cd, p)
+    Cn1, cnt1, _ = ctx.update_centroids(Xd, lab1, Cd, p, min_dist=md1)
+    lab2, md2, Cn2, cnt2, _ = ctx.lloyd_step(Xd, Cd, p)
+    torch.cuda.synchronize()
+    assert np.array_equal(lab2.cpu().numpy(), lab1.cpu().numpy())
+    assert np.array_equal(md2.cpu().numpy().view(np.uint64), md1.cpu().numpy().view(np.uint64))
+    assert np.array_equal(Cn2.cpu().numpy().view(np.uint32), Cn1.cpu().numpy().view(np.uint32))
+    assert np.array_equal(cnt2.cpu().numpy(), cnt1.cpu().numpy())
+    olab, od, _ = oracle.assign(X, C)
+    assert np.array_equal(lab2.cpu().numpy(), olab)
+    np.testing.assert_allclose(md2.cpu().numpy(), od, rtol=1e-12)
+
+
 # ------------------------------------------------------ quantisation (step a1)
 def _e4m3_edge_rows(d):
     rows = []
