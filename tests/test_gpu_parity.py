@@ -367,6 +367,33 @@ def test_lloyd_step_host_equals_device(ctx, low, empty, shape):
     assert np.array_equal(Cn3.numpy().view(np.uint32), ref[2].view(np.uint32))
 
 
+@pytest.mark.parametrize("low,shape", [("bf16", (20000, 32, 50)), ("fp32", (30000, 5, 16)), ("fp16", (12000, 128, 64))])
+@pytest.mark.parametrize("where", ["later", "first"])
+def test_lloyd_step_host_chunk_scales(ctx, low, shape, where):
+    """km_lloyd_step_host with the largest |x| (and with it the fixed-point
+    scale of the centre sums) in the last chunk, or only in the first: both
+    ways it equals km_lloyd_step bit for bit."""
+    import paper_2407_12208_gb300 as pkg
+    n, d, k = shape
+    X, C = workloads.gaussian_mixture(n, d, k, seed=63)
+    if where == "later":
+        X[n - n // 10:] *= 8.0  # the last chunk holds the largest |x|
+    else:
+        X[: n // 20] *= 8.0     # only the first chunk does
+    p = pkg.params(low, empty="keep")
+    lab1, md1, Cn1, cnt1, sh1 = ctx.lloyd_step(_dev(X), _dev(C), p)
+    torch.cuda.synchronize()
+    Xh, Ch = torch.from_numpy(X).pin_memory(), torch.from_numpy(C).pin_memory()
+    md = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+    cnt = torch.full((k,), -1, dtype=torch.int64).pin_memory()
+    lab2, md2, Cn2, cnt2, sh2 = ctx.lloyd_step_host(Xh, Ch, p, min_dist=md, counts=cnt)
+    assert np.array_equal(lab2.numpy(), lab1.cpu().numpy())
+    assert np.array_equal(md2.numpy().view(np.uint64), md1.cpu().numpy().view(np.uint64))
+    assert np.array_equal(Cn2.numpy().view(np.uint32), Cn1.cpu().numpy().view(np.uint32))
+    assert np.array_equal(cnt2.numpy(), cnt1.cpu().numpy())
+    assert sh2 == sh1
+
+
 def test_lloyd_step_host_rejects_bad_arguments(ctx):
     import paper_2407_12208_gb300 as pkg
     p = pkg.params("bf16")
