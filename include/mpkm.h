@@ -230,7 +230,8 @@ km_status km_set_screen_variant(km_ctx* ctx, int64_t n, int d, int k, int32_t lo
  * (order-independent, hence deterministic), divided in binary64 and stored
  * in fp32.  counts (k int64), C_new (k x d fp32).  min_dist (nullable, n
  * doubles) is needed only for KM_EMPTY_FARTHEST.  shift_host (nullable,
- * host): max_j ||c_new_j - c_old_j||. */
+ * host): max_j ||c_new_j - c_old_j||; with NULL the shift is not computed
+ * (here and in km_lloyd_step / km_lloyd_step_host). */
 km_status km_update_centroids(km_ctx* ctx, const float* X, int64_t n, int d,
                               const int32_t* labels, int k, const float* C_old,
                               const km_params* p, const double* min_dist, float* C_new,
