@@ -52,6 +52,19 @@ WORKLOADS = {
 METRIC = "point-center pairs/s (dist+argmin)"
 
 
+def _direct_kernel_name(low: str, d: int, k: int) -> str:
+    """The direct-formula kernel the library launches for this shape (the
+    same choice as its launcher: small d with C in shared memory, the tiled
+    FP32 kernel for 16 <= d <= 128 with d % 4 == 0, else one thread per row)."""
+    if low == "fp64":
+        return "k_direct_assign<double>"
+    if d <= 8 and k * d * 4 <= 32 * 1024:
+        return "k_direct_small<%d>" % d
+    if d % 4 == 0 and 16 <= d <= 128:
+        return "k_direct_tiled"
+    return "k_direct_assign<float>"
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -284,7 +297,7 @@ def run_ours(args):
         gbs = nbytes / (dir_ms / max(dir_cnt, 1) / 1e3) / 1e9 if dir_cnt else None
         hbm = (peaks or {}).get("hbm_gbs") or 6800.0
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": (gbs / hbm) if gbs else None,
-                "traffic": None, "kernel": "k_direct_assign<%s>" % ("float" if args.low == "fp32" else "double"),
+                "traffic": None, "kernel": _direct_kernel_name(args.low, d, k),
                 "algorithmic_bytes_per_launch": nbytes,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"}
 

@@ -52,3 +52,15 @@ def test_profile_traffic_only_for_the_profiled_source(monkeypatch):
     assert bench._profile_traffic(1000) == per_row * 1000
     monkeypatch.setattr(bench, "screen_source_hash", lambda: "0" * 16)
     assert bench._profile_traffic(1000) is None
+
+
+def test_direct_kernel_name_follows_the_launcher():
+    """The roofline line names the direct-formula kernel the library runs for
+    the shape: small d with C in shared memory, the tiled FP32 kernel for
+    16 <= d <= 128 with d % 4 == 0, one thread per row otherwise, FP64 alone."""
+    import bench
+    assert bench._direct_kernel_name("fp32", 5, 16) == "k_direct_small<5>"
+    assert bench._direct_kernel_name("fp32", 8, 2048) == "k_direct_assign<float>"  # C over 32 KB
+    assert bench._direct_kernel_name("fp32", 128, 1024) == "k_direct_tiled"
+    assert bench._direct_kernel_name("fp32", 130, 64) == "k_direct_assign<float>"
+    assert bench._direct_kernel_name("fp64", 5, 16) == "k_direct_assign<double>"
